@@ -1,0 +1,249 @@
+/*
+ * qs.h -- C ABI of the GB300 (sm_103a) state-vector simulator library (libqs.so).
+ *
+ * The library implements the hot path of the Schroedinger-type simulator in
+ * "Fast simulation of quantum algorithms using circuit optimization"
+ * (arXiv 2010.09746): 1- and 2-qubit (and fused k-qubit) gates applied to a vector
+ * of 2^n complex amplitudes, the qubit-order permutation instruction PermuteQubits,
+ * and the compiler pass that inserts permutations so that most gates run without
+ * "communication".  On one GPU the paper's local/global qubit split (Sec. 2) becomes
+ * the split between the storage bits of a shared-memory tile and the others: a tile
+ * pass applies every gate whose non-diagonal qubits sit in the tile in one HBM read
+ * and one HBM write.
+ *
+ * Conventions (all calls):
+ *  - Qubit q of a gate is a LOGICAL qubit.  Amplitude alpha_i, i = sum_q i_q 2^q, is
+ *    stored at component j(i, sigma) = sum_q i_q 2^{sigma(q)} of the device vector
+ *    (Sec. 2); sigma starts as the identity and changes only through qs_permute or
+ *    plans that contain permutations.
+ *  - Matrices are host memory owned by the caller, read during the call, row-major,
+ *    complex entries as (re, im) pairs of doubles.  For a k-qubit matrix on qubits
+ *    (q_0 .. q_{k-1}) the row/column index is r = sum_t b(q_t) 2^t (first listed qubit
+ *    is the least significant bit).  Controlled gates list (control, target).
+ *  - Calls that only enqueue GPU work are asynchronous on the state's stream; read-outs
+ *    (qs_probabilities, qs_get_amplitudes, qs_norm) synchronise that stream.
+ *  - Every call returns a qs_status; on failure qs_last_error() gives a thread-local
+ *    message.  No call throws across the ABI.  Bad arguments return QS_EINVAL and leave
+ *    the state unchanged.
+ *  - Device memory comes from the allocator installed with qs_set_allocator, else from
+ *    cudaMallocAsync on the state's stream.
+ */
+#ifndef QS_H
+#define QS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qs_state* qs_handle;   /* opaque, owned by the library */
+typedef struct qs_plan* qs_plan_t;    /* opaque compiled circuit, owned by the library */
+
+typedef enum { QS_C64 = 0, QS_C128 = 1 } qs_dtype;
+
+typedef enum {
+  QS_OK = 0,
+  QS_EINVAL = 1,       /* invalid argument (qubit out of range, duplicate qubits, ...) */
+  QS_ENOMEM = 2,       /* device allocation failed */
+  QS_ECUDA = 3,        /* a CUDA call failed */
+  QS_ETIMEOUT = 4,     /* a bounded device-side wait ran out (status word set by a kernel) */
+  QS_EBUSY = 5,        /* resource in use */
+  QS_EUNSUPPORTED = 6  /* valid request this build does not implement */
+} qs_status;
+
+/* Arithmetic used for complex128 states (complex64 always computes in FP32). */
+typedef enum {
+  QS_ARITH_AUTO = 0,   /* QS_ARITH_DF for complex128 */
+  QS_ARITH_DF = 1,     /* double-float (pairs of FP32) arithmetic, FP64 storage */
+  QS_ARITH_F64 = 2     /* native FP64 arithmetic */
+} qs_arith;
+
+/* Gate kinds of qs_op.kind (definitions as in the standard literature):
+ * H = (X+Z)/sqrt2, RZ(t) = exp(-i t Z/2), RX(t) = exp(-i t X/2), RY(t) = exp(-i t Y/2),
+ * P(t) = diag(1, e^{it}), S = P(pi/2), T = P(pi/4), CP(t) = controlled P(t). */
+enum {
+  QS_OP_U1 = 0,   /* arbitrary 2x2, matrix at mats[mat .. mat+7] */
+  QS_OP_H = 1, QS_OP_X = 2, QS_OP_Y = 3, QS_OP_Z = 4, QS_OP_S = 5, QS_OP_T = 6,
+  QS_OP_RZ = 7, QS_OP_RX = 8, QS_OP_RY = 9, QS_OP_P = 10,
+  QS_OP_CNOT = 11, QS_OP_CZ = 12, QS_OP_CP = 13,
+  QS_OP_CU = 14,  /* controlled arbitrary 2x2, matrix at mats[mat .. mat+7] */
+  QS_OP_SWAP = 15,
+  QS_OP_U2 = 16,  /* arbitrary 4x4, 32 doubles at mats[mat ..] */
+  QS_OP_UK = 17   /* arbitrary 2^k x 2^k (k = nq <= 6), 2*4^k doubles at mats[mat ..] */
+};
+
+/* One gate of a circuit.  48 bytes, no padding. */
+typedef struct {
+  int32_t kind;    /* QS_OP_* */
+  int32_t nq;      /* number of qubits used in q[] */
+  int32_t q[6];    /* logical qubits */
+  double param;    /* angle for RZ/RX/RY/P/CP */
+  int64_t mat;     /* offset in doubles into the caller's matrix buffer, -1 if unused */
+} qs_op;
+
+/* Compilation modes of qs_compile / qs_run. */
+typedef enum {
+  QS_MODE_PERGATE = 0,  /* one strided-pair kernel launch per gate, no reordering */
+  QS_MODE_PAPER = 1,    /* Algorithm 1 (Sec. 3) with m = tile bits: runs of local gates fused
+                           into tile passes over storage bits [0, L), one local<->global
+                           transposition per PermuteQubits, non-local gates per gate */
+  QS_MODE_TILE = 2      /* tile passes over gathered bit sets: each pass picks the L storage
+                           bits (the low `low_bits` always included) that let the most gates
+                           run; equivalent to a multi-transposition permutation folded into
+                           the pass's addressing, so no separate permutation pass is needed */
+} qs_mode;
+
+typedef struct {
+  int32_t mode;       /* qs_mode */
+  int32_t dtype;      /* qs_dtype of the states the plan will run on */
+  int32_t arith;      /* qs_arith */
+  int32_t tile_bits;  /* L: amplitudes per tile = 2^L, 1..14; 0 = default for the dtype.
+                         QS_MODE_PAPER: the number m of local qubits, 1..n (runs of local
+                         gates execute gate by gate when m > 14) */
+  int32_t low_bits;   /* storage bits always inside a tile (contiguous segment = 2^low_bits
+                         amplitudes); 0 = default */
+  int32_t max_ops;    /* cap on gates per tile pass, 0 = none */
+  int32_t scoring;    /* Algorithm 1 candidate score: 0 = closure (default), 1 = frontier */
+  int32_t flags;      /* reserved, must be 0 */
+} qs_compile_opts;
+
+typedef struct {
+  int64_t n_gates;        /* gates in the input circuit */
+  int64_t n_passes;       /* tile passes */
+  int64_t n_pergate;      /* gates executed by per-gate kernels */
+  int64_t n_permutes;     /* permutation kernels */
+  int64_t n_comm_gates;   /* QS_MODE_PAPER: gates executed non-locally */
+  double hbm_bytes;       /* algorithmic HBM bytes of one execution (reads + writes) */
+  double compile_ms;      /* host time spent compiling */
+} qs_plan_stats;
+
+/* Per-kernel-class timing collected while profiling is on (qs_set_profiling). */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double total_ms;        /* sum of CUDA-event durations on the state's stream */
+  double bytes;           /* algorithmic HBM bytes of those launches */
+} qs_kernel_stat;
+
+/* ---- library ------------------------------------------------------------------------ */
+
+/* Thread-local description of the last failure of the calling thread ("" if none). */
+const char* qs_last_error(void);
+
+/* Library version string. */
+const char* qs_version(void);
+
+/* Install a device allocator used by every later allocation: alloc(bytes, ctx, stream)
+ * returns a device pointer or NULL; free(ptr, bytes, ctx, stream) releases it.  Pass
+ * NULLs to restore the default (cudaMallocAsync/cudaFreeAsync).  The callbacks must stay
+ * valid until the last state / plan is destroyed. */
+qs_status qs_set_allocator(void* (*alloc_fn)(size_t bytes, void* ctx, void* stream),
+                           void (*free_fn)(void* ptr, size_t bytes, void* ctx, void* stream),
+                           void* ctx);
+
+/* ---- states (Sec. 2: the 2^n-amplitude vector and its qubit permutation sigma) ------ */
+
+/* Allocate a state of n qubits (1 <= n <= 36) on the current device, set to |0...0>
+ * with sigma = identity.  Work is enqueued on the default stream until qs_set_stream. */
+qs_status qs_create(int n, qs_dtype dtype, qs_handle* out);
+qs_status qs_destroy(qs_handle h);
+
+/* Stream (cudaStream_t) on which all later work of this state is enqueued. */
+qs_status qs_set_stream(qs_handle h, void* stream);
+
+/* Arithmetic for complex128 gate application through the qs_apply_* calls. */
+qs_status qs_set_arith(qs_handle h, qs_arith arith);
+
+/* Record CUDA events around every kernel launch of this state (per-kernel-class totals
+ * in qs_get_kernel_stats).  Costs two events per launch. */
+qs_status qs_set_profiling(qs_handle h, int on);
+qs_status qs_get_kernel_stats(qs_handle h, qs_kernel_stat* out, int max, int* count);
+qs_status qs_reset_kernel_stats(qs_handle h);
+
+/* Re-initialise to |0...0> and sigma = identity (state preparation, Sec. 2). */
+qs_status qs_reset(qs_handle h);
+
+qs_status qs_get_info(qs_handle h, int* n, qs_dtype* dtype, void** device_ptr, size_t* bytes);
+qs_status qs_sync(qs_handle h);
+
+/* ---- gates (Sec. 2: arbitrary 1-qubit gates, controlled 1-qubit gates) ------------- */
+
+/* Arbitrary 1-qubit gate U (8 doubles) on logical qubit q: for every amplitude pair
+ * differing only in qubit q, (a0, a1) <- U (a0, a1). */
+qs_status qs_apply_1q(qs_handle h, const double* U, int q);
+
+/* Arbitrary 2-qubit gate U (32 doubles, r = b(q0) + 2 b(q1)) on logical qubits q0 != q1. */
+qs_status qs_apply_2q(qs_handle h, const double* U, int q0, int q1);
+
+/* Controlled 1-qubit gate: U applied to qubit t on the amplitudes whose qubit c is 1
+ * (CNOT is U = X). */
+qs_status qs_apply_controlled(qs_handle h, const double* U, int c, int t);
+
+/* Dense k-qubit gate (1 <= k <= 6, 2*4^k doubles) on distinct logical qubits[0..k-1]. */
+qs_status qs_apply_dense(qs_handle h, const double* U, int k, const int* qubits);
+
+/* ---- qubit permutation (Sec. 2 PermuteQubits; Appendix A) -------------------------- */
+
+/* PermuteQubits(sigma'): perm[q] is the new storage bit of logical qubit q (a
+ * permutation of 0..n-1, else QS_EINVAL).  Rewrites the vector so that alpha_i moves
+ * from j(i, sigma) to j(i, sigma'); a pure move, bit-exact.  Uses a scratch vector the
+ * size of the state unless sigma' differs from sigma only inside one tile. */
+qs_status qs_permute(qs_handle h, const int* perm);
+/* Current sigma: perm_out[q] = storage bit of logical qubit q (n ints). */
+qs_status qs_get_permutation(qs_handle h, int* perm_out);
+
+/* ---- circuits and the compiler pass (Sec. 3, Algorithm 1) -------------------------- */
+
+/* Compile n-qubit circuit `ops` (matrix data in `mats`, nmats doubles) for states whose
+ * permutation is currently sigma0 (NULL = identity).  opts NULL = defaults (QS_MODE_TILE,
+ * complex128).  The plan holds copies of everything it needs, on host and device. */
+qs_status qs_compile(int n, const qs_op* ops, size_t nops, const double* mats, size_t nmats,
+                     const int* sigma0, const qs_compile_opts* opts, qs_plan_t* out);
+qs_status qs_plan_destroy(qs_plan_t p);
+qs_status qs_plan_get_stats(qs_plan_t p, qs_plan_stats* out);
+/* sigma after the plan has run (n ints). */
+qs_status qs_plan_final_permutation(qs_plan_t p, int* perm_out);
+
+/* The schedule the compiler emitted: entry i is (kinds[i], values[i]) with
+ * kind 0 = gate run locally / inside a tile pass (value = gate index), 1 = gate run by the
+ * per-gate kernel as a non-local gate (QS_MODE_PAPER), 2 = permutation exchanging logical
+ * qubits l and g (value = 64 l + g, QS_MODE_PAPER), 3 and 4 = start of a tile pass whose
+ * storage-bit set is (value of 3) | (value of 4) << 31 (QS_MODE_TILE).  Up to `max` entries
+ * are written; *count gets the total.  Empty for QS_MODE_PERGATE. */
+qs_status qs_plan_get_trace(qs_plan_t p, int32_t* kinds, int32_t* values, size_t max, size_t* count);
+
+/* Enqueue the plan on the state's stream.  The state must have the plan's n and dtype and
+ * the permutation the plan was compiled for; afterwards sigma is the plan's final one. */
+qs_status qs_execute(qs_handle h, qs_plan_t p);
+
+/* qs_compile + qs_execute + qs_plan_destroy. */
+qs_status qs_run(qs_handle h, const qs_op* ops, size_t nops, const double* mats, size_t nmats,
+                 const qs_compile_opts* opts);
+
+/* ---- read-outs (Sec. 2: measurement) ------------------------------------------------ */
+
+enum { QS_ORDER_LOGICAL = 0, QS_ORDER_STORAGE = 1 };
+
+/* p[i] = |alpha_i|^2 for all 2^n i into HOST memory `out` (logical order: index i;
+ * storage order: index j).  Synchronises the stream. */
+qs_status qs_probabilities(qs_handle h, double* out, int order);
+
+/* `count` amplitudes starting at index `first` (logical or storage order) into HOST memory
+ * `out`, as interleaved (re, im) in the state's dtype (float for complex64, double for
+ * complex128).  Synchronises the stream. */
+qs_status qs_get_amplitudes(qs_handle h, void* out, uint64_t first, uint64_t count, int order);
+
+/* Overwrite the whole vector from HOST memory (storage order under the current sigma,
+ * interleaved, the state's dtype); for checkpoint / restore and tests. */
+qs_status qs_set_amplitudes(qs_handle h, const void* in);
+
+/* sum_i |alpha_i|^2 accumulated in FP64 with a fixed reduction order (deterministic).
+ * Synchronises the stream. */
+qs_status qs_norm(qs_handle h, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QS_H */

@@ -1,0 +1,293 @@
+"""GB300 (sm_103a) state-vector simulator: Python binding of libqs.so.
+
+Thin ctypes marshalling over the C ABI of include/qs.h -- gates, PermuteQubits, the
+compiler pass and the read-outs all run in the library's CUDA kernels (there is no
+CPU implementation here).  PyTorch is optional plumbing: `use_torch_allocator()` routes
+device allocations through torch's caching allocator and `State.set_stream` accepts a
+torch.cuda.Stream.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Iterable, List, Optional, Sequence
+
+import numpy as np
+
+from . import _lib
+from ._lib import (QS_ARITH_AUTO, QS_ARITH_DF, QS_ARITH_F64, QS_C64, QS_C128, QS_MODE_PAPER,
+                   QS_MODE_PERGATE, QS_MODE_TILE, QS_ORDER_LOGICAL, QS_ORDER_STORAGE, QSError)
+
+__all__ = ["State", "Plan", "compile", "marshal", "use_torch_allocator", "QSError", "QS_C64", "QS_C128",
+           "QS_MODE_PERGATE", "QS_MODE_PAPER", "QS_MODE_TILE", "QS_ARITH_AUTO", "QS_ARITH_DF", "QS_ARITH_F64",
+           "QS_ORDER_LOGICAL", "QS_ORDER_STORAGE", "lib_path"]
+
+_DTYPES = {"c64": QS_C64, "c128": QS_C128, QS_C64: QS_C64, QS_C128: QS_C128}
+_MODES = {"pergate": QS_MODE_PERGATE, "paper": QS_MODE_PAPER, "tile": QS_MODE_TILE,
+          QS_MODE_PERGATE: QS_MODE_PERGATE, QS_MODE_PAPER: QS_MODE_PAPER, QS_MODE_TILE: QS_MODE_TILE}
+_ARITH = {"auto": QS_ARITH_AUTO, "df": QS_ARITH_DF, "f64": QS_ARITH_F64,
+          QS_ARITH_AUTO: QS_ARITH_AUTO, QS_ARITH_DF: QS_ARITH_DF, QS_ARITH_F64: QS_ARITH_F64}
+
+
+def lib_path() -> str:
+    return _lib.LIB_PATH
+
+
+def _L():
+    return _lib.load()
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _cmat(m) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(m, dtype=np.complex128)).view(np.float64).ravel().copy()
+
+
+def marshal(circuit: Iterable):
+    """Gate objects (attributes kind, qubits, param, matrix) -> (qs_op array, matrix doubles)."""
+    gates = list(circuit)
+    ops = (_lib.qs_op * max(1, len(gates)))()
+    mats: List[np.ndarray] = []
+    off = 0
+    for i, g in enumerate(gates):
+        o = ops[i]
+        o.kind = _lib.OP_CODES[g.kind]
+        qs = tuple(g.qubits)
+        o.nq = len(qs)
+        for t, q in enumerate(qs):
+            o.q[t] = int(q)
+        o.param = float(getattr(g, "param", 0.0) or 0.0)
+        m = getattr(g, "matrix", None)
+        if m is not None:
+            flat = _cmat(m)
+            o.mat = off
+            mats.append(flat)
+            off += flat.size
+        else:
+            o.mat = -1
+    buf = np.concatenate(mats) if mats else np.zeros(1)
+    return ops, len(gates), np.ascontiguousarray(buf, dtype=np.float64)
+
+
+def _opts(mode="tile", dtype="c128", arith="auto", tile_bits=0, low_bits=0, max_ops=0, scoring=0):
+    o = _lib.qs_compile_opts()
+    o.mode = _MODES[mode]
+    o.dtype = _DTYPES[dtype]
+    o.arith = _ARITH[arith]
+    o.tile_bits = tile_bits
+    o.low_bits = low_bits
+    o.max_ops = max_ops
+    o.scoring = scoring
+    o.flags = 0
+    return o
+
+
+class Plan:
+    """A compiled circuit (qs_compile); run it with State.execute."""
+
+    def __init__(self, n: int, circuit: Iterable, sigma0: Optional[Sequence[int]] = None, **opts):
+        L = _L()
+        self.n = n
+        ops, nops, mats = marshal(circuit)
+        self._opts = _opts(**opts)
+        s0 = None
+        if sigma0 is not None:
+            s0 = np.ascontiguousarray(sigma0, dtype=np.int32)
+        h = ctypes.c_void_p()
+        _lib.check(L.qs_compile(n, ops, nops, _dp(mats), mats.size, _ip(s0) if s0 is not None else None,
+                                ctypes.byref(self._opts), ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _L().qs_plan_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stats(self) -> dict:
+        st = _lib.qs_plan_stats()
+        _lib.check(_L().qs_plan_get_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def final_permutation(self) -> List[int]:
+        out = np.zeros(self.n, dtype=np.int32)
+        _lib.check(_L().qs_plan_final_permutation(self._h, _ip(out)))
+        return [int(x) for x in out]
+
+    def trace(self):
+        cnt = ctypes.c_size_t()
+        _lib.check(_L().qs_plan_get_trace(self._h, None, None, 0, ctypes.byref(cnt)))
+        k = np.zeros(max(1, cnt.value), dtype=np.int32)
+        v = np.zeros(max(1, cnt.value), dtype=np.int32)
+        _lib.check(_L().qs_plan_get_trace(self._h, k.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                          v.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), cnt.value,
+                                          ctypes.byref(cnt)))
+        return [(int(a), int(b)) for a, b in zip(k[:cnt.value], v[:cnt.value])]
+
+
+def compile(n: int, circuit: Iterable, sigma0=None, **opts) -> Plan:
+    return Plan(n, circuit, sigma0, **opts)
+
+
+class State:
+    """2^n complex amplitudes on the GPU (qs_create)."""
+
+    def __init__(self, n: int, dtype="c128", arith="auto", stream=None):
+        L = _L()
+        self.n = n
+        self.dtype = _DTYPES[dtype]
+        self.arith = _ARITH[arith]
+        h = ctypes.c_void_p()
+        _lib.check(L.qs_create(n, self.dtype, ctypes.byref(h)))
+        self._h = h
+        if arith != "auto":
+            _lib.check(L.qs_set_arith(h, _ARITH[arith]))
+        if stream is not None:
+            self.set_stream(stream)
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _L().qs_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    @property
+    def np_dtype(self):
+        return np.complex128 if self.dtype == QS_C128 else np.complex64
+
+    def set_stream(self, stream):
+        ptr = getattr(stream, "cuda_stream", stream)
+        _lib.check(_L().qs_set_stream(self._h, ctypes.c_void_p(int(ptr) if ptr else 0)))
+
+    def set_arith(self, arith):
+        _lib.check(_L().qs_set_arith(self._h, _ARITH[arith]))
+        self.arith = _ARITH[arith]
+
+    def set_profiling(self, on: bool):
+        _lib.check(_L().qs_set_profiling(self._h, 1 if on else 0))
+
+    def kernel_stats(self) -> List[dict]:
+        cnt = ctypes.c_int()
+        buf = (_lib.qs_kernel_stat * 64)()
+        _lib.check(_L().qs_get_kernel_stats(self._h, buf, 64, ctypes.byref(cnt)))
+        return [{"name": buf[i].name.decode(), "launches": buf[i].launches, "total_ms": buf[i].total_ms,
+                 "bytes": buf[i].bytes} for i in range(min(cnt.value, 64))]
+
+    def reset_kernel_stats(self):
+        _lib.check(_L().qs_reset_kernel_stats(self._h))
+
+    def reset(self):
+        _lib.check(_L().qs_reset(self._h))
+
+    def sync(self):
+        _lib.check(_L().qs_sync(self._h))
+
+    def device_ptr(self) -> int:
+        p = ctypes.c_void_p()
+        _lib.check(_L().qs_get_info(self._h, None, None, ctypes.byref(p), None))
+        return int(p.value or 0)
+
+    # -- gates ----------------------------------------------------------------------------
+    def apply_1q(self, U, q: int):
+        _lib.check(_L().qs_apply_1q(self._h, _dp(_cmat(U)), int(q)))
+
+    def apply_2q(self, U, q0: int, q1: int):
+        _lib.check(_L().qs_apply_2q(self._h, _dp(_cmat(U)), int(q0), int(q1)))
+
+    def apply_controlled(self, U, c: int, t: int):
+        _lib.check(_L().qs_apply_controlled(self._h, _dp(_cmat(U)), int(c), int(t)))
+
+    def apply_dense(self, U, qubits: Sequence[int]):
+        qs = np.ascontiguousarray(qubits, dtype=np.int32)
+        _lib.check(_L().qs_apply_dense(self._h, _dp(_cmat(U)), len(qs), _ip(qs)))
+
+    def permute(self, perm: Sequence[int]):
+        p = np.ascontiguousarray(perm, dtype=np.int32)
+        if p.size != self.n:
+            raise QSError(_lib.QS_EINVAL, "perm must have n entries")
+        _lib.check(_L().qs_permute(self._h, _ip(p)))
+
+    def permutation(self) -> List[int]:
+        out = np.zeros(self.n, dtype=np.int32)
+        _lib.check(_L().qs_get_permutation(self._h, _ip(out)))
+        return [int(x) for x in out]
+
+    def execute(self, plan: Plan):
+        _lib.check(_L().qs_execute(self._h, plan.handle))
+
+    def run(self, circuit: Iterable, **opts):
+        ops, nops, mats = marshal(circuit)
+        opts.setdefault("arith", self.arith)
+        o = _opts(dtype=self.dtype, **opts)
+        _lib.check(_L().qs_run(self._h, ops, nops, _dp(mats), mats.size, ctypes.byref(o)))
+
+    # -- read-outs ------------------------------------------------------------------------
+    def probabilities(self, order=QS_ORDER_LOGICAL) -> np.ndarray:
+        out = np.empty(1 << self.n, dtype=np.float64)
+        _lib.check(_L().qs_probabilities(self._h, _dp(out), order))
+        return out
+
+    def amplitudes(self, first: int = 0, count: Optional[int] = None, order=QS_ORDER_LOGICAL) -> np.ndarray:
+        if count is None:
+            count = (1 << self.n) - first
+        out = np.empty(count, dtype=self.np_dtype)
+        _lib.check(_L().qs_get_amplitudes(self._h, out.ctypes.data_as(ctypes.c_void_p), first, count, order))
+        return out
+
+    def set_amplitudes(self, storage_vec: np.ndarray):
+        a = np.ascontiguousarray(storage_vec, dtype=self.np_dtype)
+        if a.size != (1 << self.n):
+            raise QSError(_lib.QS_EINVAL, "vector must have 2^n entries")
+        _lib.check(_L().qs_set_amplitudes(self._h, a.ctypes.data_as(ctypes.c_void_p)))
+
+    def norm(self) -> float:
+        out = ctypes.c_double()
+        _lib.check(_L().qs_norm(self._h, ctypes.byref(out)))
+        return out.value
+
+
+_torch_cb = None
+
+
+def use_torch_allocator(device: int = 0):
+    """Route every device allocation of the library through torch's caching allocator."""
+    global _torch_cb
+    import torch
+
+    def _alloc(nbytes, ctx, stream):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), device, stream if stream else None))
+        except Exception:  # noqa: BLE001 - allocation failure is reported as NULL
+            return None
+
+    def _free(ptr, nbytes, ctx, stream):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a = _lib.ALLOC_FN(_alloc)
+    f = _lib.FREE_FN(_free)
+    _lib.check(_L().qs_set_allocator(a, f, None))
+    _torch_cb = (a, f)
+
+
+def use_default_allocator():
+    global _torch_cb
+    null_a = ctypes.cast(None, _lib.ALLOC_FN)
+    null_f = ctypes.cast(None, _lib.FREE_FN)
+    _lib.check(_L().qs_set_allocator(null_a, null_f, None))
+    _torch_cb = None

@@ -1,0 +1,125 @@
+"""ctypes declarations of libqs.so (the C ABI in include/qs.h).
+
+Argument marshalling only: every step of the hot path runs in the library's CUDA
+kernels.  Loading fails loudly when the library is missing; there is no CPU path.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqs.so")
+
+# enums (include/qs.h)
+QS_C64, QS_C128 = 0, 1
+QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EBUSY, QS_EUNSUPPORTED = range(7)
+QS_ARITH_AUTO, QS_ARITH_DF, QS_ARITH_F64 = 0, 1, 2
+QS_MODE_PERGATE, QS_MODE_PAPER, QS_MODE_TILE = 0, 1, 2
+QS_ORDER_LOGICAL, QS_ORDER_STORAGE = 0, 1
+OP_CODES = {"U1": 0, "H": 1, "X": 2, "Y": 3, "Z": 4, "S": 5, "T": 6, "RZ": 7, "RX": 8, "RY": 9, "P": 10,
+            "CNOT": 11, "CZ": 12, "CP": 13, "CU": 14, "SWAP": 15, "U2": 16, "UK": 17}
+STATUS_NAMES = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ECUDA", 4: "QS_ETIMEOUT", 5: "QS_EBUSY",
+                6: "QS_EUNSUPPORTED"}
+
+
+class qs_op(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("nq", ctypes.c_int32), ("q", ctypes.c_int32 * 6),
+                ("param", ctypes.c_double), ("mat", ctypes.c_int64)]
+
+
+class qs_compile_opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("dtype", ctypes.c_int32), ("arith", ctypes.c_int32),
+                ("tile_bits", ctypes.c_int32), ("low_bits", ctypes.c_int32), ("max_ops", ctypes.c_int32),
+                ("scoring", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class qs_plan_stats(ctypes.Structure):
+    _fields_ = [("n_gates", ctypes.c_int64), ("n_passes", ctypes.c_int64), ("n_pergate", ctypes.c_int64),
+                ("n_permutes", ctypes.c_int64), ("n_comm_gates", ctypes.c_int64), ("hbm_bytes", ctypes.c_double),
+                ("compile_ms", ctypes.c_double)]
+
+
+class qs_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+assert ctypes.sizeof(qs_op) == 48
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_H = ctypes.c_void_p
+_I = ctypes.c_int
+_P = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+_I32P = ctypes.POINTER(ctypes.c_int32)
+
+# name -> (restype, argtypes); every symbol declared in include/qs.h
+SIGNATURES = {
+    "qs_last_error": (ctypes.c_char_p, []),
+    "qs_version": (ctypes.c_char_p, []),
+    "qs_set_allocator": (_I, [ALLOC_FN, FREE_FN, _P]),
+    "qs_create": (_I, [_I, _I, ctypes.POINTER(_H)]),
+    "qs_destroy": (_I, [_H]),
+    "qs_set_stream": (_I, [_H, _P]),
+    "qs_set_arith": (_I, [_H, _I]),
+    "qs_set_profiling": (_I, [_H, _I]),
+    "qs_get_kernel_stats": (_I, [_H, ctypes.POINTER(qs_kernel_stat), _I, _IP]),
+    "qs_reset_kernel_stats": (_I, [_H]),
+    "qs_reset": (_I, [_H]),
+    "qs_get_info": (_I, [_H, _IP, _IP, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_size_t)]),
+    "qs_sync": (_I, [_H]),
+    "qs_apply_1q": (_I, [_H, _DP, _I]),
+    "qs_apply_2q": (_I, [_H, _DP, _I, _I]),
+    "qs_apply_controlled": (_I, [_H, _DP, _I, _I]),
+    "qs_apply_dense": (_I, [_H, _DP, _I, _IP]),
+    "qs_permute": (_I, [_H, _IP]),
+    "qs_get_permutation": (_I, [_H, _IP]),
+    "qs_compile": (_I, [_I, ctypes.POINTER(qs_op), ctypes.c_size_t, _DP, ctypes.c_size_t, _IP,
+                        ctypes.POINTER(qs_compile_opts), ctypes.POINTER(_H)]),
+    "qs_plan_destroy": (_I, [_H]),
+    "qs_plan_get_stats": (_I, [_H, ctypes.POINTER(qs_plan_stats)]),
+    "qs_plan_final_permutation": (_I, [_H, _IP]),
+    "qs_plan_get_trace": (_I, [_H, _I32P, _I32P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "qs_execute": (_I, [_H, _H]),
+    "qs_run": (_I, [_H, ctypes.POINTER(qs_op), ctypes.c_size_t, _DP, ctypes.c_size_t,
+                    ctypes.POINTER(qs_compile_opts)]),
+    "qs_probabilities": (_I, [_H, _DP, _I]),
+    "qs_get_amplitudes": (_I, [_H, _P, ctypes.c_uint64, ctypes.c_uint64, _I]),
+    "qs_set_amplitudes": (_I, [_H, _P]),
+    "qs_norm": (_I, [_H, _DP]),
+}
+
+_lib = None
+
+
+def load():
+    """Load libqs.so (building it first if the toolkit is present and it is stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        try:
+            from . import build as _b
+            _b.build()
+        except Exception as e:  # noqa: BLE001
+            raise ImportError(f"libqs.so is missing and could not be built: {e}") from e
+    L = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+class QSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status):
+    if status != QS_OK:
+        raise QSError(status, load().qs_last_error().decode(errors="replace"))

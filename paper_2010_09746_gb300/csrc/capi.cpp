@@ -1,0 +1,613 @@
+// C ABI (include/qs.h): states, plans, device memory, streams, read-outs, profiling.
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "qs_internal.h"
+
+using namespace qs;
+
+namespace {
+
+thread_local std::string g_err;
+
+qs_status fail(qs_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+qs_status cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? QS_ENOMEM : QS_ECUDA;
+}
+#define CUDA_TRY(call, where)                  \
+  do {                                         \
+    cudaError_t _e = (call);                   \
+    if (_e != cudaSuccess) return cuda_fail(_e, where); \
+  } while (0)
+
+// ---- allocator -----------------------------------------------------------------------------
+void* (*g_alloc)(size_t, void*, void*) = nullptr;
+void (*g_free)(void*, size_t, void*, void*) = nullptr;
+void* g_alloc_ctx = nullptr;
+
+void* dev_alloc(size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 256;
+  if (g_alloc) return g_alloc(bytes, g_alloc_ctx, (void*)s);
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+void dev_free(void* p, size_t bytes, cudaStream_t s) {
+  if (!p) return;
+  if (g_free) {
+    g_free(p, bytes == 0 ? 256 : bytes, g_alloc_ctx, (void*)s);
+    return;
+  }
+  cudaFreeAsync(p, s);
+}
+
+Policy policy_for(qs_dtype dt, qs_arith a) {
+  if (dt == QS_C64) return POL_F32;
+  return a == QS_ARITH_F64 ? POL_F64 : POL_DF;
+}
+
+}  // namespace
+
+struct KernelRecord {
+  std::string name;
+  cudaEvent_t e0, e1;
+  double bytes;
+};
+
+struct qs_state {
+  int n = 0;
+  qs_dtype dtype = QS_C128;
+  qs_arith arith = QS_ARITH_AUTO;
+  int store_bytes = 16;
+  size_t bytes = 0;
+  void* psi = nullptr;
+  void* scratch = nullptr;        // permutation target, allocated on first use
+  std::vector<int> sigma;
+  cudaStream_t stream = nullptr;
+  int* status_dev = nullptr;      // device status word (bounded waits)
+  double* norm_buf = nullptr;     // norm partials + result
+  void* gate_pool = nullptr;      // matrix entries of qs_apply_* calls
+  size_t gate_pool_bytes = 0;
+  bool profiling = false;
+  std::vector<KernelRecord> pending;
+  std::vector<cudaEvent_t> free_events;
+  std::vector<qs_kernel_stat> stats;
+};
+
+struct qs_plan {
+  int n = 0;
+  int dtype = QS_C128;
+  Policy pol = POL_DF;
+  std::vector<int> sigma0;
+  CompileResult cr;
+  DevOp* ops_dev = nullptr;
+  size_t ops_bytes = 0;
+  void* pool_dev = nullptr;
+  size_t pool_bytes = 0;
+  bool uploaded = false;
+};
+
+namespace {
+
+cudaEvent_t get_event(qs_state* h) {
+  if (!h->free_events.empty()) {
+    cudaEvent_t e = h->free_events.back();
+    h->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// run `launch` on the state's stream, bracketed by events when profiling
+template <class F>
+cudaError_t timed(qs_state* h, const char* name, double bytes, F&& launch) {
+  if (!h->profiling) return launch();
+  KernelRecord r;
+  r.name = name;
+  r.bytes = bytes;
+  r.e0 = get_event(h);
+  r.e1 = get_event(h);
+  cudaEventRecord(r.e0, h->stream);
+  cudaError_t e = launch();
+  cudaEventRecord(r.e1, h->stream);
+  h->pending.push_back(r);
+  return e;
+}
+
+void collect_stats(qs_state* h) {
+  if (h->pending.empty()) return;
+  cudaStreamSynchronize(h->stream);
+  for (KernelRecord& r : h->pending) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, r.e0, r.e1);
+    qs_kernel_stat* st = nullptr;
+    for (auto& s : h->stats)
+      if (r.name == s.name) st = &s;
+    if (!st) {
+      h->stats.emplace_back();
+      st = &h->stats.back();
+      memset(st, 0, sizeof(*st));
+      strncpy(st->name, r.name.c_str(), sizeof(st->name) - 1);
+    }
+    st->launches++;
+    st->total_ms += ms;
+    st->bytes += r.bytes;
+    h->free_events.push_back(r.e0);
+    h->free_events.push_back(r.e1);
+  }
+  h->pending.clear();
+}
+
+qs_status check_status(qs_state* h) {
+  int st = 0;
+  CUDA_TRY(cudaMemcpyAsync(&st, h->status_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "status read");
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "stream sync");
+  if (st != 0) {
+    int zero = 0;
+    cudaMemcpyAsync(h->status_dev, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    cudaStreamSynchronize(h->stream);
+    return fail((qs_status)st, "a device-side wait timed out");
+  }
+  return QS_OK;
+}
+
+bool valid_perm(int n, const int* p) {
+  std::vector<char> seen(n, 0);
+  for (int q = 0; q < n; q++) {
+    if (p[q] < 0 || p[q] >= n || seen[p[q]]) return false;
+    seen[p[q]] = 1;
+  }
+  return true;
+}
+
+const char* step_name(const Step& s, Policy pol) {
+  if (s.kind == ST_PASS) return pol == POL_F32 ? "tile_pass_c64" : (pol == POL_DF ? "tile_pass_c128_df" : "tile_pass_c128_f64");
+  if (s.kind == ST_PERMUTE) return "permute";
+  return pol == POL_F32 ? "gate_c64" : (pol == POL_DF ? "gate_c128_df" : "gate_c128_f64");
+}
+
+// apply one lowered gate through the per-gate kernel
+qs_status apply_hgate(qs_state* h, const HGate& g) {
+  Pool pool;
+  std::vector<DevOp> ops;
+  LowerCtx ctx;
+  ctx.sigma = h->sigma.data();
+  ctx.tile = false;
+  if (!lower_gate(g, ctx, pool, ops)) return fail(QS_EINVAL, "gate could not be lowered");
+  const Policy pol = policy_for(h->dtype, h->arith);
+  std::vector<unsigned char> ser = pool.serialise(pol);
+  if (ser.size() > h->gate_pool_bytes) {
+    dev_free(h->gate_pool, h->gate_pool_bytes, h->stream);
+    h->gate_pool_bytes = std::max<size_t>(ser.size(), 64 * 1024);
+    h->gate_pool = dev_alloc(h->gate_pool_bytes, h->stream);
+    if (!h->gate_pool) return fail(QS_ENOMEM, "gate matrix buffer allocation failed");
+  }
+  if (!ser.empty())
+    CUDA_TRY(cudaMemcpyAsync(h->gate_pool, ser.data(), ser.size(), cudaMemcpyHostToDevice, h->stream), "matrix upload");
+  for (const DevOp& o : ops) {
+    Step s;
+    s.kind = ST_GATE;
+    CUDA_TRY(timed(h, step_name(s, pol), 0.0, [&] { return launch_gate(pol, h->psi, h->n, o, h->gate_pool, h->stream); }),
+             "gate launch");
+  }
+  return QS_OK;
+}
+
+qs_status ensure_scratch(qs_state* h) {
+  if (h->scratch) return QS_OK;
+  h->scratch = dev_alloc(h->bytes, h->stream);
+  if (!h->scratch) return fail(QS_ENOMEM, "permutation scratch allocation failed");
+  return QS_OK;
+}
+
+qs_status do_permute(qs_state* h, const std::vector<int>& src_of, const std::vector<int>& new_sigma, double bytes) {
+  qs_status st = ensure_scratch(h);
+  if (st != QS_OK) return st;
+  CUDA_TRY(timed(h, "permute", bytes,
+                 [&] { return launch_permute(h->scratch, h->psi, h->n, h->store_bytes, src_of.data(), h->stream); }),
+           "permute launch");
+  std::swap(h->psi, h->scratch);
+  h->sigma = new_sigma;
+  return QS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qs_last_error(void) { return g_err.c_str(); }
+const char* qs_version(void) { return "qs-gb300 0.1 (sm_103a)"; }
+
+qs_status qs_set_allocator(void* (*alloc_fn)(size_t, void*, void*), void (*free_fn)(void*, size_t, void*, void*),
+                           void* ctx) {
+  if ((alloc_fn == nullptr) != (free_fn == nullptr)) return fail(QS_EINVAL, "allocator needs both callbacks");
+  g_alloc = alloc_fn;
+  g_free = free_fn;
+  g_alloc_ctx = ctx;
+  return QS_OK;
+}
+
+qs_status qs_create(int n, qs_dtype dtype, qs_handle* out) {
+  if (!out) return fail(QS_EINVAL, "null output handle");
+  *out = nullptr;
+  if (n < 1 || n > kMaxQubits) return fail(QS_EINVAL, "n must be in [1, 36]");
+  if (dtype != QS_C64 && dtype != QS_C128) return fail(QS_EINVAL, "unknown dtype");
+  qs_state* h = new qs_state();
+  h->n = n;
+  h->dtype = dtype;
+  h->store_bytes = dtype == QS_C128 ? 16 : 8;
+  h->bytes = (size_t)h->store_bytes << n;
+  h->sigma.resize(n);
+  for (int q = 0; q < n; q++) h->sigma[q] = q;
+  h->psi = dev_alloc(h->bytes, h->stream);
+  h->status_dev = (int*)dev_alloc(256, h->stream);
+  h->norm_buf = (double*)dev_alloc(sizeof(double) * (norm_num_partials() + 1), h->stream);
+  if (!h->psi || !h->status_dev || !h->norm_buf) {
+    qs_destroy(h);
+    return fail(QS_ENOMEM, "state allocation failed (" + std::to_string(h->bytes) + " bytes)");
+  }
+  cudaMemsetAsync(h->status_dev, 0, 256, h->stream);
+  cudaError_t e = launch_init_zero(h->psi, n, h->store_bytes, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    qs_destroy(h);
+    return cuda_fail(e, "init");
+  }
+  *out = h;
+  return QS_OK;
+}
+
+qs_status qs_destroy(qs_handle h) {
+  if (!h) return QS_OK;
+  cudaStreamSynchronize(h->stream);
+  for (auto& r : h->pending) {
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  for (auto e : h->free_events) cudaEventDestroy(e);
+  dev_free(h->psi, h->bytes, h->stream);
+  dev_free(h->scratch, h->bytes, h->stream);
+  dev_free(h->status_dev, 256, h->stream);
+  dev_free(h->norm_buf, sizeof(double) * (norm_num_partials() + 1), h->stream);
+  dev_free(h->gate_pool, h->gate_pool_bytes, h->stream);
+  cudaStreamSynchronize(h->stream);
+  delete h;
+  return QS_OK;
+}
+
+qs_status qs_set_stream(qs_handle h, void* stream) {
+  if (!h) return fail(QS_EINVAL, "null handle");
+  // work already enqueued on the old stream completes before the new stream sees the state
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "stream switch");
+  h->stream = (cudaStream_t)stream;
+  return QS_OK;
+}
+
+qs_status qs_set_arith(qs_handle h, qs_arith a) {
+  if (!h) return fail(QS_EINVAL, "null handle");
+  if (a != QS_ARITH_AUTO && a != QS_ARITH_DF && a != QS_ARITH_F64) return fail(QS_EINVAL, "unknown arith");
+  h->arith = a;
+  return QS_OK;
+}
+
+qs_status qs_set_profiling(qs_handle h, int on) {
+  if (!h) return fail(QS_EINVAL, "null handle");
+  h->profiling = on != 0;
+  return QS_OK;
+}
+
+qs_status qs_get_kernel_stats(qs_handle h, qs_kernel_stat* out, int max, int* count) {
+  if (!h || !count) return fail(QS_EINVAL, "null argument");
+  collect_stats(h);
+  const int k = std::min<int>(max, (int)h->stats.size());
+  for (int i = 0; i < k; i++) out[i] = h->stats[i];
+  *count = (int)h->stats.size();
+  return QS_OK;
+}
+
+qs_status qs_reset_kernel_stats(qs_handle h) {
+  if (!h) return fail(QS_EINVAL, "null handle");
+  collect_stats(h);
+  h->stats.clear();
+  return QS_OK;
+}
+
+qs_status qs_reset(qs_handle h) {
+  if (!h) return fail(QS_EINVAL, "null handle");
+  for (int q = 0; q < h->n; q++) h->sigma[q] = q;
+  CUDA_TRY(timed(h, "init", (double)h->bytes, [&] { return launch_init_zero(h->psi, h->n, h->store_bytes, h->stream); }),
+           "init");
+  return QS_OK;
+}
+
+qs_status qs_get_info(qs_handle h, int* n, qs_dtype* dtype, void** device_ptr, size_t* bytes) {
+  if (!h) return fail(QS_EINVAL, "null handle");
+  if (n) *n = h->n;
+  if (dtype) *dtype = h->dtype;
+  if (device_ptr) *device_ptr = h->psi;
+  if (bytes) *bytes = h->bytes;
+  return QS_OK;
+}
+
+qs_status qs_sync(qs_handle h) {
+  if (!h) return fail(QS_EINVAL, "null handle");
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "sync");
+  return check_status(h);
+}
+
+static qs_status apply_op(qs_handle h, const qs_op& op, const double* mats, size_t nmats) {
+  HGate g;
+  std::string err;
+  if (!make_hgate(h->n, op, mats, nmats, &g, &err)) return fail(QS_EINVAL, err);
+  return apply_hgate(h, g);
+}
+
+qs_status qs_apply_1q(qs_handle h, const double* U, int q) {
+  if (!h || !U) return fail(QS_EINVAL, "null argument");
+  qs_op op{};
+  op.kind = QS_OP_U1;
+  op.nq = 1;
+  op.q[0] = q;
+  op.mat = 0;
+  return apply_op(h, op, U, 8);
+}
+
+qs_status qs_apply_2q(qs_handle h, const double* U, int q0, int q1) {
+  if (!h || !U) return fail(QS_EINVAL, "null argument");
+  qs_op op{};
+  op.kind = QS_OP_U2;
+  op.nq = 2;
+  op.q[0] = q0;
+  op.q[1] = q1;
+  op.mat = 0;
+  return apply_op(h, op, U, 32);
+}
+
+qs_status qs_apply_controlled(qs_handle h, const double* U, int c, int t) {
+  if (!h || !U) return fail(QS_EINVAL, "null argument");
+  qs_op op{};
+  op.kind = QS_OP_CU;
+  op.nq = 2;
+  op.q[0] = c;
+  op.q[1] = t;
+  op.mat = 0;
+  return apply_op(h, op, U, 8);
+}
+
+qs_status qs_apply_dense(qs_handle h, const double* U, int k, const int* qubits) {
+  if (!h || !U || !qubits) return fail(QS_EINVAL, "null argument");
+  if (k < 1 || k > kMaxDenseK) return fail(QS_EINVAL, "k must be in [1, 6]");
+  qs_op op{};
+  op.kind = QS_OP_UK;
+  op.nq = k;
+  for (int t = 0; t < k; t++) op.q[t] = qubits[t];
+  op.mat = 0;
+  return apply_op(h, op, U, (size_t)2 << (2 * k));
+}
+
+qs_status qs_permute(qs_handle h, const int* perm) {
+  if (!h || !perm) return fail(QS_EINVAL, "null argument");
+  if (!valid_perm(h->n, perm)) return fail(QS_EINVAL, "perm is not a permutation of 0..n-1");
+  std::vector<int> ns(perm, perm + h->n);
+  if (ns == h->sigma) return QS_OK;
+  std::vector<int> src_of(h->n);
+  for (int q = 0; q < h->n; q++) src_of[ns[q]] = h->sigma[q];
+  return do_permute(h, src_of, ns, 2.0 * (double)h->bytes);
+}
+
+qs_status qs_get_permutation(qs_handle h, int* perm_out) {
+  if (!h || !perm_out) return fail(QS_EINVAL, "null argument");
+  for (int q = 0; q < h->n; q++) perm_out[q] = h->sigma[q];
+  return QS_OK;
+}
+
+qs_status qs_compile(int n, const qs_op* ops, size_t nops, const double* mats, size_t nmats, const int* sigma0,
+                     const qs_compile_opts* opts, qs_plan_t* out) {
+  if (!out) return fail(QS_EINVAL, "null output plan");
+  *out = nullptr;
+  if (n < 1 || n > kMaxQubits) return fail(QS_EINVAL, "n must be in [1, 36]");
+  if (nops > 0 && !ops) return fail(QS_EINVAL, "null ops");
+  qs_compile_opts o{};
+  o.mode = QS_MODE_TILE;
+  o.dtype = QS_C128;
+  if (opts) o = *opts;
+  if (o.dtype != QS_C64 && o.dtype != QS_C128) return fail(QS_EINVAL, "unknown dtype");
+  if (o.mode < QS_MODE_PERGATE || o.mode > QS_MODE_TILE) return fail(QS_EINVAL, "unknown mode");
+  if (o.flags != 0) return fail(QS_EINVAL, "flags must be 0");
+  if (o.tile_bits == 0) o.tile_bits = default_tile_bits(o.dtype);
+  if (o.low_bits == 0) o.low_bits = default_low_bits(o.dtype);
+  if (o.tile_bits < 1 || (o.mode != QS_MODE_PAPER && o.tile_bits > kMaxTileBits))
+    return fail(QS_EINVAL, "tile_bits must be in [1, 14] (QS_MODE_PAPER: [1, n])");
+  if (o.tile_bits > n) o.tile_bits = n;
+  if (o.low_bits > o.tile_bits) o.low_bits = o.tile_bits;
+  const int min_low = (o.dtype == QS_C64) ? 1 : 0;   // 16-byte bulk copies
+  if (o.low_bits < min_low) o.low_bits = min_low;
+  if (o.low_bits > o.tile_bits) return fail(QS_EINVAL, "state too small for a tile pass");
+  std::vector<int> s0(n);
+  if (sigma0) {
+    if (!valid_perm(n, sigma0)) return fail(QS_EINVAL, "sigma0 is not a permutation");
+    s0.assign(sigma0, sigma0 + n);
+  } else {
+    for (int q = 0; q < n; q++) s0[q] = q;
+  }
+  std::vector<HGate> gates(nops);
+  std::string err;
+  for (size_t i = 0; i < nops; i++)
+    if (!make_hgate(n, ops[i], mats, nmats, &gates[i], &err)) return fail(QS_EINVAL, "op " + std::to_string(i) + ": " + err);
+  qs_plan* p = new qs_plan();
+  p->n = n;
+  p->dtype = o.dtype;
+  p->pol = policy_for((qs_dtype)o.dtype, (qs_arith)o.arith);
+  p->sigma0 = s0;
+  if (!compile_circuit(n, gates, s0, o, &p->cr, &err)) {
+    delete p;
+    return fail(QS_EINVAL, err);
+  }
+  // device copies are made on first execution, so compiling needs no GPU
+  *out = p;
+  return QS_OK;
+}
+
+qs_status qs_plan_destroy(qs_plan_t p) {
+  if (!p) return QS_OK;
+  if (p->uploaded) {
+    cudaDeviceSynchronize();
+    dev_free(p->ops_dev, p->ops_bytes, nullptr);
+    dev_free(p->pool_dev, p->pool_bytes, nullptr);
+    cudaDeviceSynchronize();
+  }
+  delete p;
+  return QS_OK;
+}
+
+qs_status qs_plan_get_stats(qs_plan_t p, qs_plan_stats* out) {
+  if (!p || !out) return fail(QS_EINVAL, "null argument");
+  *out = p->cr.stats;
+  return QS_OK;
+}
+
+qs_status qs_plan_final_permutation(qs_plan_t p, int* perm_out) {
+  if (!p || !perm_out) return fail(QS_EINVAL, "null argument");
+  for (int q = 0; q < p->n; q++) perm_out[q] = p->cr.sigma_final[q];
+  return QS_OK;
+}
+
+qs_status qs_plan_get_trace(qs_plan_t p, int32_t* kinds, int32_t* values, size_t max, size_t* count) {
+  if (!p || !count) return fail(QS_EINVAL, "null argument");
+  const size_t k = std::min(max, p->cr.trace.size());
+  for (size_t i = 0; i < k; i++) {
+    if (kinds) kinds[i] = p->cr.trace[i].first;
+    if (values) values[i] = p->cr.trace[i].second;
+  }
+  *count = p->cr.trace.size();
+  return QS_OK;
+}
+
+static qs_status plan_upload(qs_plan* p) {
+  if (p->uploaded) return QS_OK;
+  p->ops_bytes = p->cr.tile_ops.size() * sizeof(DevOp);
+  std::vector<unsigned char> ser = p->cr.pool.serialise(p->pol);
+  p->pool_bytes = ser.size();
+  if (p->ops_bytes) p->ops_dev = (DevOp*)dev_alloc(p->ops_bytes, nullptr);
+  if (p->pool_bytes) p->pool_dev = dev_alloc(p->pool_bytes, nullptr);
+  if ((p->ops_bytes && !p->ops_dev) || (p->pool_bytes && !p->pool_dev)) return fail(QS_ENOMEM, "plan upload allocation failed");
+  cudaError_t e = cudaSuccess;
+  if (p->ops_bytes) e = cudaMemcpy(p->ops_dev, p->cr.tile_ops.data(), p->ops_bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && p->pool_bytes) e = cudaMemcpy(p->pool_dev, ser.data(), p->pool_bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "plan upload");
+  p->uploaded = true;
+  return QS_OK;
+}
+
+qs_status qs_execute(qs_handle h, qs_plan_t p) {
+  if (!h || !p) return fail(QS_EINVAL, "null argument");
+  {
+    qs_status ust = plan_upload(p);
+    if (ust != QS_OK) return ust;
+  }
+  if (h->n != p->n) return fail(QS_EINVAL, "plan and state have different n");
+  if ((int)h->dtype != p->dtype) return fail(QS_EINVAL, "plan and state have different dtype");
+  if (h->sigma != p->sigma0) return fail(QS_EINVAL, "state permutation differs from the plan's start permutation");
+  for (const Step& s : p->cr.steps) {
+    const char* name = step_name(s, p->pol);
+    if (s.kind == ST_PASS) {
+      CUDA_TRY(timed(h, name, s.bytes,
+                     [&] { return launch_tile_pass(p->pol, h->psi, s.pass, p->ops_dev, p->pool_dev, h->status_dev, h->stream); }),
+               "tile pass launch");
+    } else if (s.kind == ST_GATE) {
+      CUDA_TRY(timed(h, name, s.bytes, [&] { return launch_gate(p->pol, h->psi, h->n, s.op, p->pool_dev, h->stream); }),
+               "gate launch");
+    } else {
+      qs_status st = do_permute(h, s.src_of, s.perm, s.bytes);
+      if (st != QS_OK) return st;
+    }
+  }
+  h->sigma = p->cr.sigma_final;
+  return QS_OK;
+}
+
+qs_status qs_run(qs_handle h, const qs_op* ops, size_t nops, const double* mats, size_t nmats,
+                 const qs_compile_opts* opts) {
+  if (!h) return fail(QS_EINVAL, "null handle");
+  qs_compile_opts o{};
+  o.mode = QS_MODE_TILE;
+  if (opts) o = *opts;
+  o.dtype = h->dtype;
+  if (!opts) o.arith = h->arith;
+  qs_plan_t p = nullptr;
+  qs_status st = qs_compile(h->n, ops, nops, mats, nmats, h->sigma.data(), &o, &p);
+  if (st != QS_OK) return st;
+  st = qs_execute(h, p);
+  // the plan's buffers are freed after the stream has consumed them
+  cudaStreamSynchronize(h->stream);
+  qs_plan_destroy(p);
+  return st;
+}
+
+qs_status qs_probabilities(qs_handle h, double* out, int order) {
+  if (!h || !out) return fail(QS_EINVAL, "null argument");
+  if (order != QS_ORDER_LOGICAL && order != QS_ORDER_STORAGE) return fail(QS_EINVAL, "unknown order");
+  const size_t N = (size_t)1 << h->n;
+  double* d = (double*)dev_alloc(N * sizeof(double), h->stream);
+  if (!d) return fail(QS_ENOMEM, "probability buffer allocation failed");
+  cudaError_t e = launch_probabilities(h->psi, h->n, h->dtype == QS_C128, d, h->sigma.data(),
+                                       order == QS_ORDER_LOGICAL, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, N * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dev_free(d, N * sizeof(double), h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "probabilities");
+  return check_status(h);
+}
+
+qs_status qs_get_amplitudes(qs_handle h, void* out, uint64_t first, uint64_t count, int order) {
+  if (!h || (!out && count)) return fail(QS_EINVAL, "null argument");
+  if (order != QS_ORDER_LOGICAL && order != QS_ORDER_STORAGE) return fail(QS_EINVAL, "unknown order");
+  const uint64_t N = 1ull << h->n;
+  if (first > N || count > N - first) return fail(QS_EINVAL, "amplitude range out of bounds");
+  if (count == 0) return QS_OK;
+  const size_t bytes = (size_t)count * h->store_bytes;
+  void* d = dev_alloc(bytes, h->stream);
+  if (!d) return fail(QS_ENOMEM, "amplitude buffer allocation failed");
+  cudaError_t e = launch_gather_amplitudes(h->psi, h->n, h->store_bytes, d, first, count, h->sigma.data(),
+                                           order == QS_ORDER_LOGICAL, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  dev_free(d, bytes, h->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "get amplitudes");
+  return check_status(h);
+}
+
+qs_status qs_set_amplitudes(qs_handle h, const void* in) {
+  if (!h || !in) return fail(QS_EINVAL, "null argument");
+  CUDA_TRY(cudaMemcpyAsync(h->psi, in, h->bytes, cudaMemcpyHostToDevice, h->stream), "set amplitudes");
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "set amplitudes sync");
+  return QS_OK;
+}
+
+qs_status qs_norm(qs_handle h, double* out) {
+  if (!h || !out) return fail(QS_EINVAL, "null argument");
+  const int np = norm_num_partials();
+  CUDA_TRY(timed(h, "norm", (double)h->bytes,
+                 [&] { return launch_norm_partials(h->psi, h->n, h->dtype == QS_C128, h->norm_buf, np, h->stream); }),
+           "norm partials");
+  CUDA_TRY(launch_norm_final(h->norm_buf, np, h->norm_buf + np, h->stream), "norm final");
+  CUDA_TRY(cudaMemcpyAsync(out, h->norm_buf + np, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "norm read");
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "norm sync");
+  return check_status(h);
+}
+
+}  // extern "C"

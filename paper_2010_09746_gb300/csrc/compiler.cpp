@@ -1,0 +1,429 @@
+// Circuit compiler: the dependency DAG, Algorithm 1 of the paper (Sec. 3) run with the
+// tile bits as the local qubits, and the tile-pass scheduler that generalises it to
+// multi-qubit reorderings folded into the pass addressing.
+//
+// Locality (Sec. 2, Appendix C): a gate needs "communication" -- here: cannot run inside a
+// tile pass -- iff one of the qubits on which it acts non-diagonally sits outside the tile.
+// Controls and diagonal factors on any qubit are constants of a tile block.
+#include <chrono>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+
+#include "qs_internal.h"
+
+namespace qs {
+
+int default_tile_bits(int dtype) { return dtype == QS_C128 ? 12 : 13; }
+int default_low_bits(int dtype) { return dtype == QS_C128 ? 3 : 4; }
+
+// Gate j depends on an earlier gate i iff they share a qubit on which their action
+// classes differ (classes Z and X each commute with themselves, N with nothing).  Per
+// qubit, consecutive gates of one commuting class form a group; a gate's immediate
+// predecessors on that qubit are the members of the latest group it does not commute with.
+std::vector<std::vector<int>> build_dag(const std::vector<HGate>& gates) {
+  const int G = (int)gates.size();
+  std::vector<std::vector<int>> preds(G);
+  struct QState {
+    int cls = -1;
+    std::vector<int> cur, prev;
+  };
+  std::vector<QState> qs(kMaxQubits + 1);
+  for (int j = 0; j < G; j++) {
+    const HGate& g = gates[j];
+    for (int t = 0; t < g.nq; t++) {
+      QState& s = qs[g.q[t]];
+      const int c = g.cls[t];
+      if (s.cls >= 0 && c == s.cls && c != CLS_N) {
+        preds[j].insert(preds[j].end(), s.prev.begin(), s.prev.end());
+        s.cur.push_back(j);
+      } else {
+        preds[j].insert(preds[j].end(), s.cur.begin(), s.cur.end());
+        s.prev.swap(s.cur);
+        s.cur.assign(1, j);
+        s.cls = c;
+      }
+    }
+    std::sort(preds[j].begin(), preds[j].end());
+    preds[j].erase(std::unique(preds[j].begin(), preds[j].end()), preds[j].end());
+  }
+  return preds;
+}
+
+namespace {
+
+// Qubits a gate needs inside the tile: those on which it acts non-diagonally; a general
+// 2- or k-qubit matrix (applied as a dense block) needs all of its qubits.
+bool needs_qubit(const HGate& g, int t) {
+  if (g.nq >= 2 && (g.kind == QS_OP_U2 || g.kind == QS_OP_UK)) return true;
+  return g.cls[t] != CLS_Z;
+}
+// storage-bit mask of the qubits the gate needs inside the tile
+uint64_t nd_mask(const HGate& g, const std::vector<int>& sigma) {
+  uint64_t m = 0;
+  for (int t = 0; t < g.nq; t++)
+    if (needs_qubit(g, t)) m |= 1ull << sigma[g.q[t]];
+  return m;
+}
+
+struct Sched {
+  const std::vector<HGate>& gates;
+  std::vector<std::vector<int>> preds, succs;
+  std::vector<int> npred;
+  std::vector<char> done;
+  std::vector<int> rem;      // remaining gate indices in program order
+  int remaining;
+  explicit Sched(const std::vector<HGate>& g) : gates(g) {
+    const int G = (int)g.size();
+    preds = build_dag(g);
+    succs.assign(G, {});
+    npred.assign(G, 0);
+    for (int j = 0; j < G; j++) {
+      npred[j] = (int)preds[j].size();
+      for (int i : preds[j]) succs[i].push_back(j);
+    }
+    done.assign(G, 0);
+    rem.resize(G);
+    std::iota(rem.begin(), rem.end(), 0);
+    remaining = G;
+  }
+  void mark(int v) {
+    done[v] = 1;
+    remaining--;
+    for (int s : succs[v]) npred[s]--;
+  }
+  void compact() {
+    size_t w = 0;
+    for (size_t r = 0; r < rem.size(); r++)
+      if (!done[rem[r]]) rem[w++] = rem[r];
+    rem.resize(w);
+  }
+  // number of gates one program-order sweep would schedule if every gate whose
+  // non-diagonal storage bits lie in `local` (a storage-bit mask) were runnable;
+  // `tmp` is scratch of size G.
+  int closure(uint64_t local, const std::vector<uint64_t>& ndm, std::vector<char>& tmp, int cap = 1 << 30) const {
+    int cnt = 0;
+    for (int v : rem) {
+      bool ok = (ndm[v] & ~local) == 0;
+      if (ok)
+        for (int p : preds[v])
+          if (!done[p] && !tmp[p]) {
+            ok = false;
+            break;
+          }
+      tmp[v] = ok;
+      if (ok && ++cnt >= cap) break;
+    }
+    for (int v : rem) tmp[v] = 0;
+    return cnt;
+  }
+};
+
+double gate_bytes(const HGate& g, int n, int store_bytes) {
+  // bytes read + written by the per-gate kernel of this gate
+  const double S = (double)store_bytes * (double)(1ull << n);
+  int fixed = 0;   // bits fixed by controls / phase predicates
+  bool diag = true;
+  for (int t = 0; t < g.nq; t++)
+    if (g.cls[t] != CLS_Z) diag = false;
+  if (g.kind == QS_OP_CNOT || g.kind == QS_OP_CU || g.kind == QS_OP_CP || g.kind == QS_OP_CZ) fixed = 1;
+  if (g.kind == QS_OP_CZ || g.kind == QS_OP_CP) fixed = 2;
+  if (g.nq == 1 && diag && g.U[0] == cd(1, 0)) fixed = 1;   // phase on |1>
+  if (g.kind == QS_OP_SWAP) fixed = 1;                        // only |01>,|10> move
+  return 2.0 * S / (double)(1ull << fixed);
+}
+
+void fill_tile_ctx(LowerCtx* ctx, const int* tpos, int L) {
+  for (int b = 0; b < 64; b++) ctx->tile_index[b] = -1;
+  for (int k = 0; k < L; k++) ctx->tile_index[tpos[k]] = k;
+}
+
+bool emit_pass(int n, int L, int c, const std::vector<int>& tbits_sorted, const std::vector<int>& gate_ids,
+               const std::vector<HGate>& gates, const std::vector<int>& sigma, CompileResult* out,
+               std::string* err) {
+  Step st;
+  st.kind = ST_PASS;
+  memset(&st.pass, 0, sizeof(st.pass));
+  st.pass.L = L;
+  st.pass.c = c;
+  st.pass.n = n;
+  for (int k = 0; k < L; k++) st.pass.tpos[k] = tbits_sorted[k];
+  int nn = 0;
+  std::vector<char> in(n, 0);
+  for (int k = 0; k < L; k++) in[tbits_sorted[k]] = 1;
+  for (int b = 0; b < n; b++)
+    if (!in[b]) st.pass.npos[nn++] = b;
+  LowerCtx ctx;
+  ctx.sigma = sigma.data();
+  ctx.tile = true;
+  fill_tile_ctx(&ctx, st.pass.tpos, L);
+  st.pass.op0 = (int)out->tile_ops.size();
+  for (int v : gate_ids) {
+    if (!lower_gate(gates[v], ctx, out->pool, out->tile_ops)) {
+      *err = "internal: gate not lowerable in its tile pass";
+      return false;
+    }
+  }
+  st.pass.nops = (int)out->tile_ops.size() - st.pass.op0;
+  if (st.pass.nops == 0) return true;   // identity gates only
+  const int store_bytes = out->store_bytes;
+  st.bytes = 2.0 * (double)store_bytes * (double)(1ull << n);
+  out->steps.push_back(std::move(st));
+  out->stats.n_passes++;
+  return true;
+}
+
+bool emit_gate(int n, const HGate& g, const std::vector<int>& sigma, int store_bytes, CompileResult* out,
+               std::string* err) {
+  LowerCtx ctx;
+  ctx.sigma = sigma.data();
+  ctx.tile = false;
+  std::vector<DevOp> ops;
+  if (!lower_gate(g, ctx, out->pool, ops)) {
+    *err = "internal: gate not lowerable";
+    return false;
+  }
+  for (const DevOp& o : ops) {
+    Step st;
+    st.kind = ST_GATE;
+    st.op = o;
+    st.bytes = gate_bytes(g, n, store_bytes);
+    out->steps.push_back(std::move(st));
+  }
+  return true;
+}
+
+bool emit_permute(int n, const std::vector<int>& sigma, const std::vector<int>& sigma_new, int store_bytes,
+                  CompileResult* out) {
+  Step st;
+  st.kind = ST_PERMUTE;
+  st.perm = sigma_new;
+  st.src_of.assign(n, 0);
+  for (int q = 0; q < n; q++) st.src_of[sigma_new[q]] = sigma[q];
+  st.bytes = 2.0 * (double)store_bytes * (double)(1ull << n);
+  out->steps.push_back(std::move(st));
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// QS_MODE_PAPER: Algorithm 1 with m = L local storage positions.
+// Readings (as in the tests' reference): the sweep visits remaining gates in program order
+// and a removed gate unblocks its successors later in the same sweep; candidates
+// sigma o (l g) run over local qubits l then global qubits g in ascending qubit order; the
+// score is the number of gates the next sweep would schedule under the candidate
+// ("closure", default) or the number of frontier gates it makes local with the count of
+// all remaining gates it makes local as tie-break ("frontier"); the first best candidate
+// wins; with no positive score the first frontier gate runs non-locally.
+bool compile_paper(int n, const std::vector<HGate>& gates, std::vector<int> sigma, const qs_compile_opts& o,
+                   int store_bytes, CompileResult* out, std::string* err) {
+  const int L = o.tile_bits;
+  const int m = L;
+  const int G = (int)gates.size();
+  Sched S(gates);
+  std::vector<char> tmp(G, 0);
+  std::vector<int> run;   // consecutive local gates -> one tile pass over storage bits [0, L)
+  std::vector<int> tpos(L);
+  std::iota(tpos.begin(), tpos.end(), 0);
+  auto flush = [&]() -> bool {
+    if (run.empty()) return true;
+    bool ok = true;
+    if (L <= kMaxTileBits) {
+      ok = emit_pass(n, L, std::min(o.low_bits, L), tpos, run, gates, sigma, out, err);
+    } else {   // more local qubits than a tile holds: the run executes gate by gate
+      for (int v : run) {
+        ok = ok && emit_gate(n, gates[v], sigma, store_bytes, out, err);
+        out->stats.n_pergate++;
+      }
+    }
+    run.clear();
+    return ok;
+  };
+  // logical-qubit masks of the non-diagonal qubits of every gate
+  std::vector<uint64_t> ndq(G, 0);
+  for (int v = 0; v < G; v++)
+    for (int t = 0; t < gates[v].nq; t++)
+      if (needs_qubit(gates[v], t)) ndq[v] |= 1ull << gates[v].q[t];
+  auto local_mask = [&](const std::vector<int>& sg) {
+    uint64_t lm = 0;
+    for (int q = 0; q < n; q++)
+      if (sg[q] < m) lm |= 1ull << q;
+    return lm;
+  };
+  while (S.remaining) {
+    // sweep (lines 5-10)
+    const uint64_t lm = local_mask(sigma);
+    for (int v : S.rem) {
+      if (S.done[v] || S.npred[v] != 0 || (ndq[v] & ~lm)) continue;
+      S.mark(v);
+      out->trace.push_back({0, v});
+      run.push_back(v);
+      if (o.max_ops > 0 && (int)run.size() >= o.max_ops && !flush()) return false;
+    }
+    S.compact();
+    if (!S.remaining) break;
+    // candidate transpositions (lines 11-22)
+    std::vector<int> loc, glo;
+    for (int q = 0; q < n; q++) (sigma[q] < m ? loc : glo).push_back(q);
+    int best_l = -1, best_g = -1;
+    long best0 = 0, best1 = -1;
+    bool have = false;
+    for (int l : loc)
+      for (int g : glo) {
+        const uint64_t lm2 = (lm & ~(1ull << l)) | (1ull << g);
+        long f, a = 0;
+        if (o.scoring == 0) {
+          f = S.closure(lm2, ndq, tmp);
+        } else {
+          f = 0;
+          for (int v : S.rem) {
+            if (ndq[v] & ~lm2) continue;
+            a++;
+            if (S.npred[v] == 0) f++;
+          }
+        }
+        if (!have || f > best0 || (o.scoring != 0 && f == best0 && a > best1)) {
+          have = true;
+          best0 = f;
+          best1 = a;
+          best_l = l;
+          best_g = g;
+        }
+      }
+    // lines 23-30
+    if (have && best0 > 0) {
+      if (!flush()) return false;
+      std::vector<int> sg = sigma;
+      std::swap(sg[best_l], sg[best_g]);
+      emit_permute(n, sigma, sg, store_bytes, out);
+      out->stats.n_permutes++;
+      out->trace.push_back({2, best_l * 64 + best_g});
+      sigma = sg;
+    } else {
+      int v = -1;
+      for (int u : S.rem)
+        if (S.npred[u] == 0) {
+          v = u;
+          break;
+        }
+      if (v < 0) {
+        *err = "internal: no frontier gate";
+        return false;
+      }
+      if (!flush()) return false;
+      S.mark(v);
+      S.compact();
+      out->trace.push_back({1, v});
+      if (!emit_gate(n, gates[v], sigma, store_bytes, out, err)) return false;
+      out->stats.n_pergate++;
+      out->stats.n_comm_gates++;
+    }
+  }
+  if (!flush()) return false;
+  out->sigma_final = sigma;
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// QS_MODE_TILE: every pass picks its own set of L storage bits (the c lowest always in),
+// greedily: starting from the c low bits, add the bit whose inclusion lets one program-order
+// sweep schedule the most gates (ties: the bit most wanted by frontier gates, then the
+// lowest bit).  The pass then runs that sweep.
+bool compile_tile(int n, const std::vector<HGate>& gates, const std::vector<int>& sigma, const qs_compile_opts& o,
+                  int store_bytes, CompileResult* out, std::string* err) {
+  const int L = std::min(o.tile_bits, n);
+  const int c = std::min(o.low_bits, L);
+  const int G = (int)gates.size();
+  Sched S(gates);
+  std::vector<uint64_t> ndm(G);
+  for (int v = 0; v < G; v++) ndm[v] = nd_mask(gates[v], sigma);
+  std::vector<char> tmp(G, 0);
+  const uint64_t low = (c >= 64) ? ~0ull : ((1ull << c) - 1);
+  for (int v = 0; v < G; v++)
+    if (__builtin_popcountll(ndm[v] | low) > L) {
+      *err = "gate " + std::to_string(v) + " needs more qubits than a tile holds";
+      return false;
+    }
+  while (S.remaining) {
+    uint64_t T = low;
+    int nt = c;
+    // demand: how many frontier gates need each bit
+    std::vector<int> demand(n, 0);
+    for (int v : S.rem)
+      if (S.npred[v] == 0)
+        for (int b = 0; b < n; b++)
+          if ((ndm[v] >> b) & 1) demand[b]++;
+    while (nt < L) {
+      int best_b = -1, best_s = -1, best_d = -1;
+      for (int b = 0; b < n; b++) {
+        if ((T >> b) & 1) continue;
+        const int s = S.closure(T | (1ull << b), ndm, tmp);
+        if (s > best_s || (s == best_s && demand[b] > best_d)) {
+          best_s = s;
+          best_d = demand[b];
+          best_b = b;
+        }
+      }
+      if (best_b < 0) break;
+      T |= 1ull << best_b;
+      nt++;
+    }
+    // the sweep of this pass
+    std::vector<int> ids;
+    for (int v : S.rem) {
+      if (S.done[v] || S.npred[v] != 0 || (ndm[v] & ~T)) continue;
+      S.mark(v);
+      ids.push_back(v);
+      if (o.max_ops > 0 && (int)ids.size() >= o.max_ops) break;
+    }
+    S.compact();
+    if (ids.empty()) {
+      *err = "internal: tile pass scheduled no gate (a gate needs more than L - low_bits tile bits)";
+      return false;
+    }
+    std::vector<int> tb;
+    for (int b = 0; b < n; b++)
+      if ((T >> b) & 1) tb.push_back(b);
+    out->trace.push_back({3, (int)(T & 0x7FFFFFFFull)});
+    out->trace.push_back({4, (int)(T >> 31)});
+    for (int v : ids) out->trace.push_back({0, v});
+    if (!emit_pass(n, (int)tb.size(), c, tb, ids, gates, sigma, out, err)) return false;
+  }
+  out->sigma_final = sigma;
+  return true;
+}
+
+}  // namespace
+
+bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<int>& sigma0,
+                     const qs_compile_opts& o, CompileResult* out, std::string* err) {
+  auto t0 = std::chrono::steady_clock::now();
+  const int store_bytes = (o.dtype == QS_C128) ? 16 : 8;
+  out->store_bytes = store_bytes;
+  out->stats = qs_plan_stats{};
+  out->stats.n_gates = (int64_t)gates.size();
+  bool ok = true;
+  if (o.mode == QS_MODE_PERGATE) {
+    for (const HGate& g : gates) {
+      if (!emit_gate(n, g, sigma0, store_bytes, out, err)) return false;
+      out->stats.n_pergate++;
+    }
+    out->sigma_final = sigma0;
+  } else if (o.mode == QS_MODE_PAPER) {
+    ok = compile_paper(n, gates, sigma0, o, store_bytes, out, err);
+  } else if (o.mode == QS_MODE_TILE) {
+    ok = compile_tile(n, gates, sigma0, o, store_bytes, out, err);
+  } else {
+    *err = "unknown compile mode";
+    return false;
+  }
+  if (!ok) return false;
+  double bytes = 0;
+  for (const Step& s : out->steps) bytes += s.bytes;
+  out->stats.hbm_bytes = bytes;
+  out->stats.compile_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return true;
+}
+
+}  // namespace qs

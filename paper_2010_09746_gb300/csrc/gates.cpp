@@ -1,0 +1,287 @@
+// Host gate model: ABI op -> matrix + per-qubit action classes, lowering to device ops,
+// and the policy-specific serialisation of matrix pools.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "qs_internal.h"
+
+namespace qs {
+
+namespace {
+
+const double kInvSqrt2 = 0.70710678118654752440;
+
+bool one_qubit(int kind, double t, cd m[4]) {
+  const cd I(0, 1);
+  switch (kind) {
+    case QS_OP_H: m[0] = kInvSqrt2; m[1] = kInvSqrt2; m[2] = kInvSqrt2; m[3] = -kInvSqrt2; return true;
+    case QS_OP_X: m[0] = 0; m[1] = 1; m[2] = 1; m[3] = 0; return true;
+    case QS_OP_Y: m[0] = 0; m[1] = -I; m[2] = I; m[3] = 0; return true;
+    case QS_OP_Z: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = -1; return true;
+    case QS_OP_S: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = I; return true;
+    case QS_OP_T: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = cd(kInvSqrt2, kInvSqrt2); return true;
+    case QS_OP_RZ: m[0] = cd(cos(0.5 * t), -sin(0.5 * t)); m[1] = 0; m[2] = 0; m[3] = cd(cos(0.5 * t), sin(0.5 * t)); return true;
+    case QS_OP_RX: m[0] = cos(0.5 * t); m[1] = cd(0, -sin(0.5 * t)); m[2] = cd(0, -sin(0.5 * t)); m[3] = cos(0.5 * t); return true;
+    case QS_OP_RY: m[0] = cos(0.5 * t); m[1] = -sin(0.5 * t); m[2] = sin(0.5 * t); m[3] = cos(0.5 * t); return true;
+    case QS_OP_P: m[0] = 1; m[1] = 0; m[2] = 0; m[3] = cd(cos(t), sin(t)); return true;
+    default: return false;
+  }
+}
+
+// classes by exact commutation with Z / X on each qubit of a 2^k x 2^k matrix
+void classify(HGate* g) {
+  const int D = 1 << g->nq;
+  for (int t = 0; t < g->nq; t++) {
+    const int bq = 1 << t;
+    bool diag = true, xtype = true;
+    for (int r = 0; r < D && (diag || xtype); r++)
+      for (int c = 0; c < D; c++) {
+        const cd u = g->U[(size_t)r * D + c];
+        if (((r ^ c) & bq) && u != cd(0, 0)) diag = false;
+        if (u != g->U[(size_t)(r ^ bq) * D + (c ^ bq)]) xtype = false;
+      }
+    g->cls[t] = diag ? CLS_Z : (xtype ? CLS_X : CLS_N);
+  }
+}
+
+}  // namespace
+
+bool make_hgate(int n, const qs_op& op, const double* mats, size_t nmats, HGate* g, std::string* err) {
+  g->kind = op.kind;
+  g->param = op.param;
+  int nq;
+  switch (op.kind) {
+    case QS_OP_U1: case QS_OP_H: case QS_OP_X: case QS_OP_Y: case QS_OP_Z: case QS_OP_S: case QS_OP_T:
+    case QS_OP_RZ: case QS_OP_RX: case QS_OP_RY: case QS_OP_P:
+      nq = 1; break;
+    case QS_OP_CNOT: case QS_OP_CZ: case QS_OP_CP: case QS_OP_CU: case QS_OP_SWAP: case QS_OP_U2:
+      nq = 2; break;
+    case QS_OP_UK:
+      nq = op.nq;
+      if (nq < 1 || nq > kMaxDenseK) { *err = "UK gate needs 1 <= nq <= 6"; return false; }
+      break;
+    default:
+      *err = "unknown gate kind " + std::to_string(op.kind);
+      return false;
+  }
+  if (op.nq != nq) { *err = "gate kind " + std::to_string(op.kind) + " needs nq = " + std::to_string(nq); return false; }
+  g->nq = nq;
+  for (int t = 0; t < nq; t++) {
+    if (op.q[t] < 0 || op.q[t] >= n) { *err = "qubit index out of range"; return false; }
+    for (int s = 0; s < t; s++)
+      if (op.q[s] == op.q[t]) { *err = "duplicate qubit in gate"; return false; }
+    g->q[t] = op.q[t];
+  }
+  const int D = 1 << nq;
+  g->U.assign((size_t)D * D, cd(0, 0));
+  auto need_mat = [&](size_t count) -> const double* {
+    if (op.mat < 0 || mats == nullptr || (size_t)op.mat + count > nmats) return nullptr;
+    return mats + op.mat;
+  };
+  cd m[4];
+  if (nq == 1 && op.kind != QS_OP_UK) {
+    if (op.kind == QS_OP_U1) {
+      const double* p = need_mat(8);
+      if (!p) { *err = "U1 gate matrix offset out of range"; return false; }
+      for (int k = 0; k < 4; k++) m[k] = cd(p[2 * k], p[2 * k + 1]);
+    } else {
+      one_qubit(op.kind, op.param, m);
+    }
+    for (int k = 0; k < 4; k++) g->U[k] = m[k];
+  } else if (op.kind == QS_OP_CNOT || op.kind == QS_OP_CZ || op.kind == QS_OP_CP || op.kind == QS_OP_CU) {
+    if (op.kind == QS_OP_CU) {
+      const double* p = need_mat(8);
+      if (!p) { *err = "CU gate matrix offset out of range"; return false; }
+      for (int k = 0; k < 4; k++) m[k] = cd(p[2 * k], p[2 * k + 1]);
+    } else {
+      one_qubit(op.kind == QS_OP_CNOT ? QS_OP_X : (op.kind == QS_OP_CZ ? QS_OP_Z : QS_OP_P), op.param, m);
+    }
+    // r = b(control) + 2 b(target); control = 1 rows/cols are 1 and 3
+    g->U[0 * 4 + 0] = 1;
+    g->U[2 * 4 + 2] = 1;
+    g->U[1 * 4 + 1] = m[0];
+    g->U[1 * 4 + 3] = m[1];
+    g->U[3 * 4 + 1] = m[2];
+    g->U[3 * 4 + 3] = m[3];
+  } else if (op.kind == QS_OP_SWAP) {
+    g->U[0] = 1; g->U[1 * 4 + 2] = 1; g->U[2 * 4 + 1] = 1; g->U[15] = 1;
+  } else {   // U2, UK
+    const double* p = need_mat((size_t)2 * D * D);
+    if (!p) { *err = "gate matrix offset out of range"; return false; }
+    for (int k = 0; k < D * D; k++) g->U[k] = cd(p[2 * k], p[2 * k + 1]);
+  }
+  classify(g);
+  return true;
+}
+
+std::vector<unsigned char> Pool::serialise(Policy pol) const {
+  const size_t E = entries();
+  std::vector<unsigned char> out;
+  if (pol == POL_F32) {
+    out.resize(E * 8);
+    float* f = (float*)out.data();
+    for (size_t k = 0; k < E; k++) {
+      f[2 * k] = (float)f64[2 * k];
+      f[2 * k + 1] = (float)f64[2 * k + 1];
+    }
+  } else if (pol == POL_F64) {
+    out.resize(E * 16);
+    memcpy(out.data(), f64.data(), E * 16);
+  } else {
+    out.resize(E * 16);
+    float* f = (float*)out.data();
+    for (size_t k = 0; k < 2 * E; k++) {
+      const double x = f64[k];
+      const float hi = (float)x;
+      const float lo = (float)(x - (double)hi);
+      f[2 * k] = hi;
+      f[2 * k + 1] = lo;
+    }
+  }
+  return out;
+}
+
+// ------------------------------------------------------------------------------------------
+// Lowering
+// ------------------------------------------------------------------------------------------
+namespace {
+
+struct Addr {
+  bool ok;
+  int idx;          // bit index in the addressed space (tile-local or storage), -1 if outside
+  int storage;      // storage bit
+};
+
+Addr addr_of(const LowerCtx& ctx, int q) {
+  Addr a;
+  a.storage = ctx.sigma[q];
+  if (ctx.tile) {
+    a.idx = ctx.tile_index[a.storage];
+    a.ok = a.idx >= 0;
+  } else {
+    a.idx = a.storage;
+    a.ok = true;
+  }
+  return a;
+}
+
+DevOp blank() {
+  DevOp o;
+  memset(&o, 0, sizeof(o));
+  o.k0 = o.k1 = -1;
+  o.mat = -1;
+  o.gbit = -1;
+  return o;
+}
+
+// add a control on logical qubit q (addressable -> cmask, else gmask)
+void add_ctrl(const LowerCtx& ctx, int q, DevOp* o) {
+  Addr a = addr_of(ctx, q);
+  if (a.ok) o->cmask |= 1ull << a.idx;
+  else o->gmask |= 1ull << a.storage;
+}
+
+bool is_real(const cd& z) { return z.imag() == 0.0; }
+
+// 2x2 matrix m on logical qubit t with controls ctrls
+bool lower_2x2(const cd m[4], int t, const int* ctrls, int nc, const LowerCtx& ctx, Pool& pool,
+               std::vector<DevOp>& out) {
+  DevOp o = blank();
+  for (int k = 0; k < nc; k++) add_ctrl(ctx, ctrls[k], &o);
+  Addr a = addr_of(ctx, t);
+  const bool diag = m[1] == cd(0, 0) && m[2] == cd(0, 0);
+  if (diag) {
+    if (m[0] == cd(1, 0)) {
+      if (m[3] == cd(1, 0)) return true;   // identity
+      // phase on bit t = 1
+      if (a.ok) o.cmask |= 1ull << a.idx;
+      else o.gmask |= 1ull << a.storage;
+      o.type = OP_PHASE;
+      o.mat = (m[3] == cd(-1, 0)) ? -1 : pool.add(m[3]);
+      out.push_back(o);
+      return true;
+    }
+    o.type = OP_DIAG;
+    o.mat = pool.add(m[0]);
+    pool.add(m[3]);
+    if (a.ok) {
+      o.k0 = a.idx;
+    } else {
+      if (!ctx.tile) return false;
+      o.k0 = -1;
+      o.gbit = a.storage;
+    }
+    out.push_back(o);
+    return true;
+  }
+  if (!a.ok) return false;   // non-diagonal target must be addressable
+  o.k0 = a.idx;
+  if (m[0] == cd(0, 0) && m[3] == cd(0, 0) && m[1] == cd(1, 0) && m[2] == cd(1, 0)) {
+    o.type = OP_X;
+    out.push_back(o);
+    return true;
+  }
+  if (m[0] == m[3] && is_real(m[0]) && m[1] == m[2] && m[1].real() == 0.0) {
+    o.type = OP_RX;   // c I - i s X
+    o.mat = pool.add(cd(m[0].real(), -m[1].imag()));
+    out.push_back(o);
+    return true;
+  }
+  o.type = OP_U1;
+  o.mat = pool.add(m[0]);
+  pool.add(m[1]);
+  pool.add(m[2]);
+  pool.add(m[3]);
+  out.push_back(o);
+  return true;
+}
+
+}  // namespace
+
+bool lower_gate(const HGate& g, const LowerCtx& ctx, Pool& pool, std::vector<DevOp>& out) {
+  const int D = 1 << g.nq;
+  if (g.nq == 1) {
+    cd m[4] = {g.U[0], g.U[1], g.U[2], g.U[3]};
+    return lower_2x2(m, g.q[0], nullptr, 0, ctx, pool, out);
+  }
+  if (g.kind == QS_OP_CNOT || g.kind == QS_OP_CZ || g.kind == QS_OP_CP || g.kind == QS_OP_CU) {
+    cd m[4] = {g.U[1 * 4 + 1], g.U[1 * 4 + 3], g.U[3 * 4 + 1], g.U[3 * 4 + 3]};
+    int c = g.q[0];
+    return lower_2x2(m, g.q[1], &c, 1, ctx, pool, out);
+  }
+  if (g.kind == QS_OP_SWAP) {
+    Addr a = addr_of(ctx, g.q[0]), b = addr_of(ctx, g.q[1]);
+    if (!a.ok || !b.ok) return false;
+    DevOp o = blank();
+    o.type = OP_SWAP;
+    o.k0 = std::min(a.idx, b.idx);
+    o.k1 = std::max(a.idx, b.idx);
+    out.push_back(o);
+    return true;
+  }
+  // general 2-qubit / k-qubit dense: every qubit must be addressable
+  DevOp o = blank();
+  int idx[kMaxDenseK];
+  for (int t = 0; t < g.nq; t++) {
+    Addr a = addr_of(ctx, g.q[t]);
+    if (!a.ok) return false;
+    idx[t] = a.idx;
+  }
+  o.mat = (int)pool.entries();
+  for (int k = 0; k < D * D; k++) pool.add(g.U[k]);
+  if (g.nq == 2) {
+    o.type = OP_U2;
+    o.k0 = idx[0];
+    o.k1 = idx[1];
+  } else {
+    o.type = OP_DENSE;
+    o.nk = g.nq;
+    for (int t = 0; t < g.nq; t++) o.kq[t] = idx[t];
+  }
+  out.push_back(o);
+  return true;
+}
+
+}  // namespace qs

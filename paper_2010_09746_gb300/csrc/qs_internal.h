@@ -1,0 +1,157 @@
+// Internal declarations shared by the host runtime, the compiler and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "../../include/qs.h"
+
+namespace qs {
+
+using cd = std::complex<double>;
+
+constexpr int kMaxQubits = 36;
+constexpr int kMaxTileBits = 14;
+constexpr int kMaxDenseK = 6;
+
+// Arithmetic policy selector.
+enum Policy : int { POL_F32 = 0, POL_F64 = 1, POL_DF = 2 };
+
+// ------------------------------------------------------------------------------------------
+// Device op records.  Bit positions are storage bits for per-gate ops and tile-local bit
+// indices for tile ops.  Matrix entries live in a pool (one entry = one complex number in
+// the policy's format); `mat` is the index of the first entry.
+// ------------------------------------------------------------------------------------------
+enum OpType : int32_t {
+  OP_U1 = 1,     // general 2x2 on bit k0 (controls cmask)
+  OP_RX = 2,     // c*I - i*s*X on bit k0: one pool entry (c, s)
+  OP_DIAG = 3,   // diag(d0, d1) on bit k0 (tile op: k0 < 0 -> storage bit `gbit`, block factor)
+  OP_X = 4,      // swap of the pair on bit k0 (CNOT / X), controls cmask
+  OP_PHASE = 5,  // multiply by d0 where all cmask bits (and gmask bits) are 1: CZ, CP, Z, S, T
+  OP_U2 = 6,     // general 4x4 on bits (k0, k1), r = b(k0) + 2 b(k1)
+  OP_DENSE = 7,  // general 2^nk x 2^nk on bits kq[0..nk-1]
+  OP_SWAP = 8,   // exchange bits k0 and k1 (controls cmask)
+};
+
+struct DevOp {
+  int32_t type;
+  int32_t k0, k1;
+  int32_t nk;
+  uint64_t cmask;     // control bits inside the addressed space (tile-local or storage)
+  uint64_t gmask;     // tile ops: storage-bit controls outside the tile (block predicate)
+  int32_t mat;        // first pool entry
+  int32_t gbit;       // tile OP_DIAG on a bit outside the tile: its storage bit
+  int32_t kq[6];
+};
+static_assert(sizeof(DevOp) == 64, "DevOp layout");
+
+// Tile pass launch description.
+struct TilePass {
+  int32_t L;          // tile bits
+  int32_t c;          // low storage bits of every segment (tpos[i] = i for i < c)
+  int32_t n;
+  int32_t nops;
+  int32_t op0;        // first op in the plan's op array
+  int32_t tpos[kMaxTileBits];        // storage positions of tile bits, ascending
+  int32_t npos[kMaxQubits];          // storage positions of the other bits, ascending
+};
+
+// One plan step.
+enum StepKind : int32_t { ST_PASS = 0, ST_GATE = 1, ST_PERMUTE = 2 };
+struct Step {
+  StepKind kind;
+  TilePass pass{};           // ST_PASS
+  DevOp op{};                // ST_GATE (storage bits)
+  std::vector<int> perm;     // ST_PERMUTE: new sigma (logical -> storage)
+  std::vector<int> src_of;   // ST_PERMUTE: storage bit p of the output takes input bit src_of[p]
+  double bytes = 0;          // algorithmic HBM bytes
+};
+
+// ------------------------------------------------------------------------------------------
+// Kernel launchers (kernels_*.cu).  All take the stream and return cudaError_t of the
+// launch.  `pool` is a device array of policy-format matrix entries.
+// ------------------------------------------------------------------------------------------
+cudaError_t launch_init_zero(void* psi, int n, int store_bytes, cudaStream_t s);
+cudaError_t launch_gate(Policy pol, void* psi, int n, const DevOp& op, const void* pool, cudaStream_t s);
+cudaError_t launch_tile_pass(Policy pol, void* psi, const TilePass& tp, const DevOp* ops_dev,
+                             const void* pool, int* status_dev, cudaStream_t s);
+cudaError_t launch_permute(void* dst, const void* src, int n, int store_bytes, const int* src_of,
+                           cudaStream_t s);
+cudaError_t launch_norm_partials(const void* psi, int n, int is_c128, double* partials, int nparts,
+                                 cudaStream_t s);
+cudaError_t launch_norm_final(const double* partials, int nparts, double* out, cudaStream_t s);
+cudaError_t launch_probabilities(const void* psi, int n, int is_c128, double* out, const int* sigma,
+                                 int logical, cudaStream_t s);
+cudaError_t launch_gather_amplitudes(const void* psi, int n, int store_bytes, void* out,
+                                     uint64_t first, uint64_t count, const int* sigma, int logical,
+                                     cudaStream_t s);
+int tile_pass_smem_bytes(Policy pol, int L);
+int tile_pass_ctas_per_sm(Policy pol, int L);
+int norm_num_partials();
+
+// ------------------------------------------------------------------------------------------
+// Host gate model shared by the runtime and the compiler.
+// ------------------------------------------------------------------------------------------
+enum QCls : int { CLS_Z = 0, CLS_X = 1, CLS_N = 2 };
+
+struct HGate {
+  int kind;                   // QS_OP_*
+  int nq;
+  int q[6];                   // logical qubits
+  double param;
+  std::vector<cd> U;          // full 2^nq x 2^nq matrix over q[] (r = sum b(q_t) 2^t)
+  int cls[6];                 // action class per qubit
+};
+
+// Build the HGate of an ABI op (validates qubits and matrix offsets).
+bool make_hgate(int n, const qs_op& op, const double* mats, size_t nmats, HGate* out, std::string* err);
+
+// Matrix pool in policy format.
+struct Pool {
+  std::vector<double> f64;  // (re, im) pairs
+  int add(const cd& z) {
+    f64.push_back(z.real());
+    f64.push_back(z.imag());
+    return (int)(f64.size() / 2 - 1);
+  }
+  size_t entries() const { return f64.size() / 2; }
+  // serialised for a policy: F32 -> float2, F64 -> double2, DF -> float4 (hi, lo, hi, lo)
+  std::vector<unsigned char> serialise(Policy pol) const;
+};
+
+// Lower one gate to device ops with positions mapped through `bitpos` (logical qubit ->
+// target bit index in the addressed space) for gates whose non-diagonal qubits are all
+// addressable; `ctrl_outside` receives storage-bit controls that are not addressable
+// (tile ops only).  Returns false if the gate needs a bit that is not addressable.
+struct LowerCtx {
+  const int* sigma;           // logical -> storage bit
+  bool tile;                  // lowering for a tile pass
+  int tile_index[64];         // storage bit -> tile-local index, -1 if outside
+};
+bool lower_gate(const HGate& g, const LowerCtx& ctx, Pool& pool, std::vector<DevOp>& out);
+
+// ------------------------------------------------------------------------------------------
+// Compiler (compiler.cpp)
+// ------------------------------------------------------------------------------------------
+struct CompileResult {
+  int store_bytes = 16;
+  std::vector<Step> steps;
+  std::vector<std::pair<int, int>> trace;   // QS_MODE_PAPER: (0 local gate | 1 non-local gate | 2 permute, value)
+  std::vector<DevOp> tile_ops;   // ops of all passes, concatenated
+  Pool pool;
+  std::vector<int> sigma_final;
+  qs_plan_stats stats{};
+};
+bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<int>& sigma0,
+                     const qs_compile_opts& o, CompileResult* out, std::string* err);
+
+// Dependency DAG with commutation-pruned edges: immediate predecessors per gate.
+std::vector<std::vector<int>> build_dag(const std::vector<HGate>& gates);
+
+int default_tile_bits(int dtype);
+int default_low_bits(int dtype);
+
+}  // namespace qs

@@ -1,0 +1,176 @@
+"""CPU tests of the C ABI: the library loads, exports every symbol include/qs.h declares,
+validates its arguments, and its host compiler (no GPU needed to compile) emits the
+schedules the oracle's Algorithm 1 emits and valid tile-pass schedules."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2010_09746_gb300 as qs
+from paper_2010_09746_gb300 import _lib
+from oracle import compiler_ref as cr
+from oracle import sv
+from workloads import circuits as wc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "qs.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qs_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = _lib.load()
+    syms = declared_symbols()
+    assert len(syms) >= 30
+    for s in syms:
+        assert hasattr(L, s), s
+    assert set(syms) == set(_lib.SIGNATURES), "binding and header disagree"
+
+
+def test_struct_layout():
+    assert ctypes.sizeof(_lib.qs_op) == 48
+    assert ctypes.sizeof(_lib.qs_compile_opts) == 32
+
+
+def test_version():
+    assert b"sm_103a" in _lib.load().qs_version()
+
+
+def _compile_status(n, circ, **kw):
+    try:
+        qs.compile(n, circ, **kw)
+        return _lib.QS_OK
+    except qs.QSError as e:
+        return e.status
+
+
+def test_compile_rejects_bad_input():
+    g = wc.Gate("H", (0,))
+    assert _compile_status(3, [g]) == _lib.QS_OK
+    assert _compile_status(3, [wc.Gate("H", (3,))]) == _lib.QS_EINVAL
+    assert _compile_status(3, [wc.Gate("CNOT", (1, 1))]) == _lib.QS_EINVAL
+    assert _compile_status(0, [g]) == _lib.QS_EINVAL
+    assert _compile_status(3, [g], sigma0=[0, 0, 1]) == _lib.QS_EINVAL
+    # matrix offset beyond the buffer
+    ops, nops, mats = qs.marshal([wc.Gate("U1", (0,), matrix=np.eye(2))])
+    ops[0].mat = 100
+    h = ctypes.c_void_p()
+    o = qs._opts()
+    st = _lib.load().qs_compile(2, ops, nops, mats.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), mats.size,
+                                None, ctypes.byref(o), ctypes.byref(h))
+    assert st == _lib.QS_EINVAL
+    assert b"offset" in _lib.load().qs_last_error()
+
+
+def test_state_calls_validate_null():
+    L = _lib.load()
+    assert L.qs_destroy(None) == _lib.QS_OK
+    assert L.qs_sync(None) == _lib.QS_EINVAL
+    assert L.qs_norm(None, None) == _lib.QS_EINVAL
+    h = ctypes.c_void_p()
+    assert L.qs_create(0, 1, ctypes.byref(h)) == _lib.QS_EINVAL
+    assert L.qs_create(37, 1, ctypes.byref(h)) == _lib.QS_EINVAL
+
+
+def oracle_trace(n, m, circ, scoring="closure"):
+    prog, st = cr.alg1(n, m, circ, scoring=scoring)
+    out = []
+    sigma = list(range(n))
+    for ins in prog:
+        if ins[0] == "gate":
+            out.append((1 if ins[2] else 0, ins[1]))
+        else:
+            new = ins[1]
+            a, b = [q for q in range(n) if new[q] != sigma[q]]
+            l, g = (a, b) if sigma[a] < m else (b, a)
+            out.append((2, 64 * l + g))
+            sigma = list(new)
+    return out, st
+
+
+@pytest.mark.parametrize("scoring", [0, 1])
+@pytest.mark.parametrize("n,m,p,seed", [(12, 9, 0.3, 0), (12, 9, 1.0, 1), (12, 9, 0.0, 2), (20, 16, 0.3, 3),
+                                        (35, 28, 0.3, 4), (35, 28, 1.0, 5), (50, 40, 0.3, 6)])
+def test_paper_mode_schedule_matches_oracle_alg1(n, m, p, seed, scoring):
+    """Integer work, bit-exact: the library's Algorithm 1 emits exactly the oracle's
+    instruction list (gates, non-local gates, transpositions)."""
+    if n > 36:
+        pytest.skip("library limit n <= 36")
+    circ = wc.paper_random_circuit(n, p, seed)
+    want, st = oracle_trace(n, m, circ, scoring="closure" if scoring == 0 else "frontier")
+    plan = qs.compile(n, circ, mode="paper", tile_bits=m, scoring=scoring)
+    got = plan.trace()
+    assert got == want
+    s = plan.stats()
+    assert s["n_permutes"] == st["n_permutes"]
+    assert s["n_comm_gates"] == st["n_comm_gates"]
+
+
+def test_paper_mode_fig3_statistic_through_library():
+    n, m = 35, 28
+    fr = []
+    for seed in range(20):
+        circ = wc.paper_random_circuit(n, 0.3, seed)
+        s = qs.compile(n, circ, mode="paper", tile_bits=m).stats()
+        fr.append((s["n_permutes"] + s["n_comm_gates"]) / s["n_gates"])
+    assert abs(np.mean(fr) - 0.035) < 0.01
+
+
+def tile_schedule(plan):
+    passes = []
+    for k, v in plan.trace():
+        if k == 3:
+            passes.append([v, []])
+        elif k == 4:
+            passes[-1][0] |= v << 31
+        else:
+            assert k == 0
+            passes[-1][1].append(v)
+    return passes
+
+
+@pytest.mark.parametrize("n,L,c,seed", [(10, 6, 2, 0), (14, 8, 3, 1), (16, 9, 3, 2), (30, 12, 3, 3)])
+def test_tile_mode_schedule_is_valid(n, L, c, seed):
+    circ = wc.rzrx_cz_circuit(n, 6, seed) + wc.random_mixed_circuit(n, 60, seed, kmax=3)
+    plan = qs.compile(n, circ, mode="tile", tile_bits=L, low_bits=c)
+    passes = tile_schedule(plan)
+    preds = cr.build_dag(circ)
+    seen = set()
+    for mask, ids in passes:
+        assert bin(mask).count("1") == L
+        assert mask & ((1 << c) - 1) == (1 << c) - 1
+        for v in ids:
+            for p in preds[v]:
+                assert p in seen
+            seen.add(v)
+            g = circ[v]
+            need = [q for q, k in zip(g.qubits, cr.qubit_classes(g)) if k != cr.CLS_Z]
+            if g.kind in ("U2", "UK") and len(g.qubits) >= 2:
+                need = list(g.qubits)
+            for q in need:
+                assert (mask >> q) & 1, "non-diagonal qubit outside the tile"
+    assert seen == set(range(len(circ)))
+    assert plan.stats()["n_passes"] == len(passes)
+
+
+def test_tile_mode_order_simulates_to_original():
+    n = 9
+    circ = wc.random_mixed_circuit(n, 120, seed=5, kmax=3)
+    plan = qs.compile(n, circ, mode="tile", tile_bits=6, low_bits=2)
+    order = [v for _, ids in tile_schedule(plan) for v in ids]
+    np.testing.assert_allclose(sv.simulate(n, [circ[v] for v in order]), sv.simulate(n, circ), atol=1e-13)
+
+
+def test_tile_mode_pass_count_beats_per_gate():
+    n = 30
+    circ = wc.rzrx_cz_circuit(n, 40, seed=0)
+    st = qs.compile(n, circ, mode="tile").stats()
+    assert st["n_gates"] == 2680
+    assert st["n_passes"] < 300
+    pg = qs.compile(n, circ, mode="pergate").stats()
+    assert st["hbm_bytes"] < pg["hbm_bytes"] / 5
