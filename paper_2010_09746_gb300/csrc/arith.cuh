@@ -131,7 +131,8 @@ static __device__ __forceinline__ dfl two_prod(float a, float b) {
 // Split a binary64 value into hi + lo floats without FP64 instructions.
 // hi keeps the leading 24 significant bits (truncated), lo = x - hi (its 29 bits rounded
 // to 24): |x - (hi + lo)| <= 2^-47 |x|.  |x| < 2^-126 flushes to 0 (absolute error
-// below 1.2e-38); the lo part flushes when |x| < 2^-74 (absolute error below 2^-97).
+// below 1.2e-38); the lo part flushes when it would leave the normal float range
+// (|x| below about 2^-98; absolute error below 2^-120).
 static __device__ __forceinline__ dfl split_double(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned int w1 = (unsigned int)(b >> 32);
@@ -143,16 +144,18 @@ static __device__ __forceinline__ dfl split_double(double x) {
   float hi = __uint_as_float(sign | ((unsigned int)ef << 23) | m23);
   hi = (ef > 0) ? hi : 0.0f;
   const unsigned int r = w0 & 0x1FFFFFFFu;                   // low 29 mantissa bits
-  const int es = e - 948;                                   // biased exponent of 2^(e-1075)
-  float scale = __uint_as_float(((unsigned int)(es > 0 ? es : 1)) << 23);
-  float lo = __fmul_rn(__uint2float_rn(r), scale);
-  lo = (es > 0 && ef > 0) ? __uint_as_float(__float_as_uint(lo) ^ sign) : 0.0f;
+  // lo = r * 2^(e - 1075): convert r exactly-rounded, then move its exponent field
+  const unsigned int rb = __float_as_uint(__uint2float_rn(r));
+  const int el = (int)(rb >> 23) + (e - 1075);               // biased exponent of lo
+  float lo = __uint_as_float(sign | ((unsigned int)el << 23) | (rb & 0x7FFFFFu));
+  lo = (r != 0u && el > 0 && ef > 0) ? lo : 0.0f;
   return {hi, lo};
 }
 
-// Join hi + lo (|lo| <= ulp(hi), as produced by the arithmetic below) into a binary64
-// with integer operations only: the binary64 pattern of hi plus lo counted in units of
-// the binary64 ulp of hi (IEEE patterns are monotonic in magnitude for a fixed sign).
+// Join hi + lo (|lo| <= ulp(hi)/2, as produced by the arithmetic below) into a binary64
+// with integer operations only: the binary64 pattern of hi plus lo counted in binary64 ulps
+// (IEEE patterns are monotonic in magnitude for a fixed sign, so adding k to the pattern
+// moves the value by k ulps, across a binade boundary included).
 static __device__ __forceinline__ double join_double(float hi, float lo) {
   const unsigned int hb = __float_as_uint(hi);
   const unsigned int sign = hb & 0x80000000u;
@@ -163,7 +166,10 @@ static __device__ __forceinline__ double join_double(float hi, float lo) {
                           ((unsigned long long)(hb & 7u) << 29);
   const unsigned int lb = __float_as_uint(lo);
   const int el = (int)((lb >> 23) & 0xFFu);
-  const int ne = el + 179 - ef;                             // exponent of lo * 2^(179-ef)
+  // lo is counted in binary64 ulps of hi's binade, 2^(ef-179); when hi is a power of two and
+  // lo points down, the result lies in the binade below, whose ulp is half as large
+  const bool down = ((lb ^ hb) & 0x80000000u) && ((hb & 0x7FFFFFu) == 0u);
+  const int ne = el + (down ? 180 : 179) - ef;             // exponent of lo / ulp
   int k = 0;
   if (el != 0 && ne > 0) {
     float ls = __uint_as_float((lb & 0x807FFFFFu) | ((unsigned int)ne << 23));

@@ -60,6 +60,10 @@ Policy policy_for(qs_dtype dt, qs_arith a) {
 
 }  // namespace
 
+namespace qs {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace qs
+
 struct KernelRecord {
   std::string name;
   cudaEvent_t e0, e1;
@@ -94,6 +98,10 @@ struct qs_plan {
   CompileResult cr;
   DevOp* ops_dev = nullptr;
   size_t ops_bytes = 0;
+  RegOp* rops_dev = nullptr;
+  size_t rops_bytes = 0;
+  StageRec* stages_dev = nullptr;
+  size_t stages_bytes = 0;
   void* pool_dev = nullptr;
   size_t pool_bytes = 0;
   bool uploaded = false;
@@ -467,6 +475,8 @@ qs_status qs_plan_destroy(qs_plan_t p) {
   if (p->uploaded) {
     cudaDeviceSynchronize();
     dev_free(p->ops_dev, p->ops_bytes, nullptr);
+    dev_free(p->rops_dev, p->rops_bytes, nullptr);
+    dev_free(p->stages_dev, p->stages_bytes, nullptr);
     dev_free(p->pool_dev, p->pool_bytes, nullptr);
     cudaDeviceSynchronize();
   }
@@ -500,13 +510,22 @@ qs_status qs_plan_get_trace(qs_plan_t p, int32_t* kinds, int32_t* values, size_t
 static qs_status plan_upload(qs_plan* p) {
   if (p->uploaded) return QS_OK;
   p->ops_bytes = p->cr.tile_ops.size() * sizeof(DevOp);
+  p->rops_bytes = p->cr.reg_ops.size() * sizeof(RegOp);
+  p->stages_bytes = p->cr.stages.size() * sizeof(StageRec);
   std::vector<unsigned char> ser = p->cr.pool.serialise(p->pol);
   p->pool_bytes = ser.size();
   if (p->ops_bytes) p->ops_dev = (DevOp*)dev_alloc(p->ops_bytes, nullptr);
+  if (p->rops_bytes) p->rops_dev = (RegOp*)dev_alloc(p->rops_bytes, nullptr);
+  if (p->stages_bytes) p->stages_dev = (StageRec*)dev_alloc(p->stages_bytes, nullptr);
   if (p->pool_bytes) p->pool_dev = dev_alloc(p->pool_bytes, nullptr);
-  if ((p->ops_bytes && !p->ops_dev) || (p->pool_bytes && !p->pool_dev)) return fail(QS_ENOMEM, "plan upload allocation failed");
+  if ((p->ops_bytes && !p->ops_dev) || (p->pool_bytes && !p->pool_dev) || (p->rops_bytes && !p->rops_dev) ||
+      (p->stages_bytes && !p->stages_dev))
+    return fail(QS_ENOMEM, "plan upload allocation failed");
   cudaError_t e = cudaSuccess;
   if (p->ops_bytes) e = cudaMemcpy(p->ops_dev, p->cr.tile_ops.data(), p->ops_bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && p->rops_bytes) e = cudaMemcpy(p->rops_dev, p->cr.reg_ops.data(), p->rops_bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && p->stages_bytes)
+    e = cudaMemcpy(p->stages_dev, p->cr.stages.data(), p->stages_bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && p->pool_bytes) e = cudaMemcpy(p->pool_dev, ser.data(), p->pool_bytes, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "plan upload");
   p->uploaded = true;
@@ -526,7 +545,10 @@ qs_status qs_execute(qs_handle h, qs_plan_t p) {
     const char* name = step_name(s, p->pol);
     if (s.kind == ST_PASS) {
       CUDA_TRY(timed(h, name, s.bytes,
-                     [&] { return launch_tile_pass(p->pol, h->psi, s.pass, p->ops_dev, p->pool_dev, h->status_dev, h->stream); }),
+                     [&] {
+                       return launch_tile_pass(p->pol, h->psi, s.pass, p->stages_dev, p->rops_dev, p->ops_dev,
+                                               p->pool_dev, h->status_dev, h->stream);
+                     }),
                "tile pass launch");
     } else if (s.kind == ST_GATE) {
       CUDA_TRY(timed(h, name, s.bytes, [&] { return launch_gate(p->pol, h->psi, h->n, s.op, p->pool_dev, h->stream); }),

@@ -158,15 +158,16 @@ bool emit_pass(int n, int L, int c, const std::vector<int>& tbits_sorted, const 
   ctx.sigma = sigma.data();
   ctx.tile = true;
   fill_tile_ctx(&ctx, st.pass.tpos, L);
-  st.pass.op0 = (int)out->tile_ops.size();
+  std::vector<DevOp> ops;
   for (int v : gate_ids) {
-    if (!lower_gate(gates[v], ctx, out->pool, out->tile_ops)) {
+    if (!lower_gate(gates[v], ctx, out->pool, ops)) {
       *err = "internal: gate not lowerable in its tile pass";
       return false;
     }
   }
-  st.pass.nops = (int)out->tile_ops.size() - st.pass.op0;
-  if (st.pass.nops == 0) return true;   // identity gates only
+  if (ops.empty()) return true;   // identity gates only
+  st.pass.K = register_bits(out->store_bytes == 16 ? QS_C128 : QS_C64, L);
+  build_stages(ops, L, st.pass.K, out, &st.pass.st0, &st.pass.nst);
   const int store_bytes = out->store_bytes;
   st.bytes = 2.0 * (double)store_bytes * (double)(1ull << n);
   out->steps.push_back(std::move(st));

@@ -98,12 +98,61 @@ __device__ __forceinline__ int bit_list(uint32_t m, int* pos) {
   return k;
 }
 
-// Apply one tile op to the shared-memory tile T (2^L elements in policy register format).
+// Shared-memory tile addressing: element i sits at i + (i >> c) * padE, i.e. every 2^c-element
+// segment is followed by 16 bytes of padding, which spreads the register-stage accesses of a
+// warp over the banks.
+struct Pad {
+  int c, padE;
+  __device__ __forceinline__ uint32_t operator()(uint32_t i) const { return i + (i >> c) * padE; }
+};
+
+// Dense 2^k x 2^k block in shared memory (kept out of line: its per-thread arrays would
+// otherwise give every tile kernel a large stack frame).
 template <class A>
-__device__ __forceinline__ void apply_op(typename A::reg_t* T, int L, const DevOp& op,
-                                         const typename A::mat_t* __restrict__ pool, uint64_t base) {
+__device__ __noinline__ void apply_dense_op(typename A::reg_t* Tm, int L, const DevOp& op,
+                                            const typename A::mat_t* __restrict__ pool, Pad px) {
   using R = typename A::reg_t;
   using M = typename A::mat_t;
+  const int tid = threadIdx.x;
+  const uint32_t cm = (uint32_t)op.cmask;
+  int pos[8];
+  const int K = op.nk;
+  const int D = 1 << K;
+  uint32_t zb = cm;
+  for (int b = 0; b < K; b++) zb |= 1u << op.kq[b];
+  const int nz = bit_list(zb, pos);
+  const uint32_t nw = 1u << (L - nz);
+  const M* m = pool + op.mat;
+  for (uint32_t t = tid; t < nw; t += kTileThreads) {
+    const uint32_t i = texpand(t, pos, nz, cm);
+    R x[1 << kMaxDenseK];
+    uint32_t off[1 << kMaxDenseK];
+    for (int r = 0; r < D; r++) {
+      uint32_t o = 0;
+      for (int b = 0; b < K; b++)
+        if ((r >> b) & 1) o |= 1u << op.kq[b];
+      off[r] = px(i | o);
+      x[r] = Tm[off[r]];
+    }
+    for (int r = 0; r < D; r++) {
+      R acc = A::zero();
+      for (int c = 0; c < D; c++) acc = A::mac(acc, m[r * D + c], x[c]);
+      Tm[off[r]] = acc;
+    }
+  }
+}
+
+// Apply one tile op to the shared-memory tile (2^L elements in policy register format).
+template <class A>
+__device__ __forceinline__ void apply_op(typename A::reg_t* Tm, int L, const DevOp& op,
+                                         const typename A::mat_t* __restrict__ pool, uint64_t base, Pad px) {
+  using R = typename A::reg_t;
+  using M = typename A::mat_t;
+  struct TV {
+    R* t;
+    Pad px;
+    __device__ __forceinline__ R& operator[](uint32_t i) const { return t[px(i)]; }
+  } T{Tm, px};
   const int tid = threadIdx.x;
   const uint32_t cm = (uint32_t)op.cmask;
   int pos[8];
@@ -210,65 +259,232 @@ __device__ __forceinline__ void apply_op(typename A::reg_t* T, int L, const DevO
       }
       break;
     }
-    case OP_DENSE: {
-      const int K = op.nk;
-      const int D = 1 << K;
-      uint32_t zb = cm;
-      for (int b = 0; b < K; b++) zb |= 1u << op.kq[b];
-      const int nz = bit_list(zb, pos);
-      const uint32_t nw = 1u << (L - nz);
-      const M* m = pool + op.mat;
-      for (uint32_t t = tid; t < nw; t += kTileThreads) {
-        const uint32_t i = texpand(t, pos, nz, cm);
-        R x[1 << kMaxDenseK];
-        uint32_t off[1 << kMaxDenseK];
-        for (int r = 0; r < D; r++) {
-          uint32_t o = 0;
-          for (int b = 0; b < K; b++)
-            if ((r >> b) & 1) o |= 1u << op.kq[b];
-          off[r] = i | o;
-          x[r] = T[off[r]];
-        }
-        for (int r = 0; r < D; r++) {
-          R acc = A::zero();
-          for (int c = 0; c < D; c++) acc = A::mac(acc, m[r * D + c], x[c]);
-          T[off[r]] = acc;
-        }
+    case OP_DENSE:
+      apply_dense_op<A>(Tm, L, op, pool, px);
+      break;
+    default:
+      break;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Register stages
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t pdep32(uint32_t g, uint32_t mask) {
+  uint32_t r = 0;
+  for (uint32_t m = mask; m; m &= m - 1u) {
+    if (g & 1u) r |= m & (0u - m);
+    g >>= 1;
+  }
+  return r;
+}
+
+template <class A, int K, int S>
+__device__ __forceinline__ void r_u1(typename A::reg_t (&x)[1 << K], const typename A::mat_t* m, uint32_t csl) {
+  const typename A::mat_t u00 = m[0], u01 = m[1], u10 = m[2], u11 = m[3];
+#pragma unroll
+  for (int j = 0; j < (1 << K); j++) {
+    if (j & (1 << S)) continue;
+    if ((j & csl) != csl) continue;
+    const typename A::reg_t a = x[j], b = x[j | (1 << S)];
+    x[j] = A::mac2(u00, a, u01, b);
+    x[j | (1 << S)] = A::mac2(u10, a, u11, b);
+  }
+}
+template <class A, int K, int S>
+__device__ __forceinline__ void r_rx(typename A::reg_t (&x)[1 << K], const typename A::mat_t* m, uint32_t csl) {
+  const typename A::mat_t cs = m[0];
+#pragma unroll
+  for (int j = 0; j < (1 << K); j++) {
+    if (j & (1 << S)) continue;
+    if ((j & csl) != csl) continue;
+    const typename A::reg_t a = x[j], b = x[j | (1 << S)];
+    x[j] = A::rx(cs, a, b);
+    x[j | (1 << S)] = A::rx(cs, b, a);
+  }
+}
+template <class A, int K, int S>
+__device__ __forceinline__ void r_x(typename A::reg_t (&x)[1 << K], const typename A::mat_t*, uint32_t csl) {
+#pragma unroll
+  for (int j = 0; j < (1 << K); j++) {
+    if (j & (1 << S)) continue;
+    if ((j & csl) != csl) continue;
+    const typename A::reg_t a = x[j];
+    x[j] = x[j | (1 << S)];
+    x[j | (1 << S)] = a;
+  }
+}
+template <class A, int K, int S0, int S1>
+__device__ __forceinline__ void r_u2(typename A::reg_t (&x)[1 << K], const typename A::mat_t* m, uint32_t csl) {
+  using R = typename A::reg_t;
+#pragma unroll
+  for (int j = 0; j < (1 << K); j++) {
+    if (j & ((1 << S0) | (1 << S1))) continue;
+    if ((j & csl) != csl) continue;
+    const int i0 = j, i1 = j | (1 << S0), i2 = j | (1 << S1), i3 = j | (1 << S0) | (1 << S1);
+    const R x0 = x[i0], x1 = x[i1], x2 = x[i2], x3 = x[i3];
+    R y[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+      R acc = A::mac2(m[4 * r + 0], x0, m[4 * r + 1], x1);
+      acc = A::mac(acc, m[4 * r + 2], x2);
+      y[r] = A::mac(acc, m[4 * r + 3], x3);
+    }
+    x[i0] = y[0];
+    x[i1] = y[1];
+    x[i2] = y[2];
+    x[i3] = y[3];
+  }
+}
+
+// slot dispatch (the pair structure of the register array must be known at compile time)
+#define QS_SLOT_DISPATCH(FN, s, ...)                                  \
+  do {                                                                \
+    if constexpr (K > 0) if ((s) == 0) { FN<A, K, 0>(__VA_ARGS__); break; } \
+    if constexpr (K > 1) if ((s) == 1) { FN<A, K, 1>(__VA_ARGS__); break; } \
+    if constexpr (K > 2) if ((s) == 2) { FN<A, K, 2>(__VA_ARGS__); break; } \
+    if constexpr (K > 3) if ((s) == 3) { FN<A, K, 3>(__VA_ARGS__); break; } \
+    if constexpr (K > 4) if ((s) == 4) { FN<A, K, 4>(__VA_ARGS__); break; } \
+  } while (0)
+
+template <class A, int K, int S0>
+__device__ __forceinline__ void r_u2_s1(typename A::reg_t (&x)[1 << K], int s1, const typename A::mat_t* m,
+                                        uint32_t csl) {
+  if constexpr (K > 0 && S0 != 0) if (s1 == 0) { r_u2<A, K, S0, 0>(x, m, csl); return; }
+  if constexpr (K > 1 && S0 != 1) if (s1 == 1) { r_u2<A, K, S0, (K > 1 ? 1 : 0)>(x, m, csl); return; }
+  if constexpr (K > 2 && S0 != 2) if (s1 == 2) { r_u2<A, K, S0, (K > 2 ? 2 : 0)>(x, m, csl); return; }
+  if constexpr (K > 3 && S0 != 3) if (s1 == 3) { r_u2<A, K, S0, (K > 3 ? 3 : 0)>(x, m, csl); return; }
+  if constexpr (K > 4 && S0 != 4) if (s1 == 4) { r_u2<A, K, S0, (K > 4 ? 4 : 0)>(x, m, csl); return; }
+}
+
+template <class A, int K>
+__device__ __forceinline__ void apply_regop(typename A::reg_t (&x)[1 << K], const RegOp& op,
+                                            const typename A::mat_t* __restrict__ pool, uint32_t gidx,
+                                            uint64_t base) {
+  using R = typename A::reg_t;
+  using M = typename A::mat_t;
+  if ((gidx & op.cot) != op.cot) return;   // a control outside the registers is 0 for this group
+  const M* m = pool + op.mat;
+  const uint32_t csl = op.csl;
+  switch (op.type) {
+    case OP_U1: QS_SLOT_DISPATCH(r_u1, op.s0, x, m, csl); break;
+    case OP_RX: QS_SLOT_DISPATCH(r_rx, op.s0, x, m, csl); break;
+    case OP_X: QS_SLOT_DISPATCH(r_x, op.s0, x, m, csl); break;
+    case OP_U2: {
+      if constexpr (K >= 2) {
+        const int s1 = op.s1;
+        QS_SLOT_DISPATCH(r_u2_s1, op.s0, x, s1, m, csl);
+      }
+      break;
+    }
+    case OP_DIAG: {
+      const M d0 = m[0], d1 = m[1];
+      if (op.s0 >= 0) {
+        const int s0 = op.s0;
+#pragma unroll
+        for (int j = 0; j < (1 << K); j++)
+          if ((j & csl) == csl) x[j] = A::mul(((j >> s0) & 1) ? d1 : d0, x[j]);
+      } else {
+        const M d = (op.tb >= 0) ? (((gidx >> op.tb) & 1u) ? d1 : d0) : (((base >> op.gbit) & 1ull) ? d1 : d0);
+#pragma unroll
+        for (int j = 0; j < (1 << K); j++)
+          if ((j & csl) == csl) x[j] = A::mul(d, x[j]);
+      }
+      break;
+    }
+    case OP_PHASE: {
+      if (op.neg) {
+#pragma unroll
+        for (int j = 0; j < (1 << K); j++)
+          if ((j & csl) == csl) x[j] = A::neg(x[j]);
+      } else {
+        const M d = m[0];
+#pragma unroll
+        for (int j = 0; j < (1 << K); j++)
+          if ((j & csl) == csl) x[j] = A::mul(d, x[j]);
       }
       break;
     }
     default:
       break;
   }
+  (void)sizeof(R);
 }
 
-template <class A>
-__global__ void __launch_bounds__(kTileThreads) k_tile_pass(typename A::store_t* __restrict__ psi, const TilePass tp,
-                                                            const DevOp* __restrict__ ops,
-                                                            const typename A::mat_t* __restrict__ pool,
-                                                            int* __restrict__ status) {
+// One register stage over the whole tile.  from_store / to_store: the shared-memory tile
+// holds storage-format elements before / after the stage (policies whose register format
+// differs from the storage format convert here instead of in a separate pass).
+template <class A, int K>
+__device__ __forceinline__ void run_reg_stage(typename A::reg_t* T, const StageRec& sr, const RegOp* __restrict__ rops,
+                                              const typename A::mat_t* __restrict__ pool, int L, Pad px,
+                                              uint64_t base, bool from_store, bool to_store) {
+  using R = typename A::reg_t;
+  using S = typename A::store_t;
+  const uint32_t tile_mask = (L >= 32) ? 0xFFFFFFFFu : ((1u << L) - 1u);
+  const uint32_t omask = tile_mask & ~(uint32_t)sr.rmask;
+  const uint32_t ngroups = 1u << (L - K);
+  uint32_t rb[K];
+#pragma unroll
+  for (int b = 0; b < K; b++) rb[b] = 1u << sr.rbits[b];
+  for (uint32_t g = threadIdx.x; g < ngroups; g += kTileThreads) {
+    const uint32_t gidx = pdep32(g, omask);
+    R x[1 << K];
+#pragma unroll
+    for (int j = 0; j < (1 << K); j++) {
+      uint32_t idx = gidx;
+#pragma unroll
+      for (int b = 0; b < K; b++)
+        if ((j >> b) & 1) idx |= rb[b];
+      const uint32_t p = px(idx);
+      if constexpr (std::is_same<R, S>::value) {
+        x[j] = T[p];
+      } else {
+        x[j] = from_store ? A::from_store(reinterpret_cast<const S*>(T)[p]) : T[p];
+      }
+    }
+    for (int k = 0; k < sr.nops; k++) {
+      const RegOp op = rops[sr.op0 + k];
+      if ((base & op.gmask) != op.gmask) continue;
+      apply_regop<A, K>(x, op, pool, gidx, base);
+    }
+#pragma unroll
+    for (int j = 0; j < (1 << K); j++) {
+      uint32_t idx = gidx;
+#pragma unroll
+      for (int b = 0; b < K; b++)
+        if ((j >> b) & 1) idx |= rb[b];
+      const uint32_t p = px(idx);
+      if constexpr (std::is_same<R, S>::value) {
+        T[p] = x[j];
+      } else {
+        if (to_store) reinterpret_cast<S*>(T)[p] = A::to_store(x[j]);
+        else T[p] = x[j];
+      }
+    }
+  }
+}
+
+template <class A, int K>
+__global__ void __launch_bounds__(kTileThreads, 2)
+    k_tile_staged(typename A::store_t* __restrict__ psi, const TilePass tp, const StageRec* __restrict__ stages,
+                  const RegOp* __restrict__ rops, const DevOp* __restrict__ dops,
+                  const typename A::mat_t* __restrict__ pool, int* __restrict__ status) {
   using S = typename A::store_t;
   using R = typename A::reg_t;
   static_assert(sizeof(R) == sizeof(S), "in-place conversion needs equal element sizes");
+  constexpr bool kConv = !std::is_same<R, S>::value;
   extern __shared__ __align__(128) unsigned char smem[];
   const int L = tp.L, c = tp.c;
+  const Pad px{c, (int)(16 / sizeof(S))};
   const uint32_t nelem = 1u << L;
   const uint32_t nseg = 1u << (L - c);
   const uint32_t seg_bytes = (uint32_t)sizeof(S) << c;
+  const uint32_t seg_stride = seg_bytes + 16u;
   R* T = reinterpret_cast<R*>(smem);
-  uint64_t* seg_off = reinterpret_cast<uint64_t*>(smem + (size_t)nelem * sizeof(R));
-  uint64_t* bar_p = seg_off + nseg;
+  uint64_t* bar_p = reinterpret_cast<uint64_t*>(smem + (size_t)nseg * seg_stride);
   const uint32_t bar = smem_u32(bar_p);
   const uint32_t tile_s = smem_u32(T);
   const int tid = threadIdx.x;
-
-  // segment offsets: deposit the segment index into tile bits c .. L-1
-  for (uint32_t s = tid; s < nseg; s += kTileThreads) {
-    uint64_t o = 0;
-    for (int k = 0; k < L - c; k++)
-      if ((s >> k) & 1u) o |= 1ull << tp.tpos[c + k];
-    seg_off[s] = o;
-  }
   if (tid == 0) {
     mbar_init(bar, 1);
     fence_async_smem();
@@ -283,44 +499,61 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_pass(typename A::store_t*
     for (int k = 0; k < nout; k++)
       if ((b >> k) & 1ull) base |= 1ull << tp.npos[k];
 
-    // ---- load: 2^(L-c) bulk copies into the tile, counted on the mbarrier
+    // ---- load: 2^(L-c) bulk copies of 2^c contiguous amplitudes, counted on the mbarrier
     if (tid == 0) mbar_arrive_expect_tx(bar, nseg * seg_bytes);
     __syncthreads();
-    for (uint32_t s = tid; s < nseg; s += kTileThreads)
-      bulk_load(tile_s + s * seg_bytes, psi + (base | seg_off[s]), seg_bytes, bar);
+    for (uint32_t s = tid; s < nseg; s += kTileThreads) {
+      uint64_t off = 0;
+      for (int k = 0; k < L - c; k++)
+        if ((s >> k) & 1u) off |= 1ull << tp.tpos[c + k];
+      bulk_load(tile_s + s * seg_stride, psi + (base | off), seg_bytes, bar);
+    }
     if (!mbar_wait(bar, phase, globaltimer() + kWaitNs)) {
       if (tid == 0) atomicExch(status, (int)QS_ETIMEOUT);
       return;
     }
     phase ^= 1u;
 
-    // ---- convert storage -> register format in place (double-float policy)
-    if constexpr (!std::is_same<R, S>::value) {
-      S* Ts = reinterpret_cast<S*>(smem);
-      for (uint32_t i = tid; i < nelem; i += kTileThreads) T[i] = A::from_store(Ts[i]);
+    // ---- stages
+    bool in_store = true;   // the tile holds storage-format elements
+    for (int k = 0; k < tp.nst; k++) {
+      const StageRec sr = stages[tp.st0 + k];
+      const bool last = (k == tp.nst - 1);
+      if (sr.kind == 0) {
+        run_reg_stage<A, K>(T, sr, rops, pool, L, px, base, in_store, last);
+        in_store = last;
+      } else {
+        if (kConv && in_store) {
+          S* Ts = reinterpret_cast<S*>(smem);
+          for (uint32_t i = tid; i < nelem; i += kTileThreads) T[px(i)] = A::from_store(Ts[px(i)]);
+          __syncthreads();
+        }
+        in_store = false;
+        for (int o = 0; o < sr.nops; o++) {
+          const DevOp& op = dops[sr.op0 + o];
+          if ((base & op.gmask) != op.gmask) continue;
+          apply_op<A>(T, L, op, pool, base, px);
+          __syncthreads();
+        }
+      }
       __syncthreads();
     }
-
-    // ---- the pass's gates
-    for (int k = 0; k < tp.nops; k++) {
-      const DevOp& op = ops[tp.op0 + k];
-      if ((base & op.gmask) != op.gmask) continue;   // block-uniform predicate
-      apply_op<A>(T, L, op, pool, base);
-      __syncthreads();
-    }
-
-    if constexpr (!std::is_same<R, S>::value) {
+    if (kConv && !in_store) {
       S* Ts = reinterpret_cast<S*>(smem);
       for (uint32_t i = tid; i < nelem; i += kTileThreads) {
-        const R v = T[i];
-        Ts[i] = A::to_store(v);
+        const R v = T[px(i)];
+        Ts[px(i)] = A::to_store(v);
       }
     }
-    // ---- store: bulk copies back; smem is reused only after they have been read
+    // ---- store: bulk copies back; the tile is reused only after they have been read
     fence_async_smem();
     __syncthreads();
-    for (uint32_t s = tid; s < nseg; s += kTileThreads)
-      bulk_store(psi + (base | seg_off[s]), tile_s + s * seg_bytes, seg_bytes);
+    for (uint32_t s = tid; s < nseg; s += kTileThreads) {
+      uint64_t off = 0;
+      for (int k = 0; k < L - c; k++)
+        if ((s >> k) & 1u) off |= 1ull << tp.tpos[c + k];
+      bulk_store(psi + (base | off), tile_s + s * seg_stride, seg_bytes);
+    }
     bulk_commit();
     bulk_wait_read0();
     __syncthreads();
@@ -328,16 +561,17 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_pass(typename A::store_t*
   bulk_wait0();
 }
 
-template <class A>
-cudaError_t launch_tile_t(void* psi, const TilePass& tp, const DevOp* ops, const void* pool, int* status,
-                          cudaStream_t st) {
-  const int smem = (int)((sizeof(typename A::reg_t) << tp.L) + (8u << (tp.L - tp.c)) + 16);
-  static int configured_bytes = 0;
+template <class A, int K>
+cudaError_t launch_staged(void* psi, const TilePass& tp, const StageRec* stages, const RegOp* rops,
+                          const DevOp* dops, const void* pool, int* status, cudaStream_t st) {
+  using S = typename A::store_t;
+  const size_t smem = ((size_t)1 << (tp.L - tp.c)) * (((size_t)sizeof(S) << tp.c) + 16) + 16;
+  static bool configured = false;
   static int sms = 0;
-  if (smem > configured_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_tile_pass<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_tile_staged<A, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
-    configured_bytes = 227 * 1024;
+    configured = true;
   }
   if (sms == 0) {
     int dev = 0;
@@ -345,30 +579,47 @@ cudaError_t launch_tile_t(void* psi, const TilePass& tp, const DevOp* ops, const
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_pass<A>, kTileThreads, smem);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_staged<A, K>, kTileThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const uint64_t nblocks = 1ull << (tp.n - tp.L);
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > nblocks) grid = nblocks;
-  k_tile_pass<A><<<(unsigned)grid, kTileThreads, smem, st>>>(
-      (typename A::store_t*)psi, tp, ops, (const typename A::mat_t*)pool, status);
+  k_tile_staged<A, K><<<(unsigned)grid, kTileThreads, smem, st>>>((S*)psi, tp, stages, rops, dops,
+                                                                   (const typename A::mat_t*)pool, status);
   return cudaGetLastError();
+}
+
+template <class A>
+cudaError_t launch_tile_t(void* psi, const TilePass& tp, const StageRec* stages, const RegOp* rops,
+                          const DevOp* dops, const void* pool, int* status, cudaStream_t st) {
+  switch (tp.K) {
+    case 1: return launch_staged<A, 1>(psi, tp, stages, rops, dops, pool, status, st);
+    case 2: return launch_staged<A, 2>(psi, tp, stages, rops, dops, pool, status, st);
+    case 3: return launch_staged<A, 3>(psi, tp, stages, rops, dops, pool, status, st);
+    case 4: return launch_staged<A, 4>(psi, tp, stages, rops, dops, pool, status, st);
+    case 5:
+      if constexpr (sizeof(typename A::reg_t) <= 8) return launch_staged<A, 5>(psi, tp, stages, rops, dops, pool, status, st);
+      break;
+  }
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
 int tile_pass_smem_bytes(Policy pol, int L) {
-  const int reg = (pol == POL_F32) ? 8 : 16;
-  return (reg << L) + (8 << L) + 16;   // upper bound (segment table for c = 0)
+  const int e = (pol == POL_F32) ? 8 : 16;
+  return (e << L) + (16 << L) + 16;   // upper bound (padding for c = 0)
 }
 
-cudaError_t launch_tile_pass(Policy pol, void* psi, const TilePass& tp, const DevOp* ops_dev, const void* pool,
-                             int* status_dev, cudaStream_t s) {
+cudaError_t launch_tile_pass(Policy pol, void* psi, const TilePass& tp, const StageRec* stages_dev,
+                             const RegOp* regops_dev, const DevOp* ops_dev, const void* pool, int* status_dev,
+                             cudaStream_t s) {
+  if (tp.nst == 0) return cudaSuccess;
   switch (pol) {
-    case POL_F32: return launch_tile_t<AF32>(psi, tp, ops_dev, pool, status_dev, s);
-    case POL_F64: return launch_tile_t<AF64>(psi, tp, ops_dev, pool, status_dev, s);
-    case POL_DF: return launch_tile_t<ADF>(psi, tp, ops_dev, pool, status_dev, s);
+    case POL_F32: return launch_tile_t<AF32>(psi, tp, stages_dev, regops_dev, ops_dev, pool, status_dev, s);
+    case POL_F64: return launch_tile_t<AF64>(psi, tp, stages_dev, regops_dev, ops_dev, pool, status_dev, s);
+    case POL_DF: return launch_tile_t<ADF>(psi, tp, stages_dev, regops_dev, ops_dev, pool, status_dev, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -48,13 +48,39 @@ struct DevOp {
 };
 static_assert(sizeof(DevOp) == 64, "DevOp layout");
 
+// Register-stage op: a tile op whose target bits are held in registers.  Slots index the
+// stage's register bits; controls are split into register slots (csl) and tile bits
+// outside the registers (cot); gmask is the block predicate (storage bits outside the tile).
+struct RegOp {
+  int32_t type;       // OP_U1, OP_RX, OP_X, OP_DIAG, OP_PHASE, OP_U2
+  int8_t s0, s1;      // register slots of the target bit(s), -1 if none
+  int8_t tb;          // OP_DIAG on a tile bit outside the registers, -1 if none
+  int8_t neg;         // OP_PHASE: exact sign flip
+  uint32_t csl;       // control mask over register slots
+  uint32_t cot;       // control mask over tile-local bits outside the registers
+  int32_t mat;        // first pool entry
+  int32_t gbit;       // OP_DIAG on a storage bit outside the tile, -1 if none
+  uint64_t gmask;     // block predicate
+};
+static_assert(sizeof(RegOp) == 32, "RegOp layout");
+
+// A stage of a tile pass: either K tile bits held in registers by every thread (2^K
+// amplitudes per thread) with a list of RegOps, or a list of shared-memory DevOps.
+struct StageRec {
+  int32_t kind;       // 0 = register stage, 1 = shared-memory stage
+  int32_t op0, nops;  // RegOp range (kind 0) or DevOp range (kind 1)
+  int32_t rmask;      // kind 0: tile-local bits held in registers
+  int32_t rbits[8];   // kind 0: those bits in slot order
+};
+static_assert(sizeof(StageRec) == 48, "StageRec layout");
+
 // Tile pass launch description.
 struct TilePass {
   int32_t L;          // tile bits
   int32_t c;          // low storage bits of every segment (tpos[i] = i for i < c)
   int32_t n;
-  int32_t nops;
-  int32_t op0;        // first op in the plan's op array
+  int32_t K;          // register bits per thread in register stages
+  int32_t st0, nst;   // stage range in the plan's stage array
   int32_t tpos[kMaxTileBits];        // storage positions of tile bits, ascending
   int32_t npos[kMaxQubits];          // storage positions of the other bits, ascending
 };
@@ -76,8 +102,9 @@ struct Step {
 // ------------------------------------------------------------------------------------------
 cudaError_t launch_init_zero(void* psi, int n, int store_bytes, cudaStream_t s);
 cudaError_t launch_gate(Policy pol, void* psi, int n, const DevOp& op, const void* pool, cudaStream_t s);
-cudaError_t launch_tile_pass(Policy pol, void* psi, const TilePass& tp, const DevOp* ops_dev,
-                             const void* pool, int* status_dev, cudaStream_t s);
+cudaError_t launch_tile_pass(Policy pol, void* psi, const TilePass& tp, const StageRec* stages_dev,
+                             const RegOp* regops_dev, const DevOp* ops_dev, const void* pool, int* status_dev,
+                             cudaStream_t s);
 cudaError_t launch_permute(void* dst, const void* src, int n, int store_bytes, const int* src_of,
                            cudaStream_t s);
 cudaError_t launch_norm_partials(const void* psi, int n, int is_c128, double* partials, int nparts,
@@ -140,7 +167,9 @@ struct CompileResult {
   int store_bytes = 16;
   std::vector<Step> steps;
   std::vector<std::pair<int, int>> trace;   // QS_MODE_PAPER: (0 local gate | 1 non-local gate | 2 permute, value)
-  std::vector<DevOp> tile_ops;   // ops of all passes, concatenated
+  std::vector<DevOp> tile_ops;   // shared-memory ops of all passes, concatenated
+  std::vector<RegOp> reg_ops;    // register-stage ops of all passes
+  std::vector<StageRec> stages;  // stages of all passes
   Pool pool;
   std::vector<int> sigma_final;
   qs_plan_stats stats{};
@@ -151,7 +180,15 @@ bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<i
 // Dependency DAG with commutation-pruned edges: immediate predecessors per gate.
 std::vector<std::vector<int>> build_dag(const std::vector<HGate>& gates);
 
+// Thread-local error text returned by qs_last_error (capi.cpp).
+void set_last_error(const std::string& msg);
+
 int default_tile_bits(int dtype);
 int default_low_bits(int dtype);
+int register_bits(int dtype, int L);
+
+// Split a pass's op list (tile-local DevOps, program order) into register / shared-memory
+// stages with K register bits; appends to out->stages / reg_ops / tile_ops.
+void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* out, int* st0, int* nst);
 
 }  // namespace qs

@@ -1,0 +1,251 @@
+// Stage builder for tile passes: groups a pass's ops so that most of them run on
+// amplitudes held in registers.
+//
+// In a register stage every thread holds 2^K amplitudes of the tile -- those that differ
+// only in the stage's K register bits R -- and applies, in program order, every op whose
+// non-diagonal target bits lie in R; diagonal ops (phases, controls) apply to any bit.  A
+// stage costs one shared-memory round trip of the tile instead of one per gate.  R is
+// chosen like the pass's own bit set: greedily add the tile bit that lets one program-order
+// sweep schedule the most ops (ties: the bit the earliest ready op needs, then the lowest
+// bit).  Dense k-qubit blocks and SWAPs run as shared-memory stages.
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "qs_internal.h"
+
+namespace qs {
+
+namespace {
+
+struct OpInfo {
+  uint32_t need = 0;      // tile bits that must be in registers (non-diagonal targets)
+  bool smem_only = false; // dense / swap
+  int nb = 0;
+  int bit[8];
+  int cls[8];
+};
+
+OpInfo classify_op(const DevOp& o) {
+  OpInfo in;
+  auto add = [&](int b, int c) {
+    in.bit[in.nb] = b;
+    in.cls[in.nb] = c;
+    in.nb++;
+  };
+  const uint32_t cm = (uint32_t)o.cmask;
+  for (int b = 0; b < 32; b++)
+    if ((cm >> b) & 1u) add(b, CLS_Z);
+  switch (o.type) {
+    case OP_U1: add(o.k0, CLS_N); in.need = 1u << o.k0; break;
+    case OP_RX:
+    case OP_X: add(o.k0, CLS_X); in.need = 1u << o.k0; break;
+    case OP_DIAG: if (o.k0 >= 0) add(o.k0, CLS_Z); break;
+    case OP_PHASE: break;
+    case OP_U2: add(o.k0, CLS_N); add(o.k1, CLS_N); in.need = (1u << o.k0) | (1u << o.k1); break;
+    case OP_SWAP: add(o.k0, CLS_N); add(o.k1, CLS_N); in.smem_only = true; break;
+    case OP_DENSE:
+      for (int t = 0; t < o.nk; t++) add(o.kq[t], CLS_N);
+      in.smem_only = true;
+      break;
+    default: in.smem_only = true; break;
+  }
+  return in;
+}
+
+}  // namespace
+
+int register_bits(int dtype, int L) {
+  const int k = (dtype == QS_C128) ? 4 : 5;
+  return std::min(k, L);
+}
+
+void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* out, int* st0, int* nst) {
+  const int N = (int)ops.size();
+  std::vector<OpInfo> info(N);
+  for (int i = 0; i < N; i++) info[i] = classify_op(ops[i]);
+  // dependency DAG over tile bits (same grouping rule as the circuit DAG)
+  std::vector<std::vector<int>> preds(N);
+  struct BS {
+    int cls = -1;
+    std::vector<int> cur, prev;
+  };
+  std::vector<BS> bs(32);
+  for (int j = 0; j < N; j++) {
+    for (int t = 0; t < info[j].nb; t++) {
+      BS& s = bs[info[j].bit[t]];
+      const int c = info[j].cls[t];
+      if (s.cls >= 0 && c == s.cls && c != CLS_N) {
+        preds[j].insert(preds[j].end(), s.prev.begin(), s.prev.end());
+        s.cur.push_back(j);
+      } else {
+        preds[j].insert(preds[j].end(), s.cur.begin(), s.cur.end());
+        s.prev.swap(s.cur);
+        s.cur.assign(1, j);
+        s.cls = c;
+      }
+    }
+    std::sort(preds[j].begin(), preds[j].end());
+    preds[j].erase(std::unique(preds[j].begin(), preds[j].end()), preds[j].end());
+  }
+  std::vector<char> done(N, 0), tmp(N, 0);
+  std::vector<int> rem(N);
+  for (int i = 0; i < N; i++) rem[i] = i;
+  *st0 = (int)out->stages.size();
+  auto ready = [&](int v) {
+    for (int p : preds[v])
+      if (!done[p]) return false;
+    return true;
+  };
+  // ops one sweep schedules with register bits R (smem-only ops excluded)
+  auto closure = [&](uint32_t R) {
+    int cnt = 0;
+    for (int v : rem) {
+      bool ok = !info[v].smem_only && (info[v].need & ~R) == 0;
+      if (ok)
+        for (int p : preds[v])
+          if (!done[p] && !tmp[p]) {
+            ok = false;
+            break;
+          }
+      tmp[v] = ok;
+      cnt += ok;
+    }
+    for (int v : rem) tmp[v] = 0;
+    return cnt;
+  };
+  while (!rem.empty()) {
+    // the earliest ready op
+    int first = -1;
+    for (int v : rem)
+      if (ready(v)) {
+        first = v;
+        break;
+      }
+    StageRec st;
+    memset(&st, 0, sizeof(st));
+    std::vector<int> take;
+    if (info[first].smem_only || K < 1) {
+      st.kind = 1;
+      // every ready shared-memory-only op (in program order, with intra-stage chaining)
+      for (int v : rem) {
+        if (!info[v].smem_only && K >= 1) continue;
+        bool ok = true;
+        for (int p : preds[v])
+          if (!done[p] && !tmp[p]) {
+            ok = false;
+            break;
+          }
+        if (ok) {
+          tmp[v] = 1;
+          take.push_back(v);
+        }
+      }
+      for (int v : take) tmp[v] = 0;
+    } else {
+      st.kind = 0;
+      uint32_t R = 0;
+      int nr = 0;
+      // seed with the bits of the earliest ready op that needs registers
+      for (int v : rem)
+        if (!info[v].smem_only && info[v].need && ready(v)) {
+          R = info[v].need;
+          nr = __builtin_popcount(R);
+          break;
+        }
+      while (nr < K) {
+        int best = -1, best_s = -1, best_rank = 1 << 30;
+        for (int b = 0; b < L; b++) {
+          if ((R >> b) & 1u) continue;
+          const int s = closure(R | (1u << b));
+          // rank: position of the earliest remaining op needing b
+          int rank = 1 << 30;
+          for (size_t r = 0; r < rem.size(); r++)
+            if ((info[rem[r]].need >> b) & 1u) {
+              rank = (int)r;
+              break;
+            }
+          if (s > best_s || (s == best_s && rank < best_rank)) {
+            best = b;
+            best_s = s;
+            best_rank = rank;
+          }
+        }
+        R |= 1u << best;
+        nr++;
+      }
+      for (int v : rem) {
+        bool ok = !info[v].smem_only && (info[v].need & ~R) == 0;
+        if (ok)
+          for (int p : preds[v])
+            if (!done[p] && !tmp[p]) {
+              ok = false;
+              break;
+            }
+        if (ok) {
+          tmp[v] = 1;
+          take.push_back(v);
+        }
+      }
+      for (int v : take) tmp[v] = 0;
+      st.rmask = (int32_t)R;
+      int k = 0;
+      for (int b = 0; b < L; b++)
+        if ((R >> b) & 1u) st.rbits[k++] = b;
+    }
+    // emit
+    if (st.kind == 1) {
+      st.op0 = (int)out->tile_ops.size();
+      for (int v : take) out->tile_ops.push_back(ops[v]);
+      st.nops = (int)take.size();
+    } else {
+      int slot[32];
+      for (int b = 0; b < 32; b++) slot[b] = -1;
+      for (int k = 0; k < K; k++) slot[st.rbits[k]] = k;
+      const uint32_t R = (uint32_t)st.rmask;
+      st.op0 = (int)out->reg_ops.size();
+      for (int v : take) {
+        const DevOp& o = ops[v];
+        RegOp r;
+        memset(&r, 0, sizeof(r));
+        r.type = o.type;
+        r.s0 = r.s1 = r.tb = -1;
+        r.gbit = -1;
+        r.mat = o.mat;
+        r.gmask = o.gmask;
+        const uint32_t cm = (uint32_t)o.cmask;
+        for (int b = 0; b < 32; b++)
+          if ((cm >> b) & 1u) {
+            if ((R >> b) & 1u) r.csl |= 1u << slot[b];
+            else r.cot |= 1u << b;
+          }
+        switch (o.type) {
+          case OP_U1: case OP_RX: case OP_X: r.s0 = (int8_t)slot[o.k0]; break;
+          case OP_U2: r.s0 = (int8_t)slot[o.k0]; r.s1 = (int8_t)slot[o.k1]; break;
+          case OP_DIAG:
+            if (o.k0 >= 0) {
+              if ((R >> o.k0) & 1u) r.s0 = (int8_t)slot[o.k0];
+              else r.tb = (int8_t)o.k0;
+            } else {
+              r.gbit = o.gbit;
+            }
+            break;
+          case OP_PHASE: r.neg = (o.mat < 0) ? 1 : 0; break;
+          default: break;
+        }
+        out->reg_ops.push_back(r);
+      }
+      st.nops = (int)take.size();
+    }
+    out->stages.push_back(st);
+    for (int v : take) done[v] = 1;
+    size_t w = 0;
+    for (size_t r = 0; r < rem.size(); r++)
+      if (!done[rem[r]]) rem[w++] = rem[r];
+    rem.resize(w);
+  }
+  *nst = (int)out->stages.size() - *st0;
+}
+
+}  // namespace qs
