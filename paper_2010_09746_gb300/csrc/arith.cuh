@@ -193,14 +193,20 @@ struct ADF {
     dfl r = split_double(v.x), i = split_double(v.y);
     return make_float4(r.hi, r.lo, i.hi, i.lo);
   }
+  // register values are kept unnormalised between operations (hi need not be the rounded
+  // value of hi + lo); normalise once with TwoSum before the exact integer join
   static __device__ __forceinline__ store_t to_store(reg_t v) {
-    return make_double2(join_double(v.x, v.y), join_double(v.z, v.w));
+    const dfl r = two_sum(v.x, v.y), i = two_sum(v.z, v.w);
+    return make_double2(join_double(r.hi, r.lo), join_double(i.hi, i.lo));
   }
   static __device__ __forceinline__ reg_t zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
-  // Sum of two exact-ish products p0 + p1 where p_k = (a_k.hi + a_k.lo) * (b_k.hi + b_k.lo)
-  // (signs folded into the a's): TwoProduct of the high parts, first-order cross terms in
-  // FP32, TwoSum of the two leading terms, one renormalisation.
+  // Sum of two products p0 + p1 where p_k = (a_k.hi + a_k.lo) * (b_k.hi + b_k.lo) (signs
+  // folded into the a's): TwoProduct of the high parts, first-order cross terms in FP32,
+  // TwoSum of the two leading terms.  The result is left unnormalised (lo collects the
+  // TwoSum error and the first-order terms, |lo| ~ 2^-22 |hi|); the next operation uses lo
+  // only in first-order terms, so accuracy stays near 2^-44 relative, and to_store
+  // normalises before converting back to binary64.
   static __device__ __forceinline__ dfl dot2(float a0h, float a0l, float b0h, float b0l,
                                              float a1h, float a1l, float b1h, float b1l) {
     dfl p0 = two_prod(a0h, b0h);
@@ -211,7 +217,7 @@ struct ADF {
     err = __fmaf_rn(a1h, b1l, err);
     err = __fmaf_rn(a1l, b1h, err);
     dfl s = two_sum(p0.hi, p1.hi);
-    return fast_two_sum(s.hi, __fadd_rn(s.lo, err));
+    return {s.hi, __fadd_rn(s.lo, err)};
   }
   static __device__ __forceinline__ dfl dot4(float a0h, float a0l, float b0h, float b0l,
                                              float a1h, float a1l, float b1h, float b1l,
@@ -236,16 +242,14 @@ struct ADF {
     dfl s23 = two_sum(p2.hi, p3.hi);
     dfl s = two_sum(s01.hi, s23.hi);
     err = __fadd_rn(err, __fadd_rn(s01.lo, __fadd_rn(s23.lo, s.lo)));
-    return fast_two_sum(s.hi, err);
+    return {s.hi, err};
   }
   // acc + u*a (complex)
   static __device__ __forceinline__ reg_t mac(reg_t acc, mat_t u, reg_t a) {
     reg_t p = mul(u, a);
     dfl re = two_sum(acc.x, p.x);
     dfl im = two_sum(acc.z, p.z);
-    re = fast_two_sum(re.hi, __fadd_rn(re.lo, __fadd_rn(acc.y, p.y)));
-    im = fast_two_sum(im.hi, __fadd_rn(im.lo, __fadd_rn(acc.w, p.w)));
-    return make_float4(re.hi, re.lo, im.hi, im.lo);
+    return make_float4(re.hi, __fadd_rn(re.lo, __fadd_rn(acc.y, p.y)), im.hi, __fadd_rn(im.lo, __fadd_rn(acc.w, p.w)));
   }
   // u*a + v*b: re = u.re a.re - u.im a.im + v.re b.re - v.im b.im, im likewise
   static __device__ __forceinline__ reg_t mac2(mat_t u, reg_t a, mat_t v, reg_t b) {

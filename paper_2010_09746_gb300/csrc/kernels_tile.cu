@@ -392,6 +392,11 @@ __device__ __forceinline__ void apply_regop(typename A::reg_t (&x)[1 << K], cons
       }
       break;
     }
+    case OP_DTAB: {
+#pragma unroll
+      for (int j = 0; j < (1 << K); j++) x[j] = A::mul(m[j], x[j]);
+      break;
+    }
     case OP_PHASE: {
       if (op.neg) {
 #pragma unroll

@@ -34,6 +34,7 @@ enum OpType : int32_t {
   OP_U2 = 6,     // general 4x4 on bits (k0, k1), r = b(k0) + 2 b(k1)
   OP_DENSE = 7,  // general 2^nk x 2^nk on bits kq[0..nk-1]
   OP_SWAP = 8,   // exchange bits k0 and k1 (controls cmask)
+  OP_DTAB = 9,   // register stages only: multiply register element j by table entry j
 };
 
 struct DevOp {

@@ -54,6 +54,82 @@ OpInfo classify_op(const DevOp& o) {
   return in;
 }
 
+bool is_diag(const RegOp& r) { return r.type == OP_DIAG || r.type == OP_PHASE; }
+
+// register slots a diagonal op reads (its own slot and its slot controls)
+uint32_t diag_slots(const RegOp& r) {
+  uint32_t m = r.csl;
+  if (r.type == OP_DIAG && r.s0 >= 0) m |= 1u << r.s0;
+  return m;
+}
+uint32_t target_slots(const RegOp& r) {
+  uint32_t m = 0;
+  if (r.s0 >= 0) m |= 1u << r.s0;
+  if (r.type == OP_U2 && r.s1 >= 0) m |= 1u << r.s1;
+  return m;
+}
+// a factor that depends on the register slots only (no group or block dependence)
+bool slot_only(const RegOp& r) {
+  if (!is_diag(r) || r.cot != 0 || r.gmask != 0) return false;
+  if (r.type == OP_DIAG) return r.s0 >= 0;
+  return true;
+}
+
+// Hoist every diagonal op left past the non-diagonal ops it commutes with (those whose
+// target slots it does not touch), then replace each run of two or more slot-only diagonal
+// factors by one table op: entry j of a 2^K-entry table is the product of the run's
+// factors at register index j (computed on the host in FP64).
+void merge_diagonals(std::vector<RegOp>& rl, int K, Pool& pool) {
+  for (size_t i = 1; i < rl.size(); i++) {
+    if (!is_diag(rl[i])) continue;
+    size_t j = i;
+    while (j > 0 && !is_diag(rl[j - 1]) && (target_slots(rl[j - 1]) & diag_slots(rl[j])) == 0) {
+      std::swap(rl[j - 1], rl[j]);
+      j--;
+    }
+  }
+  std::vector<RegOp> out;
+  size_t i = 0;
+  const int D = 1 << K;
+  while (i < rl.size()) {
+    if (!is_diag(rl[i])) {
+      out.push_back(rl[i++]);
+      continue;
+    }
+    size_t e = i;
+    while (e < rl.size() && is_diag(rl[e])) e++;
+    std::vector<RegOp> fac, rest;
+    for (size_t k = i; k < e; k++) (slot_only(rl[k]) ? fac : rest).push_back(rl[k]);
+    if (fac.size() >= 2) {
+      std::vector<cd> tab(D, cd(1, 0));
+      for (const RegOp& r : fac) {
+        for (int j = 0; j < D; j++) {
+          if (((uint32_t)j & r.csl) != r.csl) continue;
+          if (r.type == OP_DIAG) {
+            const int m = r.mat + (((j >> r.s0) & 1) ? 1 : 0);
+            tab[j] *= cd(pool.f64[2 * m], pool.f64[2 * m + 1]);
+          } else {
+            tab[j] *= r.neg ? cd(-1, 0) : cd(pool.f64[2 * r.mat], pool.f64[2 * r.mat + 1]);
+          }
+        }
+      }
+      RegOp t;
+      memset(&t, 0, sizeof(t));
+      t.type = OP_DTAB;
+      t.s0 = t.s1 = t.tb = -1;
+      t.gbit = -1;
+      t.mat = (int)pool.entries();
+      for (int j = 0; j < D; j++) pool.add(tab[j]);
+      out.push_back(t);
+    } else {
+      rest.insert(rest.begin(), fac.begin(), fac.end());
+    }
+    out.insert(out.end(), rest.begin(), rest.end());
+    i = e;
+  }
+  rl.swap(out);
+}
+
 }  // namespace
 
 int register_bits(int dtype, int L) {
@@ -204,7 +280,7 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
       for (int b = 0; b < 32; b++) slot[b] = -1;
       for (int k = 0; k < K; k++) slot[st.rbits[k]] = k;
       const uint32_t R = (uint32_t)st.rmask;
-      st.op0 = (int)out->reg_ops.size();
+      std::vector<RegOp> rl;
       for (int v : take) {
         const DevOp& o = ops[v];
         RegOp r;
@@ -234,9 +310,12 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
           case OP_PHASE: r.neg = (o.mat < 0) ? 1 : 0; break;
           default: break;
         }
-        out->reg_ops.push_back(r);
+        rl.push_back(r);
       }
-      st.nops = (int)take.size();
+      merge_diagonals(rl, K, out->pool);
+      st.op0 = (int)out->reg_ops.size();
+      out->reg_ops.insert(out->reg_ops.end(), rl.begin(), rl.end());
+      st.nops = (int)rl.size();
     }
     out->stages.push_back(st);
     for (int v : take) done[v] = 1;
