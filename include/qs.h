@@ -243,6 +243,27 @@ qs_status qs_set_amplitudes(qs_handle h, const void* in);
  * Synchronises the stream. */
 qs_status qs_norm(qs_handle h, double* out);
 
+/* ---- allocation-free read-out (no counterpart in the paper) ------------------------- *
+ *
+ * FP64 norm sum_j |psi[j]|^2 of a state vector the caller owns, written to *out_dev (a
+ * device double), computed by the same fixed-order reduction as qs_norm, so the two agree
+ * bit for bit.  For callers that may not allocate device memory: a host program that has
+ * already divided the whole GPU among its own buffers and allows no further allocation, or
+ * a latency-critical loop that must not enter the allocator.  The call allocates nothing:
+ * the reduction's 1216 partial sums live in one fixed device array (9.5 KiB) that every GPU
+ * loading the library keeps until the process exits.
+ *   psi      device pointer to 2^n interleaved (re, im) elements of `dtype`
+ *   n        1..36; larger states are rejected with QS_EINVAL (the limit of the library)
+ *   out_dev  device pointer to one double; written asynchronously on `stream`
+ *   stream   cudaStream_t (NULL = the legacy default stream)
+ * The first call on each device looks up the device address of the fixed array
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture begins.  All calls share the one array and each call overwrites all of it, so
+ * calls whose kernels overlap on the GPU (different streams, no ordering) race and give
+ * wrong results; calls on one stream are safe.  Asynchronous: synchronise the stream
+ * before reading *out_dev. */
+qs_status qs_norm_noalloc(const void* psi, int n, qs_dtype dtype, double* out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -89,6 +89,7 @@ SIGNATURES = {
     "qs_get_amplitudes": (_I, [_H, _P, ctypes.c_uint64, ctypes.c_uint64, _I]),
     "qs_set_amplitudes": (_I, [_H, _P]),
     "qs_norm": (_I, [_H, _DP]),
+    "qs_norm_noalloc": (_I, [_P, _I, _I, _P, _P]),
 }
 
 _lib = None
