@@ -5,11 +5,14 @@ Workload (default): 30 qubits, complex128 (16 GiB state), 40 layers of RZ(U(0,2p
 RX(U(0,2pi)) on every qubit followed by floor(n/4) CZ on pairs biased toward high qubits
 (seed 0; 2680 gates).  One step = state preparation |0..0> + the compiled circuit (tile
 passes, and permutations / per-gate kernels where the mode uses them) + the FP64 norm
-read-out.  The plan is compiled before the timed region; `e2e` re-compiles from host
-buffers every step and copies inputs / results over PCIe/C2C inside its timed region.
+read-out.  The plan is compiled before the timed region; `e2e` compiles from host buffers
+every step and copies inputs / results between host and device inside its timed region.
 
 `value` = circuit gates / device-timed step time (CUDA events on the library's stream),
-whole job.  The state (16 GiB) is far larger than L2 (129 MB), so no flush is needed.
+whole job (sum over replicas).  The state (16 GiB) is far larger than L2 (129 MB), so no
+flush is needed between steps.  `modes` reports the same circuit without the reordering
+pass (one kernel per gate, measured on the first 4 layers) and with the paper's
+Algorithm 1 (m = 12 local qubits, one transposition per PermuteQubits).
 
 `--impl reference` times the FP64 CPU oracle (test infrastructure) on this host's cores on
 a bounded sample of the same workload (the first gates of the same circuit on the same
@@ -24,37 +27,34 @@ import sys
 import threading
 import time
 
-import numpy as np
-
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from workloads import circuits as wc  # noqa: E402
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+N_SM = 152
+FP32_LANES = 128        # FP32 FMA-pipe instructions per clock per SM
+FP64_PER_CLK = 1.7      # DFMA per clock per SM, measured (probe of this machine's GB300)
 
 
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
-            d = json.load(f)
-        return d, "measured"
+            return json.load(f), "measured"
     return PEAKS_FALLBACK, "fallback"
 
 
 def workload(args):
     if args.workload == "rzrx30":
-        n, layers = args.n, args.layers
-        circ = wc.rzrx_cz_circuit(n, layers, seed=args.seed)
-        name = f"rzrx_cz_{n}q_{layers}layers_{args.dtype}"
-    elif args.workload == "haar12":
-        n = 12
+        circ = wc.rzrx_cz_circuit(args.n, args.layers, seed=args.seed)
+        name = f"rzrx_cz_{args.n}q_{args.layers}layers_{args.dtype}"
+        return args.n, circ, name
+    if args.workload == "haar12":
         circ = wc.haar_cnot_circuit(12, 20, seed=args.seed)
-        name = f"haar_cnot_12q_20layers_{args.dtype}"
-    else:
-        raise SystemExit(f"unknown workload {args.workload}")
-    return n, circ, name
+        return 12, circ, f"haar_cnot_12q_20layers_{args.dtype}"
+    raise SystemExit(f"unknown workload {args.workload}")
 
 
 class ClockSampler:
@@ -73,8 +73,7 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+            threading.Thread(target=self._read, daemon=True).start()
         except Exception:  # noqa: BLE001
             self.proc = None
 
@@ -108,17 +107,87 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup(args):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+def dist_env():
+    return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def reduce_max(value, pg):
+    """Max over ranks (the slowest replica sets the whole job's time)."""
+    if pg is None:
+        return float(value)
+    import torch
+    dev = "cuda" if pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, max_ms):
+    """Whole-job throughput: every rank processed `units_per_rank`; time = slowest rank."""
+    return world * units_per_rank / (max_ms / 1e3)
+
+
+def roofline(kstats, steps, step_ms, peaks, peaks_kind, policy, clk_mhz):
+    if not kstats:
+        return None
+    dom = max(kstats, key=lambda k: k["total_ms"])
+    per_launch_ms = dom["total_ms"] / dom["launches"]
+    bytes_pl = dom["bytes"] / dom["launches"]
+    alu_pl = dom["alu"] / dom["launches"]
+    hbm = bytes_pl / (per_launch_ms * 1e-3) / 1e9
+    out = {"kernel": dom["name"], "launches_per_step": dom["launches"] / steps,
+           "ms_per_launch": round(per_launch_ms, 4), "share_of_step": round(dom["total_ms"] / steps / step_ms, 4),
+           "hbm": {"achieved": round(hbm, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                   "frac": round(hbm / peaks["hbm_gbs"], 4), "peak_source": f"{peaks_kind} hbm_gbs"}}
+    # ALU roofline: instructions the arithmetic's formulas need / time, against the
+    # pipe's issue rate at the maximum SM clock
+    f = 2070.0
+    if policy == "f64":
+        peak_alu = N_SM * FP64_PER_CLK * f * 1e6 / 1e12
+        unit = "T DFMA/s"
+    else:
+        peak_alu = N_SM * FP32_LANES * f * 1e6 / 1e12
+        unit = "T FP32-inst/s"
+    alu = alu_pl / (per_launch_ms * 1e-3) / 1e12
+    out["alu"] = {"achieved": round(alu, 3), "peak": round(peak_alu, 2), "unit": unit,
+                  "frac": round(alu / peak_alu, 4),
+                  "peak_source": f"{N_SM} SMs x {FP32_LANES if policy != 'f64' else FP64_PER_CLK}/clk x 2070 MHz"}
+    bound = "alu" if out["alu"]["frac"] > out["hbm"]["frac"] else "hbm"
+    sel = out[bound]
+    out.update({"bound": bound, "achieved": sel["achieved"], "peak": sel["peak"], "unit": sel["unit"],
+                "frac": sel["frac"], "traffic": None})
+    return out
+
+
+def measure(qs, st, plan, steps, warmup, torch, stream, profile=False):
+    def step():
+        st.reset()
+        st.execute(plan)
+        return st.norm()
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    if profile:
+        st.set_profiling(True)
+        st.reset_kernel_stats()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    norms = [step() for _ in range(steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ks = st.kernel_stats() if profile else []
+    if profile:
+        st.set_profiling(False)
+    return e0.elapsed_time(e1) / steps, norms, ks
 
 
 def run_ours(args):
     import torch
 
-    world, rank, local = dist_setup(args)
+    world, rank, local = dist_env()
     torch.cuda.set_device(local)
     pg = None
     if world > 1:
@@ -131,105 +200,76 @@ def run_ours(args):
     n, circ, name = workload(args)
     G = len(circ)
     stream = torch.cuda.Stream(device=local)
+    policy = {"c64": "f32", "c128": ("f64" if args.arith == "f64" else "df")}[args.dtype]
     st = qs.State(n, args.dtype, arith=args.arith, stream=stream)
     plan = qs.compile(n, circ, mode=args.mode, dtype=args.dtype, arith=args.arith, tile_bits=args.tile_bits,
-                      low_bits=args.low_bits)
+                      low_bits=args.low_bits, reg_bits=args.reg_bits)
     pstats = plan.stats()
 
-    def step():
-        st.reset()
-        st.execute(plan)
-        return st.norm()
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
     if pg:
         pg.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    st.set_profiling(True)
-    st.reset_kernel_stats()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    norms = []
-    for _ in range(args.steps):
-        norms.append(step())
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    kstats = st.kernel_stats()
-    st.set_profiling(False)
+    ms, norms, kstats = measure(qs, st, plan, args.steps, args.warmup, torch, stream, profile=True)
     clk = clocks.stop()
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * G / (ms / 1e3)
+    ms = reduce_max(ms, pg)
+    value = job_rate(G, world, ms)
+
+    peaks, peaks_kind = load_peaks()
+    roof = roofline(kstats, args.steps, ms, peaks, peaks_kind, policy, clk.get("sm_mhz"))
+    launches = int(round(sum(k["launches"] for k in kstats)))
+    total_bytes = pstats["hbm_bytes"] + (1 << n) * (16 if args.dtype == "c128" else 8) * 2  # + init, norm
+    out = {
+        "metric": "30q random-circuit gates/s & % HBM roofline",
+        "value": round(value, 2), "unit": "gates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": policy, "data": "synthetic (seeded random circuit)",
+        "config": {"workload": name, "n_qubits": n, "gates": G, "mode": args.mode, "state_dtype": args.dtype,
+                   "arith": policy, "tile_bits": args.tile_bits or None, "low_bits": args.low_bits or None,
+                   "reg_bits": args.reg_bits or None,
+                   "passes": pstats["n_passes"], "permutes": pstats["n_permutes"], "pergate": pstats["n_pergate"],
+                   "parallelism": f"replicas{world}",
+                   "l2": "state 16 GiB >> 129 MB L2, no flush needed" if n >= 27 else "state small vs L2"},
+        "hbm_frac_step": round(total_bytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+        "norm_max_dev": max(abs(x - 1.0) for x in norms),
+        "compile_ms": round(pstats["compile_ms"], 2),
+        "roofline": roof, "gpu_launches": launches, "kernels": kstats, "clocks": clk,
+    }
 
     # ---- e2e: host circuit -> compile -> execute -> read back, every step
-    e2e = None
     if not args.no_e2e:
         ops, nops, mats = qs.marshal(circ)
         h2d = nops * 48 + mats.nbytes
         readout = 1 << min(n, 16)
         d2h = readout * (16 if args.dtype == "c128" else 8) + 8
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
         e2e_steps = max(1, min(args.steps, 3))
+        t0 = time.perf_counter()
         for _ in range(e2e_steps):
             st.reset()
-            st.run(circ, mode=args.mode, tile_bits=args.tile_bits, low_bits=args.low_bits)
+            st.run(circ, mode=args.mode, tile_bits=args.tile_bits, low_bits=args.low_bits, reg_bits=args.reg_bits)
             st.amplitudes(0, readout)
             st.norm()
         torch.cuda.synchronize()
-        t_e2e = (time.perf_counter() - t0) / e2e_steps
-        if pg:
-            t = torch.tensor([t_e2e], device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": world * G / t_e2e, "unit": "gates/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": t_e2e * 1e3}
+        t_e2e = reduce_max((time.perf_counter() - t0) / e2e_steps * 1e3, pg)
+        out["e2e"] = {"value": round(job_rate(G, world, t_e2e), 2), "unit": "gates/s", "h2d_bytes_per_step": int(h2d),
+                      "d2h_bytes_per_step": int(d2h), "ms_per_step": round(t_e2e, 3)}
 
-    # ---- roofline of the dominant kernel (per-launch CUDA events on the library stream)
-    peaks, peaks_kind = load_peaks()
-    dom = max(kstats, key=lambda k: k["total_ms"]) if kstats else None
-    roof = None
-    if dom:
-        per_launch_ms = dom["total_ms"] / dom["launches"]
-        bytes_per_launch = dom["bytes"] / dom["launches"]
-        achieved = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9
-        peak = peaks["hbm_gbs"]
-        roof = {"kernel": dom["name"], "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_source": f"{peaks_kind} hbm_gbs",
-                "launches_per_step": dom["launches"] / args.steps,
-                "ms_per_launch": round(per_launch_ms, 4),
-                "share_of_step": round(dom["total_ms"] / args.steps / ms, 4)}
-    launches = int(sum(k["launches"] for k in kstats) / args.steps * args.steps)
-    total_bytes = pstats["hbm_bytes"] + (1 << n) * (16 if args.dtype == "c128" else 8) * 2  # + init write + norm read
-    hbm_frac_step = total_bytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]
-
-    norm_err = max(abs(x - 1.0) for x in norms)
-    out = {
-        "metric": "30q random-circuit gates/s & % HBM roofline",
-        "value": round(value, 2), "unit": "gates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"c128": ("df" if args.arith in ("auto", "df") else "f64"), "c64": "f32"}[args.dtype],
-        "data": "synthetic (seeded random circuit)",
-        "config": {"workload": name, "n_qubits": n, "gates": G, "mode": args.mode, "state_dtype": args.dtype,
-                   "tile_bits": args.tile_bits or None, "low_bits": args.low_bits or None,
-                   "passes": pstats["n_passes"], "permutes": pstats["n_permutes"], "pergate": pstats["n_pergate"],
-                   "parallelism": f"replicas{world}", "l2": "state 16 GiB >> 129 MB L2, no flush needed"
-                   if n >= 27 else "state fits in L2 (launch-bound workload)"},
-        "hbm_frac_step": round(hbm_frac_step, 4),
-        "norm_max_dev": norm_err,
-        "compile_ms": round(pstats["compile_ms"], 2),
-        "roofline": roof, "e2e": e2e, "gpu_launches": launches, "kernels": kstats,
-        "clocks": clk,
-    }
+    # ---- the same circuit without the reordering pass, and with the paper's Algorithm 1
+    if args.modes and args.mode == "tile":
+        modes = {"tile": {"gates_per_s": out["value"] / world, "passes": pstats["n_passes"]}}
+        per_layer = 2 * n + n // 4 if args.workload == "rzrx30" else len(circ) // 20
+        sub = circ[: 4 * per_layer]   # first 4 layers
+        p_pg = qs.compile(n, sub, mode="pergate", dtype=args.dtype, arith=args.arith)
+        ms_pg, _, _ = measure(qs, st, p_pg, 1, 1, torch, stream)
+        modes["pergate"] = {"gates_per_s": round(len(sub) / (ms_pg / 1e3), 2), "sample": f"first {len(sub)} gates",
+                            "kernels": p_pg.stats()["n_pergate"]}
+        p_pa = qs.compile(n, circ, mode="paper", dtype=args.dtype, arith=args.arith, tile_bits=12)
+        ms_pa, _, _ = measure(qs, st, p_pa, 1, 1, torch, stream)
+        s_pa = p_pa.stats()
+        modes["paper_alg1_m12"] = {"gates_per_s": round(G / (ms_pa / 1e3), 2), "passes": s_pa["n_passes"],
+                                   "permutes": s_pa["n_permutes"], "nonlocal_gates": s_pa["n_comm_gates"]}
+        out["modes"] = modes
     if args.cpu_baseline and rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(args, n, circ)
     if pg:
@@ -255,23 +295,17 @@ def cpu_baseline(args, n, circ, budget_s=None):
 
 
 def run_reference(args):
-    world, rank, _ = dist_setup(args)
+    world, rank, _ = dist_env()
     if rank != 0:
         return None, rank
     n, circ, name = workload(args)
     from oracle import sv
     sv.lib()
-    # each step: a bounded sample of the workload
     per_step = max(1.0, args.cpu_budget_s / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         cpu_baseline(args, n, circ, budget_s=per_step)
-    vals = []
-    samples = []
-    for _ in range(args.steps):
-        r = cpu_baseline(args, n, circ, budget_s=per_step)
-        vals.append(r["value"])
-        samples.append(r["sample"])
-    v = statistics.median(vals)
+    runs = [cpu_baseline(args, n, circ, budget_s=per_step) for _ in range(args.steps)]
+    v = statistics.median(r["value"] for r in runs)
     out = {
         "impl": "reference", "metric": "30q random-circuit gates/s & % HBM roofline", "value": v,
         "unit": "gates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -280,13 +314,13 @@ def run_reference(args):
         "config": {"workload": name, "n_qubits": n, "gates": len(circ), "mode": "oracle (per gate, FP64, CPU)",
                    "parallelism": "host cores"},
         "cpu_baseline": {"value": v, "unit": "gates/s", "cores": sv.num_threads(), "kind": "oracle",
-                         "sample": samples[0]},
+                         "sample": runs[0]["sample"]},
         "e2e": {"value": v, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     return out, rank
 
 
-def main():
+def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -301,11 +335,12 @@ def main():
     ap.add_argument("--mode", default="tile", choices=["tile", "paper", "pergate"])
     ap.add_argument("--tile-bits", type=int, default=0)
     ap.add_argument("--low-bits", type=int, default=0)
+    ap.add_argument("--reg-bits", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--modes", type=int, default=1, help="also time per-gate and Algorithm 1 modes")
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
-    ap.add_argument("--extra", default="", help="comma list of extra measurements: pergate,paper,c64")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     if args.impl == "reference":
         out, rank = run_reference(args)
     else:

@@ -107,6 +107,9 @@ typedef struct {
   int32_t max_ops;    /* cap on gates per tile pass, 0 = none */
   int32_t scoring;    /* Algorithm 1 candidate score: 0 = closure (default), 1 = frontier */
   int32_t flags;      /* reserved, must be 0 */
+  int32_t reg_bits;   /* tile bits each thread holds in registers in a register stage (2^reg_bits
+                         amplitudes per thread), 1..5 (complex128 1..4); 0 = default (4 for
+                         complex128, 5 for complex64) */
 } qs_compile_opts;
 
 typedef struct {
@@ -116,6 +119,9 @@ typedef struct {
   int64_t n_permutes;     /* permutation kernels */
   int64_t n_comm_gates;   /* QS_MODE_PAPER: gates executed non-locally */
   double hbm_bytes;       /* algorithmic HBM bytes of one execution (reads + writes) */
+  double alu_instr;       /* arithmetic instructions of one execution as the arithmetic's
+                             formulas count them (FP32 FMA-pipe instructions for complex64 and
+                             double-float, DFMA for native FP64), all amplitudes */
   double compile_ms;      /* host time spent compiling */
 } qs_plan_stats;
 
@@ -125,6 +131,7 @@ typedef struct {
   int64_t launches;
   double total_ms;        /* sum of CUDA-event durations on the state's stream */
   double bytes;           /* algorithmic HBM bytes of those launches */
+  double alu;             /* arithmetic instructions of those launches (see qs_plan_stats) */
 } qs_kernel_stat;
 
 /* ---- library ------------------------------------------------------------------------ */
@@ -221,6 +228,45 @@ qs_status qs_execute(qs_handle h, qs_plan_t p);
 /* qs_compile + qs_execute + qs_plan_destroy. */
 qs_status qs_run(qs_handle h, const qs_op* ops, size_t nops, const double* mats, size_t nmats,
                  const qs_compile_opts* opts);
+
+/* ---- batches of independent circuits ----------------------------------------------- *
+ * Many small circuits (each its own state) run together: every circuit is compiled as by
+ * qs_compile in QS_MODE_TILE, and "wave" w -- pass w of every circuit that has one -- is one
+ * persistent kernel launch over all those passes' tiles.  After the first (eager) run the
+ * sequence init -> waves -> per-circuit norms is replayed from a captured CUDA graph when a
+ * non-default stream is set.  A circuit's amplitudes are bitwise those of a solo qs_execute
+ * with the same options. */
+typedef struct qs_batch* qs_batch_t;
+
+typedef struct {
+  int64_t n_circuits;
+  int64_t n_gates;
+  int64_t n_passes;       /* tile passes over all circuits */
+  int64_t n_waves;        /* launches per run (plus init and norms) */
+  double state_bytes;     /* device bytes of all states */
+  double hbm_bytes;       /* algorithmic bytes of one run's passes */
+  double alu_instr;       /* arithmetic instructions of one run's passes (see qs_plan_stats) */
+  double compile_ms;
+} qs_batch_stats;
+
+/* count circuits; circuit i has n[i] qubits (1..30) and the ops ops[op_offsets[i] ..
+ * op_offsets[i+1]) whose matrix offsets index `mats`.  opts: mode must be QS_MODE_TILE (or
+ * opts NULL: complex64, defaults); tile_bits is capped at each circuit's n. */
+qs_status qs_batch_create(int count, const int* n, const qs_op* ops, const int64_t* op_offsets,
+                          const double* mats, size_t nmats, const qs_compile_opts* opts, qs_batch_t* out);
+qs_status qs_batch_set_stream(qs_batch_t b, void* stream);
+/* 1 (default) = replay a captured graph from the second run on a non-default stream. */
+qs_status qs_batch_set_graph(qs_batch_t b, int on);
+/* Enqueue one run: every state to |0...0>, every circuit, every norm.  Asynchronous. */
+qs_status qs_batch_run(qs_batch_t b);
+/* Wait for the batch's stream; QS_ETIMEOUT if a device-side wait expired. */
+qs_status qs_batch_sync(qs_batch_t b);
+/* FP64 norm of every state after the last run (count doubles, host). */
+qs_status qs_batch_norms(qs_batch_t b, double* out);
+/* Amplitudes first .. first+count-1 of circuit i (storage = logical order), host memory. */
+qs_status qs_batch_get_amplitudes(qs_batch_t b, int i, void* out, uint64_t first, uint64_t count);
+qs_status qs_batch_get_stats(qs_batch_t b, qs_batch_stats* out);
+qs_status qs_batch_destroy(qs_batch_t b);
 
 /* ---- read-outs (Sec. 2: measurement) ------------------------------------------------ */
 

@@ -74,7 +74,7 @@ def marshal(circuit: Iterable):
     return ops, len(gates), np.ascontiguousarray(buf, dtype=np.float64)
 
 
-def _opts(mode="tile", dtype="c128", arith="auto", tile_bits=0, low_bits=0, max_ops=0, scoring=0):
+def _opts(mode="tile", dtype="c128", arith="auto", tile_bits=0, low_bits=0, max_ops=0, scoring=0, reg_bits=0):
     o = _lib.qs_compile_opts()
     o.mode = _MODES[mode]
     o.dtype = _DTYPES[dtype]
@@ -84,6 +84,7 @@ def _opts(mode="tile", dtype="c128", arith="auto", tile_bits=0, low_bits=0, max_
     o.max_ops = max_ops
     o.scoring = scoring
     o.flags = 0
+    o.reg_bits = reg_bits
     return o
 
 
@@ -187,7 +188,7 @@ class State:
         buf = (_lib.qs_kernel_stat * 64)()
         _lib.check(_L().qs_get_kernel_stats(self._h, buf, 64, ctypes.byref(cnt)))
         return [{"name": buf[i].name.decode(), "launches": buf[i].launches, "total_ms": buf[i].total_ms,
-                 "bytes": buf[i].bytes} for i in range(min(cnt.value, 64))]
+                 "bytes": buf[i].bytes, "alu": buf[i].alu} for i in range(min(cnt.value, 64))]
 
     def reset_kernel_stats(self):
         _lib.check(_L().qs_reset_kernel_stats(self._h))

@@ -29,18 +29,24 @@ class qs_op(ctypes.Structure):
 class qs_compile_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("dtype", ctypes.c_int32), ("arith", ctypes.c_int32),
                 ("tile_bits", ctypes.c_int32), ("low_bits", ctypes.c_int32), ("max_ops", ctypes.c_int32),
-                ("scoring", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("scoring", ctypes.c_int32), ("flags", ctypes.c_int32), ("reg_bits", ctypes.c_int32)]
 
 
 class qs_plan_stats(ctypes.Structure):
     _fields_ = [("n_gates", ctypes.c_int64), ("n_passes", ctypes.c_int64), ("n_pergate", ctypes.c_int64),
                 ("n_permutes", ctypes.c_int64), ("n_comm_gates", ctypes.c_int64), ("hbm_bytes", ctypes.c_double),
-                ("compile_ms", ctypes.c_double)]
+                ("alu_instr", ctypes.c_double), ("compile_ms", ctypes.c_double)]
 
 
 class qs_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double),
-                ("bytes", ctypes.c_double)]
+                ("bytes", ctypes.c_double), ("alu", ctypes.c_double)]
+
+
+class qs_batch_stats(ctypes.Structure):
+    _fields_ = [("n_circuits", ctypes.c_int64), ("n_gates", ctypes.c_int64), ("n_passes", ctypes.c_int64),
+                ("n_waves", ctypes.c_int64), ("state_bytes", ctypes.c_double), ("hbm_bytes", ctypes.c_double),
+                ("alu_instr", ctypes.c_double), ("compile_ms", ctypes.c_double)]
 
 
 assert ctypes.sizeof(qs_op) == 48
@@ -90,6 +96,16 @@ SIGNATURES = {
     "qs_set_amplitudes": (_I, [_H, _P]),
     "qs_norm": (_I, [_H, _DP]),
     "qs_norm_noalloc": (_I, [_P, _I, _I, _P, _P]),
+    "qs_batch_create": (_I, [_I, _IP, ctypes.POINTER(qs_op), ctypes.POINTER(ctypes.c_int64), _DP, ctypes.c_size_t,
+                             ctypes.POINTER(qs_compile_opts), ctypes.POINTER(_H)]),
+    "qs_batch_set_stream": (_I, [_H, _P]),
+    "qs_batch_set_graph": (_I, [_H, _I]),
+    "qs_batch_run": (_I, [_H]),
+    "qs_batch_sync": (_I, [_H]),
+    "qs_batch_norms": (_I, [_H, _DP]),
+    "qs_batch_get_amplitudes": (_I, [_H, _I, _P, ctypes.c_uint64, ctypes.c_uint64]),
+    "qs_batch_get_stats": (_I, [_H, ctypes.POINTER(qs_batch_stats)]),
+    "qs_batch_destroy": (_I, [_H]),
 }
 
 _lib = None

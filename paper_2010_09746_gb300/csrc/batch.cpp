@@ -1,0 +1,338 @@
+// Batches of independent circuits: one state buffer, one compiled plan per circuit, and
+// "waves" of tile passes -- wave w runs pass w of every circuit that has one -- each wave a
+// single persistent launch over all its passes' blocks.  After a first eager run the whole
+// sequence (init, waves, per-circuit norms) is captured into a CUDA graph and replayed.
+// A circuit's tile passes are compiled exactly as qs_compile compiles them and run through
+// the same per-block code, so every amplitude is bitwise the value a solo qs_execute gives.
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <string>
+#include <vector>
+
+#include "qs_internal.h"
+
+using namespace qs;
+
+namespace qs {
+cudaError_t launch_batch_init(void* psi, int store_bytes, const uint64_t* offs, int count, size_t total_elems,
+                              cudaStream_t s);
+cudaError_t launch_batch_norms(const void* psi, int is_c128, const uint64_t* offs, const int* ns, int count,
+                               double* out, cudaStream_t s);
+}  // namespace qs
+
+struct qs_batch {
+  int count = 0;
+  qs_dtype dtype = QS_C64;
+  Policy pol = POL_F32;
+  int K = 0;
+  int store_bytes = 8;
+  std::vector<int> n;
+  std::vector<uint64_t> off;       // element offset of each state
+  size_t total_elems = 0;
+  // concatenated plan data
+  std::vector<StageRec> stages;
+  std::vector<RegOp> rops;
+  std::vector<DevOp> dops;
+  Pool pool;
+  struct Wave {
+    std::vector<BatchPass> passes;
+    std::vector<uint64_t> prefix;
+    int maxL = 0, minc = 64;
+    size_t pass_off = 0, prefix_off = 0;   // into the device arrays
+  };
+  std::vector<Wave> waves;
+  qs_batch_stats stats{};
+  // device
+  void* psi = nullptr;
+  StageRec* stages_d = nullptr;
+  RegOp* rops_d = nullptr;
+  DevOp* dops_d = nullptr;
+  void* pool_d = nullptr;
+  BatchPass* passes_d = nullptr;
+  uint64_t* prefix_d = nullptr;
+  uint64_t* off_d = nullptr;
+  int* n_d = nullptr;
+  double* norms_d = nullptr;
+  int* status_d = nullptr;
+  std::vector<void*> allocs;
+  cudaStream_t stream = nullptr;
+  bool use_graph = true;
+  int runs = 0;
+  cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+template <class T>
+T* upload(qs_batch* b, const std::vector<T>& v, cudaError_t* e) {
+  if (v.empty() || *e != cudaSuccess) return nullptr;
+  void* p = nullptr;
+  *e = cudaMalloc(&p, v.size() * sizeof(T));
+  if (*e != cudaSuccess) return nullptr;
+  b->allocs.push_back(p);
+  *e = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return (T*)p;
+}
+
+qs_status bfail(qs_status s, const std::string& m) {
+  set_last_error(m);
+  return s;
+}
+
+cudaError_t enqueue(qs_batch* b) {
+  cudaError_t e = launch_batch_init(b->psi, b->store_bytes, b->off_d, b->count, b->total_elems, b->stream);
+  for (const auto& w : b->waves) {
+    if (e != cudaSuccess) break;
+    e = launch_tile_batched(b->pol, b->K, b->psi, b->passes_d + w.pass_off, b->prefix_d + w.prefix_off,
+                            (int)w.passes.size(), w.prefix.back(), w.maxL, w.minc, b->stages_d, b->rops_d, b->dops_d,
+                            b->pool_d, b->status_d, b->stream);
+  }
+  if (e == cudaSuccess)
+    e = launch_batch_norms(b->psi, b->dtype == QS_C128, b->off_d, b->n_d, b->count, b->norms_d, b->stream);
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+qs_status qs_batch_create(int count, const int* n, const qs_op* ops, const int64_t* op_offsets, const double* mats,
+                          size_t nmats, const qs_compile_opts* opts, qs_batch_t* out) {
+  if (!out) return bfail(QS_EINVAL, "null output batch");
+  *out = nullptr;
+  if (count < 1 || !n || !op_offsets) return bfail(QS_EINVAL, "empty batch");
+  qs_compile_opts o{};
+  o.mode = QS_MODE_TILE;
+  o.dtype = QS_C64;
+  if (opts) o = *opts;
+  if (o.mode != QS_MODE_TILE) return bfail(QS_EINVAL, "batches run tile-mode plans only");
+  if (o.dtype != QS_C64 && o.dtype != QS_C128) return bfail(QS_EINVAL, "unknown dtype");
+  if (o.flags != 0 || o.reg_bits < 0 || o.reg_bits > 5) return bfail(QS_EINVAL, "bad options");
+  auto t0 = std::chrono::steady_clock::now();
+  qs_batch* b = new qs_batch();
+  b->count = count;
+  b->dtype = (qs_dtype)o.dtype;
+  b->store_bytes = o.dtype == QS_C128 ? 16 : 8;
+  b->n.assign(n, n + count);
+  b->off.resize(count);
+  const int Lreq = o.tile_bits ? o.tile_bits : default_tile_bits(o.dtype);
+  const int creq = o.low_bits ? o.low_bits : default_low_bits(o.dtype);
+  size_t elems = 0;
+  std::vector<std::vector<BatchPass>> per_circuit(count);
+  for (int i = 0; i < count; i++) {
+    if (n[i] < 1 || n[i] > 30) {
+      delete b;
+      return bfail(QS_EINVAL, "circuit " + std::to_string(i) + ": n must be in [1, 30] in a batch");
+    }
+    if (op_offsets[i + 1] < op_offsets[i]) {
+      delete b;
+      return bfail(QS_EINVAL, "op_offsets must be non-decreasing");
+    }
+    b->off[i] = elems;
+    elems += ((size_t)1 << n[i]);
+    elems = (elems + 31) & ~(size_t)31;   // 256-byte aligned starts
+    std::vector<HGate> gates(op_offsets[i + 1] - op_offsets[i]);
+    std::string err;
+    for (size_t g = 0; g < gates.size(); g++)
+      if (!make_hgate(n[i], ops[op_offsets[i] + g], mats, nmats, &gates[g], &err)) {
+        delete b;
+        return bfail(QS_EINVAL, "circuit " + std::to_string(i) + " op " + std::to_string(g) + ": " + err);
+      }
+    qs_compile_opts oi = o;
+    oi.tile_bits = std::min(Lreq, n[i]);
+    oi.low_bits = std::min(std::max(creq, o.dtype == QS_C64 ? 1 : 0), oi.tile_bits);
+    CompileResult cr;
+    std::vector<int> s0(n[i]);
+    for (int q = 0; q < n[i]; q++) s0[q] = q;
+    if (!compile_circuit(n[i], gates, s0, oi, &cr, &err)) {
+      delete b;
+      return bfail(QS_EINVAL, "circuit " + std::to_string(i) + ": " + err);
+    }
+    b->pol = cr.pol;
+    const int sbase = (int)b->stages.size(), rbase = (int)b->rops.size(), dbase = (int)b->dops.size();
+    const int pbase = (int)b->pool.entries();
+    for (StageRec st : cr.stages) {
+      st.op0 += (st.kind == 0) ? rbase : dbase;
+      b->stages.push_back(st);
+    }
+    for (RegOp r : cr.reg_ops) {
+      if (r.mat >= 0) r.mat += pbase;
+      b->rops.push_back(r);
+    }
+    for (DevOp d : cr.tile_ops) {
+      if (d.mat >= 0) d.mat += pbase;
+      b->dops.push_back(d);
+    }
+    b->pool.f64.insert(b->pool.f64.end(), cr.pool.f64.begin(), cr.pool.f64.end());
+    if (b->pool.entries() & 1) b->pool.add(cd(0, 0));   // next circuit's tables stay 16-byte aligned
+    for (const Step& s : cr.steps) {
+      if (s.kind != ST_PASS) {
+        delete b;
+        return bfail(QS_EUNSUPPORTED, "batch plans must consist of tile passes only");
+      }
+      BatchPass bp;
+      bp.tp = s.pass;
+      bp.tp.st0 += sbase;
+      bp.psi_off = b->off[i];
+      if (b->K == 0) b->K = bp.tp.K;
+      if (bp.tp.K != b->K) {
+        delete b;
+        return bfail(QS_EUNSUPPORTED, "all circuits of a batch need the same register bits (n too small)");
+      }
+      per_circuit[i].push_back(bp);
+      b->stats.hbm_bytes += s.bytes;
+      b->stats.alu_instr += s.alu;
+    }
+    b->stats.n_gates += cr.stats.n_gates;
+    b->stats.n_passes += cr.stats.n_passes;
+  }
+  if (b->pool.entries() == 0) b->pool.add(cd(0, 0));
+  b->total_elems = elems;
+  size_t maxw = 0;
+  for (auto& v : per_circuit) maxw = std::max(maxw, v.size());
+  for (size_t w = 0; w < maxw; w++) {
+    qs_batch::Wave wave;
+    wave.prefix.push_back(0);
+    for (int i = 0; i < count; i++) {
+      if (w >= per_circuit[i].size()) continue;
+      const BatchPass& bp = per_circuit[i][w];
+      wave.passes.push_back(bp);
+      wave.prefix.push_back(wave.prefix.back() + (1ull << (bp.tp.n - bp.tp.L)));
+      wave.maxL = std::max(wave.maxL, bp.tp.L);
+      wave.minc = std::min(wave.minc, bp.tp.c);
+    }
+    b->waves.push_back(std::move(wave));
+  }
+  b->stats.n_circuits = count;
+  b->stats.n_waves = (int64_t)b->waves.size();
+  b->stats.state_bytes = (double)elems * b->store_bytes;
+  // device copies
+  std::vector<BatchPass> all_passes;
+  std::vector<uint64_t> all_prefix;
+  for (auto& w : b->waves) {
+    w.pass_off = all_passes.size();
+    w.prefix_off = all_prefix.size();
+    all_passes.insert(all_passes.end(), w.passes.begin(), w.passes.end());
+    all_prefix.insert(all_prefix.end(), w.prefix.begin(), w.prefix.end());
+  }
+  cudaError_t e = cudaMalloc(&b->psi, elems * b->store_bytes);
+  if (e == cudaSuccess) b->allocs.push_back(b->psi);
+  std::vector<unsigned char> ser = b->pool.serialise(b->pol);
+  b->stages_d = upload(b, b->stages, &e);
+  b->rops_d = upload(b, b->rops, &e);
+  b->dops_d = upload(b, b->dops, &e);
+  b->pool_d = upload(b, ser, &e);
+  b->passes_d = upload(b, all_passes, &e);
+  b->prefix_d = upload(b, all_prefix, &e);
+  b->off_d = upload(b, b->off, &e);
+  b->n_d = upload(b, b->n, &e);
+  std::vector<double> zeros(count, 0.0);
+  b->norms_d = upload(b, zeros, &e);
+  std::vector<int> st(64, 0);
+  b->status_d = upload(b, st, &e);
+  if (e != cudaSuccess) {
+    qs_batch_destroy(b);
+    set_last_error(std::string("batch upload: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? QS_ENOMEM : QS_ECUDA;
+  }
+  b->stats.compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = b;
+  return QS_OK;
+}
+
+qs_status qs_batch_set_stream(qs_batch_t b, void* stream) {
+  if (!b) return bfail(QS_EINVAL, "null batch");
+  cudaStreamSynchronize(b->stream);
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  b->stream = (cudaStream_t)stream;
+  return QS_OK;
+}
+
+qs_status qs_batch_set_graph(qs_batch_t b, int on) {
+  if (!b) return bfail(QS_EINVAL, "null batch");
+  b->use_graph = on != 0;
+  return QS_OK;
+}
+
+qs_status qs_batch_run(qs_batch_t b) {
+  if (!b) return bfail(QS_EINVAL, "null batch");
+  cudaError_t e;
+  if (!b->use_graph || b->runs == 0 || b->stream == nullptr) {
+    // eager (the first run also configures the kernels outside any capture)
+    e = enqueue(b);
+  } else {
+    if (!b->graph) {
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        cudaError_t e2 = enqueue(b);
+        e = cudaStreamEndCapture(b->stream, &g);
+        if (e2 != cudaSuccess) e = e2;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) return bfail(QS_ECUDA, std::string("batch graph capture: ") + cudaGetErrorString(e));
+    }
+    e = cudaGraphLaunch(b->graph, b->stream);
+  }
+  if (e != cudaSuccess) return bfail(QS_ECUDA, std::string("batch run: ") + cudaGetErrorString(e));
+  b->runs++;
+  return QS_OK;
+}
+
+qs_status qs_batch_sync(qs_batch_t b) {
+  if (!b) return bfail(QS_EINVAL, "null batch");
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(QS_ECUDA, std::string("batch sync: ") + cudaGetErrorString(e));
+  int st = 0;
+  cudaMemcpy(&st, b->status_d, sizeof(int), cudaMemcpyDeviceToHost);
+  if (st != 0) {
+    cudaMemset(b->status_d, 0, sizeof(int));
+    return bfail(QS_ETIMEOUT, "a device-side wait timed out");
+  }
+  return QS_OK;
+}
+
+qs_status qs_batch_norms(qs_batch_t b, double* out) {
+  if (!b || !out) return bfail(QS_EINVAL, "null argument");
+  qs_status s = qs_batch_sync(b);
+  if (s != QS_OK) return s;
+  cudaError_t e = cudaMemcpy(out, b->norms_d, sizeof(double) * b->count, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return bfail(QS_ECUDA, std::string("batch norms: ") + cudaGetErrorString(e));
+  return QS_OK;
+}
+
+qs_status qs_batch_get_amplitudes(qs_batch_t b, int i, void* out, uint64_t first, uint64_t count) {
+  if (!b || !out) return bfail(QS_EINVAL, "null argument");
+  if (i < 0 || i >= b->count) return bfail(QS_EINVAL, "circuit index out of range");
+  const uint64_t N = 1ull << b->n[i];
+  if (first > N || count > N - first) return bfail(QS_EINVAL, "amplitude range out of bounds");
+  qs_status s = qs_batch_sync(b);
+  if (s != QS_OK) return s;
+  cudaError_t e = cudaMemcpy(out, (char*)b->psi + (b->off[i] + first) * b->store_bytes, count * b->store_bytes,
+                             cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return bfail(QS_ECUDA, std::string("batch amplitudes: ") + cudaGetErrorString(e));
+  return QS_OK;
+}
+
+qs_status qs_batch_get_stats(qs_batch_t b, qs_batch_stats* out) {
+  if (!b || !out) return bfail(QS_EINVAL, "null argument");
+  *out = b->stats;
+  return QS_OK;
+}
+
+qs_status qs_batch_destroy(qs_batch_t b) {
+  if (!b) return QS_OK;
+  cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (void* p : b->allocs) cudaFree(p);
+  delete b;
+  return QS_OK;
+}
+
+}  // extern "C"

@@ -68,6 +68,7 @@ struct KernelRecord {
   std::string name;
   cudaEvent_t e0, e1;
   double bytes;
+  double alu;
 };
 
 struct qs_state {
@@ -122,11 +123,12 @@ cudaEvent_t get_event(qs_state* h) {
 
 // run `launch` on the state's stream, bracketed by events when profiling
 template <class F>
-cudaError_t timed(qs_state* h, const char* name, double bytes, F&& launch) {
+cudaError_t timed(qs_state* h, const char* name, double bytes, F&& launch, double alu = 0.0) {
   if (!h->profiling) return launch();
   KernelRecord r;
   r.name = name;
   r.bytes = bytes;
+  r.alu = alu;
   r.e0 = get_event(h);
   r.e1 = get_event(h);
   cudaEventRecord(r.e0, h->stream);
@@ -154,6 +156,7 @@ void collect_stats(qs_state* h) {
     st->launches++;
     st->total_ms += ms;
     st->bytes += r.bytes;
+    st->alu += r.alu;
     h->free_events.push_back(r.e0);
     h->free_events.push_back(r.e1);
   }
@@ -436,6 +439,7 @@ qs_status qs_compile(int n, const qs_op* ops, size_t nops, const double* mats, s
   if (o.dtype != QS_C64 && o.dtype != QS_C128) return fail(QS_EINVAL, "unknown dtype");
   if (o.mode < QS_MODE_PERGATE || o.mode > QS_MODE_TILE) return fail(QS_EINVAL, "unknown mode");
   if (o.flags != 0) return fail(QS_EINVAL, "flags must be 0");
+  if (o.reg_bits < 0 || o.reg_bits > 5) return fail(QS_EINVAL, "reg_bits must be in [0, 5]");
   if (o.tile_bits == 0) o.tile_bits = default_tile_bits(o.dtype);
   if (o.low_bits == 0) o.low_bits = default_low_bits(o.dtype);
   if (o.tile_bits < 1 || (o.mode != QS_MODE_PAPER && o.tile_bits > kMaxTileBits))
@@ -548,10 +552,11 @@ qs_status qs_execute(qs_handle h, qs_plan_t p) {
                      [&] {
                        return launch_tile_pass(p->pol, h->psi, s.pass, p->stages_dev, p->rops_dev, p->ops_dev,
                                                p->pool_dev, h->status_dev, h->stream);
-                     }),
+                     }, s.alu),
                "tile pass launch");
     } else if (s.kind == ST_GATE) {
-      CUDA_TRY(timed(h, name, s.bytes, [&] { return launch_gate(p->pol, h->psi, h->n, s.op, p->pool_dev, h->stream); }),
+      CUDA_TRY(timed(h, name, s.bytes, [&] { return launch_gate(p->pol, h->psi, h->n, s.op, p->pool_dev, h->stream); },
+                     s.alu),
                "gate launch");
     } else {
       qs_status st = do_permute(h, s.src_of, s.perm, s.bytes);

@@ -166,10 +166,11 @@ bool emit_pass(int n, int L, int c, const std::vector<int>& tbits_sorted, const 
     }
   }
   if (ops.empty()) return true;   // identity gates only
-  st.pass.K = register_bits(out->store_bytes == 16 ? QS_C128 : QS_C64, L);
+  st.pass.K = register_bits(out->store_bytes == 16 ? QS_C128 : QS_C64, L, out->reg_bits);
   build_stages(ops, L, st.pass.K, out, &st.pass.st0, &st.pass.nst);
   const int store_bytes = out->store_bytes;
   st.bytes = 2.0 * (double)store_bytes * (double)(1ull << n);
+  st.alu = stage_alu_per_amp(*out, st.pass.st0, st.pass.nst) * (double)(1ull << n);
   out->steps.push_back(std::move(st));
   out->stats.n_passes++;
   return true;
@@ -190,6 +191,7 @@ bool emit_gate(int n, const HGate& g, const std::vector<int>& sigma, int store_b
     st.kind = ST_GATE;
     st.op = o;
     st.bytes = gate_bytes(g, n, store_bytes);
+    st.alu = (op_alu_per_amp(out->pol, o) + (out->pol == POL_DF ? 72.0 : 0.0)) * (double)(1ull << n);
     out->steps.push_back(std::move(st));
   }
   return true;
@@ -401,6 +403,8 @@ bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<i
   auto t0 = std::chrono::steady_clock::now();
   const int store_bytes = (o.dtype == QS_C128) ? 16 : 8;
   out->store_bytes = store_bytes;
+  out->reg_bits = o.reg_bits;
+  out->pol = (o.dtype == QS_C64) ? POL_F32 : (o.arith == QS_ARITH_F64 ? POL_F64 : POL_DF);
   out->stats = qs_plan_stats{};
   out->stats.n_gates = (int64_t)gates.size();
   bool ok = true;
@@ -419,9 +423,13 @@ bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<i
     return false;
   }
   if (!ok) return false;
-  double bytes = 0;
-  for (const Step& s : out->steps) bytes += s.bytes;
+  double bytes = 0, alu = 0;
+  for (const Step& s : out->steps) {
+    bytes += s.bytes;
+    alu += s.alu;
+  }
   out->stats.hbm_bytes = bytes;
+  out->stats.alu_instr = alu;
   out->stats.compile_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return true;

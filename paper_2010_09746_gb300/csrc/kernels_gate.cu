@@ -346,7 +346,63 @@ __global__ void __launch_bounds__(kThreads) k_gather(const S* __restrict__ psi, 
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Batches: amplitude 0 of every state set to 1 after the buffer was cleared; per-state FP64
+// norms, one CTA per state with a fixed reduction order.
+template <class S>
+__global__ void k_batch_ones(S* psi, const uint64_t* offs, int count) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) {
+    S v;
+    v.x = 1;
+    v.y = 0;
+    psi[offs[i]] = v;
+  }
+}
+
+template <class S>
+__global__ void __launch_bounds__(kThreads) k_batch_norms(const S* __restrict__ psi, const uint64_t* offs,
+                                                          const int* ns, double* out) {
+  __shared__ double red[kThreads];
+  const S* p = psi + offs[blockIdx.x];
+  const uint64_t N = 1ull << ns[blockIdx.x];
+  double acc = 0.0;
+  for (uint64_t i = threadIdx.x; i < N; i += kThreads) {
+    const double re = (double)p[i].x, im = (double)p[i].y;
+    acc = fma(re, re, acc);
+    acc = fma(im, im, acc);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
 }  // namespace
+
+cudaError_t launch_batch_init(void* psi, int store_bytes, const uint64_t* offs, int count, size_t total_elems,
+                              cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(psi, 0, total_elems * store_bytes, s);
+  if (e != cudaSuccess) return e;
+  const int blocks = (count + kThreads - 1) / kThreads;
+  if (store_bytes == 16)
+    k_batch_ones<double2><<<blocks, kThreads, 0, s>>>((double2*)psi, offs, count);
+  else
+    k_batch_ones<float2><<<blocks, kThreads, 0, s>>>((float2*)psi, offs, count);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_norms(const void* psi, int is_c128, const uint64_t* offs, const int* ns, int count,
+                               double* out, cudaStream_t s) {
+  if (is_c128)
+    k_batch_norms<double2><<<count, kThreads, 0, s>>>((const double2*)psi, offs, ns, out);
+  else
+    k_batch_norms<float2><<<count, kThreads, 0, s>>>((const float2*)psi, offs, ns, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gate(Policy pol, void* psi, int n, const DevOp& op, const void* pool, cudaStream_t s) {
   switch (pol) {

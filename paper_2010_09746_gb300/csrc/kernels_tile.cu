@@ -279,13 +279,14 @@ __device__ __forceinline__ uint32_t pdep32(uint32_t g, uint32_t mask) {
   return r;
 }
 
+// single-slot updates carry no register-slot controls (the compiler turns a controlled
+// update into a 4x4 block on the (target, control) slots); X keeps its predicate
 template <class A, int K, int S>
 __device__ __forceinline__ void r_u1(typename A::reg_t (&x)[1 << K], const typename A::mat_t* m, uint32_t csl) {
   const typename A::mat_t u00 = m[0], u01 = m[1], u10 = m[2], u11 = m[3];
 #pragma unroll
   for (int j = 0; j < (1 << K); j++) {
     if (j & (1 << S)) continue;
-    if ((j & csl) != csl) continue;
     const typename A::reg_t a = x[j], b = x[j | (1 << S)];
     x[j] = A::mac2(u00, a, u01, b);
     x[j | (1 << S)] = A::mac2(u10, a, u11, b);
@@ -297,7 +298,6 @@ __device__ __forceinline__ void r_rx(typename A::reg_t (&x)[1 << K], const typen
 #pragma unroll
   for (int j = 0; j < (1 << K); j++) {
     if (j & (1 << S)) continue;
-    if ((j & csl) != csl) continue;
     const typename A::reg_t a = x[j], b = x[j | (1 << S)];
     x[j] = A::rx(cs, a, b);
     x[j | (1 << S)] = A::rx(cs, b, a);
@@ -314,13 +314,15 @@ __device__ __forceinline__ void r_x(typename A::reg_t (&x)[1 << K], const typena
     x[j | (1 << S)] = a;
   }
 }
+
+
 template <class A, int K, int S0, int S1>
 __device__ __forceinline__ void r_u2(typename A::reg_t (&x)[1 << K], const typename A::mat_t* m, uint32_t csl) {
   using R = typename A::reg_t;
 #pragma unroll
   for (int j = 0; j < (1 << K); j++) {
     if (j & ((1 << S0) | (1 << S1))) continue;
-    if ((j & csl) != csl) continue;
+    if (csl && (j & csl) != csl) continue;
     const int i0 = j, i1 = j | (1 << S0), i2 = j | (1 << S1), i3 = j | (1 << S0) | (1 << S1);
     const R x0 = x[i0], x1 = x[i1], x2 = x[i2], x3 = x[i3];
     R y[4];
@@ -386,15 +388,31 @@ __device__ __forceinline__ void apply_regop(typename A::reg_t (&x)[1 << K], cons
           if ((j & csl) == csl) x[j] = A::mul(((j >> s0) & 1) ? d1 : d0, x[j]);
       } else {
         const M d = (op.tb >= 0) ? (((gidx >> op.tb) & 1u) ? d1 : d0) : (((base >> op.gbit) & 1ull) ? d1 : d0);
+        if (csl == 0) {
 #pragma unroll
-        for (int j = 0; j < (1 << K); j++)
-          if ((j & csl) == csl) x[j] = A::mul(d, x[j]);
+          for (int j = 0; j < (1 << K); j++) x[j] = A::mul(d, x[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < (1 << K); j++)
+            if ((j & csl) == csl) x[j] = A::mul(d, x[j]);
+        }
       }
       break;
     }
     case OP_DTAB: {
+      if constexpr (sizeof(M) == 8 && K >= 1) {
+        // 8-byte entries: the compiler aligns every table to 16 bytes, load two at a time
+        const float4* t4 = reinterpret_cast<const float4*>(m);
 #pragma unroll
-      for (int j = 0; j < (1 << K); j++) x[j] = A::mul(m[j], x[j]);
+        for (int j = 0; j < (1 << K); j += 2) {
+          const float4 v = t4[j >> 1];
+          x[j] = A::mul(M{v.x, v.y}, x[j]);
+          x[j + 1] = A::mul(M{v.z, v.w}, x[j + 1]);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < (1 << K); j++) x[j] = A::mul(m[j], x[j]);
+      }
       break;
     }
     case OP_PHASE: {
@@ -428,19 +446,21 @@ __device__ __forceinline__ void run_reg_stage(typename A::reg_t* T, const StageR
   const uint32_t tile_mask = (L >= 32) ? 0xFFFFFFFFu : ((1u << L) - 1u);
   const uint32_t omask = tile_mask & ~(uint32_t)sr.rmask;
   const uint32_t ngroups = 1u << (L - K);
-  uint32_t rb[K];
+  // px(a | b) = px(a) + px(b) for disjoint bit sets (no carries), so an element's padded
+  // position is the group's position plus a sum of per-register-bit offsets
+  uint32_t pb[K];
 #pragma unroll
-  for (int b = 0; b < K; b++) rb[b] = 1u << sr.rbits[b];
+  for (int b = 0; b < K; b++) pb[b] = px(1u << sr.rbits[b]);
   for (uint32_t g = threadIdx.x; g < ngroups; g += kTileThreads) {
     const uint32_t gidx = pdep32(g, omask);
+    const uint32_t gpos = px(gidx);
     R x[1 << K];
 #pragma unroll
     for (int j = 0; j < (1 << K); j++) {
-      uint32_t idx = gidx;
+      uint32_t p = gpos;
 #pragma unroll
       for (int b = 0; b < K; b++)
-        if ((j >> b) & 1) idx |= rb[b];
-      const uint32_t p = px(idx);
+        if ((j >> b) & 1) p += pb[b];
       if constexpr (std::is_same<R, S>::value) {
         x[j] = T[p];
       } else {
@@ -452,13 +472,16 @@ __device__ __forceinline__ void run_reg_stage(typename A::reg_t* T, const StageR
       if ((base & op.gmask) != op.gmask) continue;
       apply_regop<A, K>(x, op, pool, gidx, base);
     }
+    // recompute the store addresses from a value the compiler cannot equate with the load
+    // addresses, so that 2^K addresses are not kept live across the op loop
+    uint32_t spos = gpos;
+    asm volatile("" : "+r"(spos));
 #pragma unroll
     for (int j = 0; j < (1 << K); j++) {
-      uint32_t idx = gidx;
+      uint32_t p = spos;
 #pragma unroll
       for (int b = 0; b < K; b++)
-        if ((j >> b) & 1) idx |= rb[b];
-      const uint32_t p = px(idx);
+        if ((j >> b) & 1) p += pb[b];
       if constexpr (std::is_same<R, S>::value) {
         T[p] = x[j];
       } else {
@@ -469,99 +492,144 @@ __device__ __forceinline__ void run_reg_stage(typename A::reg_t* T, const StageR
   }
 }
 
+// Shared memory of a tile CTA: the mbarrier in the first 16 bytes, the tile from byte 128.
+constexpr uint32_t kTileSmemOffset = 128;
+
+// Process block b of tile pass tp on the state at psi: load, stages, store.  Returns false
+// when the load's bounded wait expired (the status word is set).
 template <class A, int K>
-__global__ void __launch_bounds__(kTileThreads, 2)
-    k_tile_staged(typename A::store_t* __restrict__ psi, const TilePass tp, const StageRec* __restrict__ stages,
-                  const RegOp* __restrict__ rops, const DevOp* __restrict__ dops,
-                  const typename A::mat_t* __restrict__ pool, int* __restrict__ status) {
+__device__ __forceinline__ bool process_block(typename A::store_t* __restrict__ psi, const TilePass& tp, uint64_t b,
+                                              const StageRec* __restrict__ stages, const RegOp* __restrict__ rops,
+                                              const DevOp* __restrict__ dops, const typename A::mat_t* __restrict__ pool,
+                                              int* __restrict__ status, unsigned char* smem, uint32_t bar,
+                                              uint32_t& phase) {
   using S = typename A::store_t;
   using R = typename A::reg_t;
   static_assert(sizeof(R) == sizeof(S), "in-place conversion needs equal element sizes");
   constexpr bool kConv = !std::is_same<R, S>::value;
-  extern __shared__ __align__(128) unsigned char smem[];
   const int L = tp.L, c = tp.c;
   const Pad px{c, (int)(16 / sizeof(S))};
   const uint32_t nelem = 1u << L;
   const uint32_t nseg = 1u << (L - c);
   const uint32_t seg_bytes = (uint32_t)sizeof(S) << c;
   const uint32_t seg_stride = seg_bytes + 16u;
-  R* T = reinterpret_cast<R*>(smem);
-  uint64_t* bar_p = reinterpret_cast<uint64_t*>(smem + (size_t)nseg * seg_stride);
-  const uint32_t bar = smem_u32(bar_p);
+  R* T = reinterpret_cast<R*>(smem + kTileSmemOffset);
   const uint32_t tile_s = smem_u32(T);
   const int tid = threadIdx.x;
-  if (tid == 0) {
+  const int nout = tp.n - L;
+  uint64_t base = 0;
+  for (int k = 0; k < nout; k++)
+    if ((b >> k) & 1ull) base |= 1ull << tp.npos[k];
+
+  // ---- load: 2^(L-c) bulk copies of 2^c contiguous amplitudes, counted on the mbarrier
+  if (tid == 0) mbar_arrive_expect_tx(bar, nseg * seg_bytes);
+  __syncthreads();
+  for (uint32_t s = tid; s < nseg; s += kTileThreads) {
+    uint64_t off = 0;
+    for (int k = 0; k < L - c; k++)
+      if ((s >> k) & 1u) off |= 1ull << tp.tpos[c + k];
+    bulk_load(tile_s + s * seg_stride, psi + (base | off), seg_bytes, bar);
+  }
+  if (!mbar_wait(bar, phase, globaltimer() + kWaitNs)) {
+    if (tid == 0) atomicExch(status, (int)QS_ETIMEOUT);
+    return false;
+  }
+  phase ^= 1u;
+
+  // ---- stages
+  bool in_store = true;   // the tile holds storage-format elements
+  for (int k = 0; k < tp.nst; k++) {
+    const StageRec sr = stages[tp.st0 + k];
+    const bool last = (k == tp.nst - 1);
+    if (sr.kind == 0) {
+      run_reg_stage<A, K>(T, sr, rops, pool, L, px, base, in_store, last);
+      in_store = last;
+    } else {
+      if (kConv && in_store) {
+        S* Ts = reinterpret_cast<S*>(T);
+        for (uint32_t i = tid; i < nelem; i += kTileThreads) T[px(i)] = A::from_store(Ts[px(i)]);
+        __syncthreads();
+      }
+      in_store = false;
+      for (int o = 0; o < sr.nops; o++) {
+        const DevOp& op = dops[sr.op0 + o];
+        if ((base & op.gmask) != op.gmask) continue;
+        apply_op<A>(T, L, op, pool, base, px);
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+  }
+  if (kConv && !in_store) {
+    S* Ts = reinterpret_cast<S*>(T);
+    for (uint32_t i = tid; i < nelem; i += kTileThreads) {
+      const R v = T[px(i)];
+      Ts[px(i)] = A::to_store(v);
+    }
+  }
+  // ---- store: bulk copies back; the tile is reused only after they have been read
+  fence_async_smem();
+  __syncthreads();
+  for (uint32_t s = tid; s < nseg; s += kTileThreads) {
+    uint64_t off = 0;
+    for (int k = 0; k < L - c; k++)
+      if ((s >> k) & 1u) off |= 1ull << tp.tpos[c + k];
+    bulk_store(psi + (base | off), tile_s + s * seg_stride, seg_bytes);
+  }
+  bulk_commit();
+  bulk_wait_read0();
+  __syncthreads();
+  return true;
+}
+
+__device__ __forceinline__ uint32_t init_tile_barrier(unsigned char* smem) {
+  const uint32_t bar = smem_u32(smem);
+  if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_async_smem();
   }
   __syncthreads();
+  return bar;
+}
 
-  const uint64_t nblocks = 1ull << (tp.n - L);
-  const int nout = tp.n - L;
+template <class A, int K>
+__global__ void __launch_bounds__(kTileThreads, 2)
+    k_tile_staged(typename A::store_t* __restrict__ psi, const TilePass tp, const StageRec* __restrict__ stages,
+                  const RegOp* __restrict__ rops, const DevOp* __restrict__ dops,
+                  const typename A::mat_t* __restrict__ pool, int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const uint32_t bar = init_tile_barrier(smem);
+  const uint64_t nblocks = 1ull << (tp.n - tp.L);
   uint32_t phase = 0;
-  for (uint64_t b = blockIdx.x; b < nblocks; b += gridDim.x) {
-    uint64_t base = 0;
-    for (int k = 0; k < nout; k++)
-      if ((b >> k) & 1ull) base |= 1ull << tp.npos[k];
+  for (uint64_t b = blockIdx.x; b < nblocks; b += gridDim.x)
+    if (!process_block<A, K>(psi, tp, b, stages, rops, dops, pool, status, smem, bar, phase)) return;
+  bulk_wait0();
+}
 
-    // ---- load: 2^(L-c) bulk copies of 2^c contiguous amplitudes, counted on the mbarrier
-    if (tid == 0) mbar_arrive_expect_tx(bar, nseg * seg_bytes);
-    __syncthreads();
-    for (uint32_t s = tid; s < nseg; s += kTileThreads) {
-      uint64_t off = 0;
-      for (int k = 0; k < L - c; k++)
-        if ((s >> k) & 1u) off |= 1ull << tp.tpos[c + k];
-      bulk_load(tile_s + s * seg_stride, psi + (base | off), seg_bytes, bar);
+// Many independent tile passes in one persistent launch: work item i is block
+// i - prefix[p] of pass p, where prefix[p] <= i < prefix[p + 1]; pass p acts on the state
+// at psi + passes[p].psi_off.
+template <class A, int K>
+__global__ void __launch_bounds__(kTileThreads, 2)
+    k_tile_batched(typename A::store_t* __restrict__ psi, const BatchPass* __restrict__ passes,
+                   const uint64_t* __restrict__ prefix, int npass, const StageRec* __restrict__ stages,
+                   const RegOp* __restrict__ rops, const DevOp* __restrict__ dops,
+                   const typename A::mat_t* __restrict__ pool, int* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const uint32_t bar = init_tile_barrier(smem);
+  const uint64_t total = prefix[npass];
+  uint32_t phase = 0;
+  for (uint64_t i = blockIdx.x; i < total; i += gridDim.x) {
+    int lo = 0, hi = npass - 1;   // last p with prefix[p] <= i
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (prefix[mid] <= i) lo = mid;
+      else hi = mid - 1;
     }
-    if (!mbar_wait(bar, phase, globaltimer() + kWaitNs)) {
-      if (tid == 0) atomicExch(status, (int)QS_ETIMEOUT);
+    const BatchPass& bp = passes[lo];
+    if (!process_block<A, K>(psi + bp.psi_off, bp.tp, i - prefix[lo], stages, rops, dops, pool, status, smem, bar,
+                             phase))
       return;
-    }
-    phase ^= 1u;
-
-    // ---- stages
-    bool in_store = true;   // the tile holds storage-format elements
-    for (int k = 0; k < tp.nst; k++) {
-      const StageRec sr = stages[tp.st0 + k];
-      const bool last = (k == tp.nst - 1);
-      if (sr.kind == 0) {
-        run_reg_stage<A, K>(T, sr, rops, pool, L, px, base, in_store, last);
-        in_store = last;
-      } else {
-        if (kConv && in_store) {
-          S* Ts = reinterpret_cast<S*>(smem);
-          for (uint32_t i = tid; i < nelem; i += kTileThreads) T[px(i)] = A::from_store(Ts[px(i)]);
-          __syncthreads();
-        }
-        in_store = false;
-        for (int o = 0; o < sr.nops; o++) {
-          const DevOp& op = dops[sr.op0 + o];
-          if ((base & op.gmask) != op.gmask) continue;
-          apply_op<A>(T, L, op, pool, base, px);
-          __syncthreads();
-        }
-      }
-      __syncthreads();
-    }
-    if (kConv && !in_store) {
-      S* Ts = reinterpret_cast<S*>(smem);
-      for (uint32_t i = tid; i < nelem; i += kTileThreads) {
-        const R v = T[px(i)];
-        Ts[px(i)] = A::to_store(v);
-      }
-    }
-    // ---- store: bulk copies back; the tile is reused only after they have been read
-    fence_async_smem();
-    __syncthreads();
-    for (uint32_t s = tid; s < nseg; s += kTileThreads) {
-      uint64_t off = 0;
-      for (int k = 0; k < L - c; k++)
-        if ((s >> k) & 1u) off |= 1ull << tp.tpos[c + k];
-      bulk_store(psi + (base | off), tile_s + s * seg_stride, seg_bytes);
-    }
-    bulk_commit();
-    bulk_wait_read0();
-    __syncthreads();
   }
   bulk_wait0();
 }
@@ -570,7 +638,7 @@ template <class A, int K>
 cudaError_t launch_staged(void* psi, const TilePass& tp, const StageRec* stages, const RegOp* rops,
                           const DevOp* dops, const void* pool, int* status, cudaStream_t st) {
   using S = typename A::store_t;
-  const size_t smem = ((size_t)1 << (tp.L - tp.c)) * (((size_t)sizeof(S) << tp.c) + 16) + 16;
+  const size_t smem = kTileSmemOffset + ((size_t)1 << (tp.L - tp.c)) * (((size_t)sizeof(S) << tp.c) + 16);
   static bool configured = false;
   static int sms = 0;
   if (!configured) {
@@ -595,6 +663,53 @@ cudaError_t launch_staged(void* psi, const TilePass& tp, const StageRec* stages,
   return cudaGetLastError();
 }
 
+template <class A, int K>
+cudaError_t launch_batched_t(void* psi, const BatchPass* passes, const uint64_t* prefix, int npass, uint64_t total_blocks,
+                             int maxL, int minc, const StageRec* stages, const RegOp* rops, const DevOp* dops,
+                             const void* pool, int* status, cudaStream_t st) {
+  using S = typename A::store_t;
+  const size_t smem = kTileSmemOffset + ((size_t)1 << (maxL - minc)) * (((size_t)sizeof(S) << minc) + 16);
+  static bool configured = false;
+  static int sms = 0;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_tile_batched<A, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_batched<A, K>, kTileThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  uint64_t grid = (uint64_t)sms * per_sm;
+  if (grid > total_blocks) grid = total_blocks;
+  if (grid < 1) return cudaSuccess;
+  k_tile_batched<A, K><<<(unsigned)grid, kTileThreads, smem, st>>>((S*)psi, passes, prefix, npass, stages, rops, dops,
+                                                                    (const typename A::mat_t*)pool, status);
+  return cudaGetLastError();
+}
+
+template <class A>
+cudaError_t launch_batched_k(int K, void* psi, const BatchPass* passes, const uint64_t* prefix, int npass,
+                             uint64_t total, int maxL, int minc, const StageRec* stages, const RegOp* rops,
+                             const DevOp* dops, const void* pool, int* status, cudaStream_t st) {
+  switch (K) {
+    case 1: return launch_batched_t<A, 1>(psi, passes, prefix, npass, total, maxL, minc, stages, rops, dops, pool, status, st);
+    case 2: return launch_batched_t<A, 2>(psi, passes, prefix, npass, total, maxL, minc, stages, rops, dops, pool, status, st);
+    case 3: return launch_batched_t<A, 3>(psi, passes, prefix, npass, total, maxL, minc, stages, rops, dops, pool, status, st);
+    case 4: return launch_batched_t<A, 4>(psi, passes, prefix, npass, total, maxL, minc, stages, rops, dops, pool, status, st);
+    case 5:
+      if constexpr (sizeof(typename A::reg_t) <= 8)
+        return launch_batched_t<A, 5>(psi, passes, prefix, npass, total, maxL, minc, stages, rops, dops, pool, status, st);
+      break;
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <class A>
 cudaError_t launch_tile_t(void* psi, const TilePass& tp, const StageRec* stages, const RegOp* rops,
                           const DevOp* dops, const void* pool, int* status, cudaStream_t st) {
@@ -615,6 +730,17 @@ cudaError_t launch_tile_t(void* psi, const TilePass& tp, const StageRec* stages,
 int tile_pass_smem_bytes(Policy pol, int L) {
   const int e = (pol == POL_F32) ? 8 : 16;
   return (e << L) + (16 << L) + 16;   // upper bound (padding for c = 0)
+}
+
+cudaError_t launch_tile_batched(Policy pol, int K, void* psi, const BatchPass* passes, const uint64_t* prefix,
+                                int npass, uint64_t total_blocks, int maxL, int minc, const StageRec* stages,
+                                const RegOp* rops, const DevOp* dops, const void* pool, int* status, cudaStream_t s) {
+  switch (pol) {
+    case POL_F32: return launch_batched_k<AF32>(K, psi, passes, prefix, npass, total_blocks, maxL, minc, stages, rops, dops, pool, status, s);
+    case POL_F64: return launch_batched_k<AF64>(K, psi, passes, prefix, npass, total_blocks, maxL, minc, stages, rops, dops, pool, status, s);
+    case POL_DF: return launch_batched_k<ADF>(K, psi, passes, prefix, npass, total_blocks, maxL, minc, stages, rops, dops, pool, status, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tile_pass(Policy pol, void* psi, const TilePass& tp, const StageRec* stages_dev,

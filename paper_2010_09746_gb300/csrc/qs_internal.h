@@ -86,6 +86,13 @@ struct TilePass {
   int32_t npos[kMaxQubits];          // storage positions of the other bits, ascending
 };
 
+// One pass of a batch: a tile pass on the state that starts psi_off elements into the batch's
+// state buffer.
+struct BatchPass {
+  TilePass tp;
+  uint64_t psi_off;
+};
+
 // One plan step.
 enum StepKind : int32_t { ST_PASS = 0, ST_GATE = 1, ST_PERMUTE = 2 };
 struct Step {
@@ -95,6 +102,7 @@ struct Step {
   std::vector<int> perm;     // ST_PERMUTE: new sigma (logical -> storage)
   std::vector<int> src_of;   // ST_PERMUTE: storage bit p of the output takes input bit src_of[p]
   double bytes = 0;          // algorithmic HBM bytes
+  double alu = 0;            // arithmetic instructions the policy's formulas need (all amplitudes)
 };
 
 // ------------------------------------------------------------------------------------------
@@ -106,6 +114,9 @@ cudaError_t launch_gate(Policy pol, void* psi, int n, const DevOp& op, const voi
 cudaError_t launch_tile_pass(Policy pol, void* psi, const TilePass& tp, const StageRec* stages_dev,
                              const RegOp* regops_dev, const DevOp* ops_dev, const void* pool, int* status_dev,
                              cudaStream_t s);
+cudaError_t launch_tile_batched(Policy pol, int K, void* psi, const BatchPass* passes, const uint64_t* prefix,
+                                int npass, uint64_t total_blocks, int maxL, int minc, const StageRec* stages,
+                                const RegOp* rops, const DevOp* dops, const void* pool, int* status, cudaStream_t s);
 cudaError_t launch_permute(void* dst, const void* src, int n, int store_bytes, const int* src_of,
                            cudaStream_t s);
 cudaError_t launch_norm_partials(const void* psi, int n, int is_c128, double* partials, int nparts,
@@ -166,6 +177,8 @@ bool lower_gate(const HGate& g, const LowerCtx& ctx, Pool& pool, std::vector<Dev
 // ------------------------------------------------------------------------------------------
 struct CompileResult {
   int store_bytes = 16;
+  Policy pol = POL_DF;
+  int reg_bits = 0;              // requested register bits (0 = default)
   std::vector<Step> steps;
   std::vector<std::pair<int, int>> trace;   // QS_MODE_PAPER: (0 local gate | 1 non-local gate | 2 permute, value)
   std::vector<DevOp> tile_ops;   // shared-memory ops of all passes, concatenated
@@ -186,10 +199,16 @@ void set_last_error(const std::string& msg);
 
 int default_tile_bits(int dtype);
 int default_low_bits(int dtype);
-int register_bits(int dtype, int L);
+int register_bits(int dtype, int L, int requested);
 
 // Split a pass's op list (tile-local DevOps, program order) into register / shared-memory
 // stages with K register bits; appends to out->stages / reg_ops / tile_ops.
 void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* out, int* st0, int* nst);
+
+// Arithmetic instructions per amplitude of a pass's stages (shared-memory and register ops)
+// as the arithmetic policy's formulas count them: the ALU-work numerator of the roofline.
+double stage_alu_per_amp(const CompileResult& cr, int st0, int nst);
+// the same for one per-gate op
+double op_alu_per_amp(Policy pol, const DevOp& op);
 
 }  // namespace qs

@@ -37,6 +37,8 @@ OpInfo classify_op(const DevOp& o) {
   const uint32_t cm = (uint32_t)o.cmask;
   for (int b = 0; b < 32; b++)
     if ((cm >> b) & 1u) add(b, CLS_Z);
+  // register-stage U1 / RX carry at most one control, which becomes a 4x4 block
+  if ((o.type == OP_U1 || o.type == OP_RX) && __builtin_popcount(cm) >= 2) in.smem_only = true;
   switch (o.type) {
     case OP_U1: add(o.k0, CLS_N); in.need = 1u << o.k0; break;
     case OP_RX:
@@ -118,6 +120,7 @@ void merge_diagonals(std::vector<RegOp>& rl, int K, Pool& pool) {
       t.type = OP_DTAB;
       t.s0 = t.s1 = t.tb = -1;
       t.gbit = -1;
+      if (pool.entries() & 1) pool.add(cd(0, 0));   // tables start at an even entry (16-byte aligned)
       t.mat = (int)pool.entries();
       for (int j = 0; j < D; j++) pool.add(tab[j]);
       out.push_back(t);
@@ -132,8 +135,9 @@ void merge_diagonals(std::vector<RegOp>& rl, int K, Pool& pool) {
 
 }  // namespace
 
-int register_bits(int dtype, int L) {
-  const int k = (dtype == QS_C128) ? 4 : 5;
+int register_bits(int dtype, int L, int requested) {
+  const int kmax = (dtype == QS_C128) ? 4 : 5;
+  const int k = (requested > 0) ? std::min(requested, kmax) : kmax;
   return std::min(k, L);
 }
 
@@ -310,6 +314,30 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
           case OP_PHASE: r.neg = (o.mat < 0) ? 1 : 0; break;
           default: break;
         }
+        if ((r.type == OP_U1 || r.type == OP_RX) && r.csl != 0) {
+          // controlled 2x2 on a register slot: a 4x4 block on (target, control) slots,
+          // index r = b(target) + 2 b(control), identity where the control is 0
+          cd u[4];
+          if (r.type == OP_U1) {
+            for (int k = 0; k < 4; k++) u[k] = cd(out->pool.f64[2 * (r.mat + k)], out->pool.f64[2 * (r.mat + k) + 1]);
+          } else {
+            const double c = out->pool.f64[2 * r.mat], sn = out->pool.f64[2 * r.mat + 1];
+            u[0] = c; u[1] = cd(0, -sn); u[2] = cd(0, -sn); u[3] = c;
+          }
+          int cs = 0;
+          while (!((r.csl >> cs) & 1u)) cs++;
+          r.type = OP_U2;
+          r.s1 = (int8_t)cs;
+          r.csl = 0;
+          r.mat = (int)out->pool.entries();
+          for (int a = 0; a < 4; a++)
+            for (int b = 0; b < 4; b++) {
+              cd v(0, 0);
+              if (a < 2 && b < 2) v = (a == b) ? cd(1, 0) : cd(0, 0);
+              else if (a >= 2 && b >= 2) v = u[(a - 2) * 2 + (b - 2)];
+              out->pool.add(v);
+            }
+        }
         rl.push_back(r);
       }
       merge_diagonals(rl, K, out->pool);
@@ -325,6 +353,67 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
     rem.resize(w);
   }
   *nst = (int)out->stages.size() - *st0;
+}
+
+}  // namespace qs
+
+namespace qs {
+
+namespace {
+
+// instructions per affected amplitude: {F32, F64 (DFMA), double-float}
+struct Cost {
+  double f32, f64, df;
+};
+double pick(const Cost& c, Policy p) { return p == POL_F32 ? c.f32 : (p == POL_F64 ? c.f64 : c.df); }
+
+const Cost kRX{4, 4, 32};       // two real products and a sum per component
+const Cost kMUL{4, 4, 32};      // complex multiply (diagonal factor, table entry)
+const Cost kU1{8, 8, 80};       // two complex products and a sum
+const Cost kNEG{0, 0, 0};       // sign flips
+const Cost kU2{16, 16, 172};    // per amplitude of a 4x4 block
+const Cost kMACK{4, 4, 46};     // per amplitude per column of a 2^k block
+const Cost kCONV{0, 0, 72};     // FP64 <-> (hi, lo) split / join per pass
+
+double fraction(int bits) { return 1.0 / (double)(1u << bits); }
+
+}  // namespace
+
+double op_alu_per_amp(Policy pol, const DevOp& o) {
+  const int ctl = __builtin_popcountll(o.cmask) + __builtin_popcountll(o.gmask);
+  switch (o.type) {
+    case OP_RX: return pick(kRX, pol) * fraction(ctl);
+    case OP_U1: return pick(kU1, pol) * fraction(ctl);
+    case OP_DIAG: return pick(kMUL, pol) * fraction(ctl);
+    case OP_PHASE: return (o.mat < 0 ? pick(kNEG, pol) : pick(kMUL, pol)) * fraction(ctl);
+    case OP_U2: return pick(kU2, pol) * fraction(ctl);
+    case OP_DENSE: return pick(kMACK, pol) * (double)(1 << o.nk) * fraction(ctl);
+    default: return 0.0;
+  }
+}
+
+double stage_alu_per_amp(const CompileResult& cr, int st0, int nst) {
+  double a = pick(kCONV, cr.pol);
+  for (int k = st0; k < st0 + nst; k++) {
+    const StageRec& st = cr.stages[k];
+    if (st.kind == 1) {
+      for (int i = st.op0; i < st.op0 + st.nops; i++) a += op_alu_per_amp(cr.pol, cr.tile_ops[i]);
+      continue;
+    }
+    for (int i = st.op0; i < st.op0 + st.nops; i++) {
+      const RegOp& r = cr.reg_ops[i];
+      const int ctl = __builtin_popcount(r.csl) + __builtin_popcount(r.cot) + __builtin_popcountll(r.gmask);
+      switch (r.type) {
+        case OP_RX: a += pick(kRX, cr.pol) * fraction(ctl); break;
+        case OP_U1: a += pick(kU1, cr.pol) * fraction(ctl); break;
+        case OP_DIAG: case OP_DTAB: a += pick(kMUL, cr.pol) * fraction(ctl); break;
+        case OP_PHASE: a += (r.neg ? pick(kNEG, cr.pol) : pick(kMUL, cr.pol)) * fraction(ctl); break;
+        case OP_U2: a += pick(kU2, cr.pol) * fraction(ctl); break;
+        default: break;
+      }
+    }
+  }
+  return a;
 }
 
 }  // namespace qs

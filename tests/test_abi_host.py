@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_layout():
     assert ctypes.sizeof(_lib.qs_op) == 48
-    assert ctypes.sizeof(_lib.qs_compile_opts) == 32
+    assert ctypes.sizeof(_lib.qs_compile_opts) == 36
 
 
 def test_version():
