@@ -27,6 +27,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -270,11 +272,92 @@ def run_ours(args):
         modes["paper_alg1_m12"] = {"gates_per_s": round(G / (ms_pa / 1e3), 2), "passes": s_pa["n_passes"],
                                    "permutes": s_pa["n_permutes"], "nonlocal_gates": s_pa["n_comm_gates"]}
         out["modes"] = modes
+    if args.batched:
+        out["batched"] = measure_batched(qs, torch, args)
+    if args.serve_requests:
+        out["serving"] = measure_serving(args)
     if args.cpu_baseline and rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(args, n, circ)
     if pg:
         pg.destroy_process_group()
     return out, rank
+
+
+def measure_batched(qs, torch, args):
+    """The batched workload: `--batched` circuits (n ~ U{10..20}, depth ~ U{10..60}, Haar 2x2 on
+    every qubit + CNOT/CZ on a random matching per layer, seed 0), complex64, one persistent
+    launch per wave of tile passes replayed from a CUDA graph.  Beside it: the first 256
+    circuits run one plan launch sequence per circuit (qs_execute on separate states)."""
+    work = wc.batched_workload(args.batched, seed=0)
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    b = qs.Batch(work, dtype="c64", stream=stream)
+    build_s = time.perf_counter() - t0
+    for _ in range(3):
+        b.run()
+    b.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        b.run()
+    e1.record(stream)
+    b.sync()
+    ms = e0.elapsed_time(e1) / reps
+    st = b.stats()
+    norms = b.norms()
+    gates = st["n_gates"]
+    res = {"circuits": len(work), "gates": gates, "ms_per_run": round(ms, 3),
+           "circuits_per_s": round(len(work) / (ms / 1e3), 1), "gates_per_s": round(gates / (ms / 1e3), 1),
+           "waves": st["n_waves"], "passes": st["n_passes"], "state_gib": round(st["state_bytes"] / 2 ** 30, 2),
+           "build_s": round(build_s, 2), "norm_max_dev": float(np.max(np.abs(norms - 1.0)))}
+    # one launch sequence per circuit, on the first 256 circuits
+    sub = work[:256]
+    states = [qs.State(n, "c64", stream=stream) for n, _ in sub]
+    plans = [qs.compile(n, c, mode="tile", dtype="c64") for n, c in sub]
+    for s_, p_ in zip(states, plans):
+        s_.reset()
+        s_.execute(p_)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for s_, p_ in zip(states, plans):
+        s_.reset()
+        s_.execute(p_)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1)
+    sub_gates = sum(len(c) for _, c in sub)
+    res["solo_first256"] = {"circuits_per_s": round(len(sub) / (ms1 / 1e3), 1),
+                            "gates_per_s": round(sub_gates / (ms1 / 1e3), 1), "ms": round(ms1, 3)}
+    return res
+
+
+def measure_serving(args):
+    """The serving workload: random circuits (n = floor(exp(U(ln 12, ln 29))), depth U{20..100},
+    Haar 2x2 + CNOT/CZ layers, complex64 or complex128 with probability 1/2), Poisson arrivals.
+    First all requests at once (saturation throughput), then Poisson arrivals at fixed
+    fractions of that throughput; latency = arrival -> result read back on the host."""
+    from paper_2010_09746_gb300 import serve
+    budget = int(args.serve_mem_gib * (1 << 30))
+    reqs = wc.serving_workload(args.serve_requests, rate_hz=1.0, seed=0)
+    srv = serve.Server(slots=args.serve_slots, mem_budget=budget)
+    t0 = time.perf_counter()
+    res = srv.run(reqs, realtime=False)
+    wall = time.perf_counter() - t0
+    sat = len(reqs) / wall
+    out = {"requests_per_load": len(reqs), "slots": args.serve_slots, "mem_budget_gib": args.serve_mem_gib,
+           "saturation": dict(serve.latency_summary(res, wall), peak_in_flight=srv.peak_in_flight)}
+    for frac in (0.5, 0.9):
+        rate = frac * sat
+        reqs = wc.serving_workload(args.serve_requests, rate_hz=rate, seed=1)
+        srv = serve.Server(slots=args.serve_slots, mem_budget=budget)
+        t0 = time.perf_counter()
+        res = srv.run(reqs, realtime=True)
+        wall = time.perf_counter() - t0
+        out[f"load_{frac:.1f}"] = dict(serve.latency_summary(res, wall), offered_rate_hz=round(rate, 3),
+                                      peak_in_flight=srv.peak_in_flight)
+    return out
 
 
 def cpu_baseline(args, n, circ, budget_s=None):
@@ -339,6 +422,10 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--modes", type=int, default=1, help="also time per-gate and Algorithm 1 modes")
     ap.add_argument("--cpu-baseline", type=int, default=1)
+    ap.add_argument("--batched", type=int, default=4096, help="circuits in the batched measurement (0 = skip)")
+    ap.add_argument("--serve-requests", type=int, default=32, help="requests per serving load point (0 = skip)")
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-mem-gib", type=float, default=96.0)
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     args = ap.parse_args(argv)
     if args.impl == "reference":

@@ -17,7 +17,7 @@ from . import _lib
 from ._lib import (QS_ARITH_AUTO, QS_ARITH_DF, QS_ARITH_F64, QS_C64, QS_C128, QS_MODE_PAPER,
                    QS_MODE_PERGATE, QS_MODE_TILE, QS_ORDER_LOGICAL, QS_ORDER_STORAGE, QSError)
 
-__all__ = ["State", "Plan", "compile", "marshal", "use_torch_allocator", "QSError", "QS_C64", "QS_C128",
+__all__ = ["State", "Plan", "Batch", "compile", "marshal", "use_torch_allocator", "QSError", "QS_C64", "QS_C128",
            "QS_MODE_PERGATE", "QS_MODE_PAPER", "QS_MODE_TILE", "QS_ARITH_AUTO", "QS_ARITH_DF", "QS_ARITH_F64",
            "QS_ORDER_LOGICAL", "QS_ORDER_STORAGE", "lib_path"]
 
@@ -261,6 +261,64 @@ class State:
         out = ctypes.c_double()
         _lib.check(_L().qs_norm(self._h, ctypes.byref(out)))
         return out.value
+
+
+class Batch:
+    """Many independent circuits run together (qs_batch_create): list of (n, circuit)."""
+
+    def __init__(self, circuits, dtype="c64", stream=None, graph=True, **opts):
+        L = _L()
+        circuits = list(circuits)
+        self.count = len(circuits)
+        self.ns = [int(n) for n, _ in circuits]
+        self.dtype = _DTYPES[dtype]
+        allg = []
+        offs = [0]
+        for _, c in circuits:
+            c = list(c)
+            allg.extend(c)
+            offs.append(offs[-1] + len(c))
+        ops, nops, mats = marshal(allg)
+        n_arr = np.ascontiguousarray(self.ns, dtype=np.int32)
+        off_arr = np.ascontiguousarray(offs, dtype=np.int64)
+        o = _opts(dtype=dtype, **opts)
+        h = ctypes.c_void_p()
+        _lib.check(L.qs_batch_create(self.count, _ip(n_arr), ops, off_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                     _dp(mats), mats.size, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        if stream is not None:
+            ptr = getattr(stream, "cuda_stream", stream)
+            _lib.check(L.qs_batch_set_stream(h, ctypes.c_void_p(int(ptr) if ptr else 0)))
+        _lib.check(L.qs_batch_set_graph(h, 1 if graph else 0))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _L().qs_batch_destroy(h)
+            self._h = None
+
+    def run(self):
+        _lib.check(_L().qs_batch_run(self._h))
+
+    def sync(self):
+        _lib.check(_L().qs_batch_sync(self._h))
+
+    def norms(self) -> np.ndarray:
+        out = np.empty(self.count, dtype=np.float64)
+        _lib.check(_L().qs_batch_norms(self._h, _dp(out)))
+        return out
+
+    def amplitudes(self, i: int, first: int = 0, count: Optional[int] = None) -> np.ndarray:
+        if count is None:
+            count = (1 << self.ns[i]) - first
+        out = np.empty(count, dtype=np.complex128 if self.dtype == QS_C128 else np.complex64)
+        _lib.check(_L().qs_batch_get_amplitudes(self._h, int(i), out.ctypes.data_as(ctypes.c_void_p), first, count))
+        return out
+
+    def stats(self) -> dict:
+        st = _lib.qs_batch_stats()
+        _lib.check(_L().qs_batch_get_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_}
 
 
 _torch_cb = None

@@ -1,0 +1,50 @@
+"""GPU: the continuous-batching request loop.  Requests admitted while others are on the
+device overlap there; each result equals the same request run alone (bitwise: same plan,
+same kernels) and the FP64 oracle within the stated tolerance; admission never exceeds
+the memory budget."""
+import numpy as np
+import pytest
+
+from oracle import sv
+from workloads import circuits as wc
+
+pytestmark = pytest.mark.gpu
+
+qs = pytest.importorskip("paper_2010_09746_gb300")
+pytest.importorskip("torch")
+from paper_2010_09746_gb300 import serve  # noqa: E402
+
+TOL = {"c128": 1e-12, "c64": 1e-5}
+
+
+def make_requests(count, seed):
+    reqs = wc.serving_workload(count, rate_hz=2000.0, seed=seed, nmin=8, nmax=15, dmin=3, dmax=12)
+    return reqs
+
+
+def test_mix_equals_alone_and_oracle():
+    reqs = make_requests(24, seed=5)
+    budget = 6 * (1 << 15) * 16          # room for a few of the largest states only
+    srv = serve.Server(slots=6, mem_budget=budget, readout=1 << 15)
+    res = srv.run(reqs, realtime=True, timeout_s=120)
+    assert len(res) == len(reqs)
+    assert srv.peak_in_flight > 1, "no overlap happened"
+    assert srv.peak_mem <= budget
+    for rid, r in enumerate(reqs):
+        got = res[rid]
+        alone = serve.Server(slots=1, readout=1 << 15).run([r], realtime=False)[0]
+        assert got.amplitudes.tobytes() == alone.amplitudes.tobytes(), f"request {rid} depends on the mix"
+        assert got.norm == alone.norm
+        ref = sv.simulate(r.n, r.circuit)
+        err = np.abs(got.amplitudes.astype(np.complex128) - ref[: got.amplitudes.size]).max()
+        assert err <= TOL[r.dtype]
+        assert abs(got.norm - 1.0) <= TOL[r.dtype]
+    summ = serve.latency_summary(res)
+    assert summ["p99_ms"] >= summ["p50_ms"] > 0
+
+
+def test_oversized_request_rejected():
+    srv = serve.Server(slots=2, mem_budget=1 << 20)
+    r = wc.Request(0.0, 20, "c128", [])
+    with pytest.raises(ValueError):
+        srv.submit(0, r, 0.0)
