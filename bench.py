@@ -350,7 +350,7 @@ def measure_serving(args):
            "saturation": dict(serve.latency_summary(res, wall), peak_in_flight=srv.peak_in_flight)}
     for frac in (0.5, 0.9):
         rate = frac * sat
-        reqs = wc.serving_workload(args.serve_requests, rate_hz=rate, seed=1)
+        reqs = wc.serving_workload(args.serve_requests, rate_hz=rate, seed=0)   # same circuits, Poisson times
         srv = serve.Server(slots=args.serve_slots, mem_budget=budget)
         t0 = time.perf_counter()
         res = srv.run(reqs, realtime=True)

@@ -6,6 +6,8 @@
 // tile pass -- iff one of the qubits on which it acts non-diagonally sits outside the tile.
 // Controls and diagonal factors on any qubit are constants of a tile block.
 #include <chrono>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -102,10 +104,11 @@ struct Sched {
   // number of gates one program-order sweep would schedule if every gate whose
   // non-diagonal storage bits lie in `local` (a storage-bit mask) were runnable;
   // `tmp` is scratch of size G.
-  int closure(uint64_t local, const std::vector<uint64_t>& ndm, std::vector<char>& tmp, int cap = 1 << 30) const {
+  template <class Skip>
+  int closure(uint64_t local, const std::vector<uint64_t>& ndm, std::vector<char>& tmp, int cap, Skip skip) const {
     int cnt = 0;
     for (int v : rem) {
-      bool ok = (ndm[v] & ~local) == 0;
+      bool ok = (ndm[v] & ~local) == 0 && !skip(v);
       if (ok)
         for (int p : preds[v])
           if (!done[p] && !tmp[p]) {
@@ -117,6 +120,9 @@ struct Sched {
     }
     for (int v : rem) tmp[v] = 0;
     return cnt;
+  }
+  int closure(uint64_t local, const std::vector<uint64_t>& ndm, std::vector<char>& tmp) const {
+    return closure(local, ndm, tmp, 1 << 30, [](int) { return false; });
   }
 };
 
@@ -342,6 +348,22 @@ bool compile_tile(int n, const std::vector<HGate>& gates, const std::vector<int>
   for (int v = 0; v < G; v++) ndm[v] = nd_mask(gates[v], sigma);
   std::vector<char> tmp(G, 0);
   const uint64_t low = (c >= 64) ? ~0ull : ((1ull << c) - 1);
+  // fully diagonal gates none of whose qubits is in the tile are deferred to a pass that
+  // holds one of them (there they merge into a register phase table); only gates acting
+  // non-diagonally on those qubits depend on them, and those cannot run in this pass anyway
+  std::vector<char> allz(G, 0);
+  std::vector<uint64_t> qmask(G, 0);
+  int nondiag_left = 0;
+  for (int v = 0; v < G; v++) {
+    bool z = true;
+    for (int t = 0; t < gates[v].nq; t++) {
+      qmask[v] |= 1ull << sigma[gates[v].q[t]];
+      if (gates[v].cls[t] != CLS_Z) z = false;
+    }
+    allz[v] = z;
+    if (!z) nondiag_left++;
+  }
+  auto deferred = [&](int v, uint64_t T) { return allz[v] && (qmask[v] & T) == 0 && nondiag_left > 0; };
   for (int v = 0; v < G; v++)
     if (__builtin_popcountll(ndm[v] | low) > L) {
       *err = "gate " + std::to_string(v) + " needs more qubits than a tile holds";
@@ -360,7 +382,8 @@ bool compile_tile(int n, const std::vector<HGate>& gates, const std::vector<int>
       int best_b = -1, best_s = -1, best_d = -1;
       for (int b = 0; b < n; b++) {
         if ((T >> b) & 1) continue;
-        const int s = S.closure(T | (1ull << b), ndm, tmp);
+        const uint64_t T2 = T | (1ull << b);
+        const int s = S.closure(T2, ndm, tmp, 1 << 30, [&](int v) { return deferred(v, T2); });
         if (s > best_s || (s == best_s && demand[b] > best_d)) {
           best_s = s;
           best_d = demand[b];
@@ -374,8 +397,9 @@ bool compile_tile(int n, const std::vector<HGate>& gates, const std::vector<int>
     // the sweep of this pass
     std::vector<int> ids;
     for (int v : S.rem) {
-      if (S.done[v] || S.npred[v] != 0 || (ndm[v] & ~T)) continue;
+      if (S.done[v] || S.npred[v] != 0 || (ndm[v] & ~T) || deferred(v, T)) continue;
       S.mark(v);
+      if (!allz[v]) nondiag_left--;
       ids.push_back(v);
       if (o.max_ops > 0 && (int)ids.size() >= o.max_ops) break;
     }
@@ -430,6 +454,15 @@ bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<i
   }
   out->stats.hbm_bytes = bytes;
   out->stats.alu_instr = alu;
+  if (getenv("QS_DEBUG_OPMIX")) {
+    long cnt[16] = {0}, slot_only = 0, tb = 0, gb = 0;
+    for (const RegOp& r : out->reg_ops) {
+      cnt[r.type & 15]++;
+      if (r.type == OP_DIAG) { if (r.s0 >= 0) slot_only++; else if (r.tb >= 0) tb++; else gb++; }
+    }
+    fprintf(stderr, "regops: U1 %ld RX %ld DIAG %ld (slot %ld tb %ld gbit %ld) X %ld PHASE %ld U2 %ld DTAB %ld; stages %zu\n",
+            cnt[OP_U1], cnt[OP_RX], cnt[OP_DIAG], slot_only, tb, gb, cnt[OP_X], cnt[OP_PHASE], cnt[OP_U2], cnt[OP_DTAB], out->stages.size());
+  }
   out->stats.compile_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return true;

@@ -21,6 +21,7 @@ namespace {
 
 struct OpInfo {
   uint32_t need = 0;      // tile bits that must be in registers (non-diagonal targets)
+  uint32_t tbits = 0;     // every tile bit the op touches
   bool smem_only = false; // dense / swap
   int nb = 0;
   int bit[8];
@@ -33,6 +34,7 @@ OpInfo classify_op(const DevOp& o) {
     in.bit[in.nb] = b;
     in.cls[in.nb] = c;
     in.nb++;
+    in.tbits |= 1u << b;
   };
   const uint32_t cm = (uint32_t)o.cmask;
   for (int b = 0; b < 32; b++)
@@ -77,19 +79,59 @@ bool slot_only(const RegOp& r) {
   return true;
 }
 
-// Hoist every diagonal op left past the non-diagonal ops it commutes with (those whose
-// target slots it does not touch), then replace each run of two or more slot-only diagonal
-// factors by one table op: entry j of a 2^K-entry table is the product of the run's
-// factors at register index j (computed on the host in FP64).
+uint32_t ctrl_slots(const RegOp& r) { return r.csl; }
+
+// Two register ops must keep their order iff one changes a slot the other reads: a
+// non-diagonal op changes its target slots; every op reads its targets and slot controls.
+bool conflict(const RegOp& a, const RegOp& b) {
+  const uint32_t wa = is_diag(a) ? 0u : target_slots(a), wb = is_diag(b) ? 0u : target_slots(b);
+  const uint32_t ra = (is_diag(a) ? diag_slots(a) : target_slots(a)) | ctrl_slots(a);
+  const uint32_t rb = (is_diag(b) ? diag_slots(b) : target_slots(b)) | ctrl_slots(b);
+  return (wa & rb) || (wb & ra);
+}
+
+// Reorder a stage's ops (a valid linear extension of their conflicts) so that diagonal ops
+// form long runs -- repeatedly emit every ready diagonal op, then every ready non-diagonal
+// one -- and replace each run of two or more slot-only diagonal factors by one table op:
+// entry j of a 2^K-entry table is the product of the run's factors at register index j
+// (computed on the host in FP64).
 void merge_diagonals(std::vector<RegOp>& rl, int K, Pool& pool) {
-  for (size_t i = 1; i < rl.size(); i++) {
-    if (!is_diag(rl[i])) continue;
-    size_t j = i;
-    while (j > 0 && !is_diag(rl[j - 1]) && (target_slots(rl[j - 1]) & diag_slots(rl[j])) == 0) {
-      std::swap(rl[j - 1], rl[j]);
-      j--;
+  const int N = (int)rl.size();
+  std::vector<std::vector<int>> pred(N);
+  for (int j = 0; j < N; j++)
+    for (int i = 0; i < j; i++)
+      if (conflict(rl[i], rl[j])) pred[j].push_back(i);
+  std::vector<char> done(N, 0);
+  std::vector<RegOp> ord;
+  int left = N;
+  bool want_diag = true;
+  while (left > 0) {
+    std::vector<int> pick;
+    for (int j = 0; j < N; j++) {
+      if (done[j] || is_diag(rl[j]) != want_diag) continue;
+      bool ok = true;
+      for (int i : pred[j])
+        if (!done[i]) {
+          ok = false;
+          break;
+        }
+      if (ok) pick.push_back(j);
     }
+    // ops picked in this round do not depend on each other: same-kind ops of one round
+    // never conflict (diagonal ops commute; ready non-diagonal ops have no unfinished
+    // predecessor, and a conflicting pair would make the later one wait)
+    for (int j : pick) {
+      bool dep = false;
+      for (int i : pred[j])
+        if (!done[i]) dep = true;
+      if (dep) continue;
+      ord.push_back(rl[j]);
+      done[j] = 1;
+      left--;
+    }
+    want_diag = !want_diag;
   }
+  rl.swap(ord);
   std::vector<RegOp> out;
   size_t i = 0;
   const int D = 1 << K;
@@ -179,10 +221,20 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
     return true;
   };
   // ops one sweep schedules with register bits R (smem-only ops excluded)
+  // a diagonal op on tile bits none of which is in R waits for a stage that holds one of
+  // them, where it merges into the phase table; ops that depend on it act non-diagonally
+  // on its bits and cannot run in this stage either
+  int nondiag_left = 0;
+  for (int v = 0; v < N; v++)
+    if (info[v].need || info[v].smem_only) nondiag_left++;
+  auto deferred = [&](int v, uint32_t R) {
+    return !info[v].smem_only && info[v].need == 0 && info[v].tbits != 0 && (info[v].tbits & R) == 0 &&
+           nondiag_left > 0;
+  };
   auto closure = [&](uint32_t R) {
     int cnt = 0;
     for (int v : rem) {
-      bool ok = !info[v].smem_only && (info[v].need & ~R) == 0;
+      bool ok = !info[v].smem_only && (info[v].need & ~R) == 0 && !deferred(v, R);
       if (ok)
         for (int p : preds[v])
           if (!done[p] && !tmp[p]) {
@@ -256,7 +308,7 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
         nr++;
       }
       for (int v : rem) {
-        bool ok = !info[v].smem_only && (info[v].need & ~R) == 0;
+        bool ok = !info[v].smem_only && (info[v].need & ~R) == 0 && !deferred(v, R);
         if (ok)
           for (int p : preds[v])
             if (!done[p] && !tmp[p]) {
@@ -346,7 +398,10 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
       st.nops = (int)rl.size();
     }
     out->stages.push_back(st);
-    for (int v : take) done[v] = 1;
+    for (int v : take) {
+      done[v] = 1;
+      if (info[v].need || info[v].smem_only) nondiag_left--;
+    }
     size_t w = 0;
     for (size_t r = 0; r < rem.size(); r++)
       if (!done[rem[r]]) rem[w++] = rem[r];
