@@ -130,6 +130,34 @@ def job_rate(units_per_rank, world, max_ms):
     return world * units_per_rank / (max_ms / 1e3)
 
 
+KERNEL_SOURCES = ("paper_2010_09746_gb300/csrc/kernels_tile.cu", "paper_2010_09746_gb300/csrc/arith.cuh")
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel_name, n):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary
+    (profiles/<kernel>.md, measured on a smaller state and scaled by the amplitudes one
+    launch processes), or None when the kernel source changed since the capture."""
+    import re
+    path = os.path.join(ROOT, "profiles", f"{kernel_name}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_hash = re.search(r"kernel_source_sha1:\s*([0-9a-f]{40})", text)
+    m_b = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)\s+at\s+n\s*=\s*(\d+)", text)
+    if not m_hash or not m_b or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_b.group(1)) * 2.0 ** (n - int(m_b.group(2)))
+
+
 def roofline(kstats, steps, step_ms, peaks, peaks_kind, policy, clk_mhz):
     if not kstats:
         return None
@@ -158,7 +186,7 @@ def roofline(kstats, steps, step_ms, peaks, peaks_kind, policy, clk_mhz):
     bound = "alu" if out["alu"]["frac"] > out["hbm"]["frac"] else "hbm"
     sel = out[bound]
     out.update({"bound": bound, "achieved": sel["achieved"], "peak": sel["peak"], "unit": sel["unit"],
-                "frac": sel["frac"], "traffic": None})
+                "frac": sel["frac"], "traffic": None, "algorithmic_bytes": bytes_pl, "algorithmic_alu": alu_pl})
     return out
 
 
@@ -219,6 +247,8 @@ def run_ours(args):
 
     peaks, peaks_kind = load_peaks()
     roof = roofline(kstats, args.steps, ms, peaks, peaks_kind, policy, clk.get("sm_mhz"))
+    if roof:
+        roof["traffic"] = profiled_traffic(roof["kernel"], n)
     launches = int(round(sum(k["launches"] for k in kstats)))
     total_bytes = pstats["hbm_bytes"] + (1 << n) * (16 if args.dtype == "c128" else 8) * 2  # + init, norm
     out = {
@@ -272,6 +302,10 @@ def run_ours(args):
         modes["paper_alg1_m12"] = {"gates_per_s": round(G / (ms_pa / 1e3), 2), "passes": s_pa["n_passes"],
                                    "permutes": s_pa["n_permutes"], "nonlocal_gates": s_pa["n_comm_gates"]}
         out["modes"] = modes
+    if args.small and args.workload == "rzrx30":
+        out["haar_cnot_12q"] = measure_small(qs, torch, args)
+    if args.qft and args.workload == "rzrx30":
+        out["qft_like"] = measure_qft_like(qs, torch, st, stream, args)
     if args.batched:
         out["batched"] = measure_batched(qs, torch, args)
     if args.serve_requests:
@@ -281,6 +315,75 @@ def run_ours(args):
     if pg:
         pg.destroy_process_group()
     return out, rank
+
+
+def measure_small(qs, torch, args):
+    """12 qubits (64 KiB state, cache-resident: launch-bound), 20 layers of Haar 2x2 on every
+    qubit + CNOT on a random perfect matching, seeds 0..19; gates/s per mode, with the
+    step's launches replayed from a captured CUDA graph and without."""
+    n, dt = 12, args.dtype
+    circs = [wc.haar_cnot_circuit(n, 20, seed=s) for s in range(20)]
+    G = sum(len(c) for c in circs)
+    stream = torch.cuda.Stream()
+    res = {"circuits": len(circs), "gates": G}
+    for mode in ("tile", "paper", "pergate"):
+        kw = {"tile_bits": 8} if mode == "paper" else {}
+        plans = [qs.compile(n, c, mode=mode, dtype=dt, arith=args.arith, **kw) for c in circs]
+        st = qs.State(n, dt, arith=args.arith, stream=stream)
+
+        def run_all():
+            for p in plans:
+                st.reset()
+                st.execute(p)
+
+        run_all()   # uploads the plans
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(stream)
+        for _ in range(reps):
+            run_all()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        entry = {"gates_per_s": round(G / (ms / 1e3), 1), "launches_per_circuit": plans[0].stats()["n_passes"]
+                 + plans[0].stats()["n_pergate"] + plans[0].stats()["n_permutes"] + 1}
+        if mode != "paper":   # permutations swap buffers on the host: not replayable as one graph
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
+                run_all()
+            g.replay()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(reps):
+                g.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            msg = e0.elapsed_time(e1) / reps
+            entry["graph_gates_per_s"] = round(G / (msg / 1e3), 1)
+        res[mode] = entry
+        st.close()
+    return res
+
+
+def measure_qft_like(qs, torch, st, stream, args):
+    """Appendix C's QFT-like circuit (controlled-Rz replaced by CNOT) on the same state:
+    the tile passes vs Algorithm 1 at m = 12 (whose permutation count the appendix bounds
+    by 2(n - m)) vs one kernel per gate."""
+    n = args.n
+    circ = wc.qft_like_circuit(n)
+    res = {"gates": len(circ)}
+    for mode, kw in (("tile", {}), ("paper_alg1_m12", {"mode": "paper", "tile_bits": 12}), ("pergate", {"mode": "pergate"})):
+        opts = dict(mode="tile", dtype=args.dtype, arith=args.arith)
+        opts.update(kw)
+        plan = qs.compile(n, circ, **opts)
+        ms, _, _ = measure(qs, st, plan, 1, 1, torch, stream)
+        ps = plan.stats()
+        res[mode] = {"gates_per_s": round(len(circ) / (ms / 1e3), 2), "ms": round(ms, 2), "passes": ps["n_passes"],
+                     "permutes": ps["n_permutes"], "pergate_kernels": ps["n_pergate"]}
+    res["paper_alg1_m12"]["permute_bound_2(n-m)"] = 2 * (n - 12)
+    return res
 
 
 def measure_batched(qs, torch, args):
@@ -422,6 +525,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--modes", type=int, default=1, help="also time per-gate and Algorithm 1 modes")
     ap.add_argument("--cpu-baseline", type=int, default=1)
+    ap.add_argument("--qft", type=int, default=1, help="also time Appendix C's QFT-like circuit")
+    ap.add_argument("--small", type=int, default=1, help="also time the 12-qubit Haar + CNOT circuits")
     ap.add_argument("--batched", type=int, default=4096, help="circuits in the batched measurement (0 = skip)")
     ap.add_argument("--serve-requests", type=int, default=32, help="requests per serving load point (0 = skip)")
     ap.add_argument("--serve-slots", type=int, default=8)

@@ -71,7 +71,10 @@ enum {
   QS_OP_CU = 14,  /* controlled arbitrary 2x2, matrix at mats[mat .. mat+7] */
   QS_OP_SWAP = 15,
   QS_OP_U2 = 16,  /* arbitrary 4x4, 32 doubles at mats[mat ..] */
-  QS_OP_UK = 17   /* arbitrary 2^k x 2^k (k = nq <= 6), 2*4^k doubles at mats[mat ..] */
+  QS_OP_UK = 17,  /* arbitrary 2^k x 2^k (k = nq <= 6), 2*4^k doubles at mats[mat ..] */
+  QS_OP_RELABEL = 18  /* Emulated-SWAP (Appendix B): the two qubits exchange storage positions
+                         in sigma, no amplitude moves; preceded by a SWAP it is the paper's
+                         PermuteQubits of one transposition.  QS_MODE_PERGATE only. */
 };
 
 /* One gate of a circuit.  48 bytes, no padding. */

@@ -71,7 +71,7 @@ def gate_full_matrix(g) -> np.ndarray:
         # qubits = (control, target): r = b(c) + 2 b(t); control=1 rows are r = 1, 3
         m[1, 1], m[1, 3], m[3, 1], m[3, 3] = u[0, 0], u[0, 1], u[1, 0], u[1, 1]
         return m
-    if k == "SWAP":
+    if k in ("SWAP", "RELABEL"):   # an Emulated-SWAP acts as a SWAP on hardware (Appendix B)
         return SWAP4.copy()
     raise ValueError(k)
 

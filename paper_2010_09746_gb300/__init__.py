@@ -124,6 +124,23 @@ class Plan:
         _lib.check(_L().qs_plan_final_permutation(self._h, _ip(out)))
         return [int(x) for x in out]
 
+    def export_swaps(self, circuit):
+        """QS_MODE_PAPER schedule as a plain gate list for any backend (Appendix B): the gates
+        in scheduled order, every PermuteQubits(l <-> g) written as SWAP(l, g) followed by the
+        Emulated-SWAP RELABEL(l, g).  On hardware RELABEL is a SWAP (the pair cancels); on this
+        simulator it only exchanges storage positions, so SWAP + RELABEL moves the data."""
+        from types import SimpleNamespace
+        circuit = list(circuit)
+        out = []
+        for kind, v in self.trace():
+            if kind in (0, 1):
+                out.append(circuit[v])
+            elif kind == 2:
+                l, g = divmod(v, 64)
+                out.append(SimpleNamespace(kind="SWAP", qubits=(l, g), param=0.0, matrix=None))
+                out.append(SimpleNamespace(kind="RELABEL", qubits=(l, g), param=0.0, matrix=None))
+        return out
+
     def trace(self):
         cnt = ctypes.c_size_t()
         _lib.check(_L().qs_plan_get_trace(self._h, None, None, 0, ctypes.byref(cnt)))

@@ -432,12 +432,23 @@ bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<i
   out->stats = qs_plan_stats{};
   out->stats.n_gates = (int64_t)gates.size();
   bool ok = true;
+  bool has_relabel = false;
+  for (const HGate& g : gates) has_relabel |= g.kind == QS_OP_RELABEL;
+  if (has_relabel && o.mode != QS_MODE_PERGATE) {
+    *err = "RELABEL (Emulated-SWAP) ops need QS_MODE_PERGATE";
+    return false;
+  }
   if (o.mode == QS_MODE_PERGATE) {
+    std::vector<int> sigma = sigma0;
     for (const HGate& g : gates) {
-      if (!emit_gate(n, g, sigma0, store_bytes, out, err)) return false;
+      if (g.kind == QS_OP_RELABEL) {   // storage positions change hands, no data moves
+        std::swap(sigma[g.q[0]], sigma[g.q[1]]);
+        continue;
+      }
+      if (!emit_gate(n, g, sigma, store_bytes, out, err)) return false;
       out->stats.n_pergate++;
     }
-    out->sigma_final = sigma0;
+    out->sigma_final = sigma;
   } else if (o.mode == QS_MODE_PAPER) {
     ok = compile_paper(n, gates, sigma0, o, store_bytes, out, err);
   } else if (o.mode == QS_MODE_TILE) {

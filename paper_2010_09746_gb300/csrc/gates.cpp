@@ -57,6 +57,7 @@ bool make_hgate(int n, const qs_op& op, const double* mats, size_t nmats, HGate*
     case QS_OP_RZ: case QS_OP_RX: case QS_OP_RY: case QS_OP_P:
       nq = 1; break;
     case QS_OP_CNOT: case QS_OP_CZ: case QS_OP_CP: case QS_OP_CU: case QS_OP_SWAP: case QS_OP_U2:
+    case QS_OP_RELABEL:
       nq = 2; break;
     case QS_OP_UK:
       nq = op.nq;
@@ -105,7 +106,7 @@ bool make_hgate(int n, const qs_op& op, const double* mats, size_t nmats, HGate*
     g->U[1 * 4 + 3] = m[1];
     g->U[3 * 4 + 1] = m[2];
     g->U[3 * 4 + 3] = m[3];
-  } else if (op.kind == QS_OP_SWAP) {
+  } else if (op.kind == QS_OP_SWAP || op.kind == QS_OP_RELABEL) {
     g->U[0] = 1; g->U[1 * 4 + 2] = 1; g->U[2 * 4 + 1] = 1; g->U[15] = 1;
   } else {   // U2, UK
     const double* p = need_mat((size_t)2 * D * D);

@@ -434,6 +434,19 @@ __device__ __forceinline__ void apply_regop(typename A::reg_t (&x)[1 << K], cons
   (void)sizeof(R);
 }
 
+// A register op is read by every thread of the CTA: two 16-byte read-only loads instead of
+// one load per field.
+__device__ __forceinline__ RegOp load_regop(const RegOp* p) {
+  static_assert(sizeof(RegOp) == 32 && alignof(RegOp) <= 16, "RegOp is loaded as two 16-byte words");
+  const uint4* q = reinterpret_cast<const uint4*>(p);
+  const uint4 a = __ldg(q), b = __ldg(q + 1);
+  RegOp r;
+  uint4* w = reinterpret_cast<uint4*>(&r);
+  w[0] = a;
+  w[1] = b;
+  return r;
+}
+
 // One register stage over the whole tile.  from_store / to_store: the shared-memory tile
 // holds storage-format elements before / after the stage (policies whose register format
 // differs from the storage format convert here instead of in a separate pass).
@@ -468,7 +481,7 @@ __device__ __forceinline__ void run_reg_stage(typename A::reg_t* T, const StageR
       }
     }
     for (int k = 0; k < sr.nops; k++) {
-      const RegOp op = rops[sr.op0 + k];
+      const RegOp op = load_regop(rops + sr.op0 + k);
       if ((base & op.gmask) != op.gmask) continue;
       apply_regop<A, K>(x, op, pool, gidx, base);
     }

@@ -52,8 +52,8 @@ static_assert(sizeof(DevOp) == 64, "DevOp layout");
 // Register-stage op: a tile op whose target bits are held in registers.  Slots index the
 // stage's register bits; controls are split into register slots (csl) and tile bits
 // outside the registers (cot); gmask is the block predicate (storage bits outside the tile).
-struct RegOp {
-  int32_t type;       // OP_U1, OP_RX, OP_X, OP_DIAG, OP_PHASE, OP_U2
+struct alignas(16) RegOp {
+  int32_t type;       // OP_U1, OP_RX, OP_X, OP_DIAG, OP_PHASE, OP_U2, OP_DTAB
   int8_t s0, s1;      // register slots of the target bit(s), -1 if none
   int8_t tb;          // OP_DIAG on a tile bit outside the registers, -1 if none
   int8_t neg;         // OP_PHASE: exact sign flip

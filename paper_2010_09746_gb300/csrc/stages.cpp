@@ -92,7 +92,7 @@ bool conflict(const RegOp& a, const RegOp& b) {
 
 // Reorder a stage's ops (a valid linear extension of their conflicts) so that diagonal ops
 // form long runs -- repeatedly emit every ready diagonal op, then every ready non-diagonal
-// one -- and replace each run of two or more slot-only diagonal factors by one table op:
+// one -- and replace the slot-only diagonal factors of each run by one table op:
 // entry j of a 2^K-entry table is the product of the run's factors at register index j
 // (computed on the host in FP64).
 void merge_diagonals(std::vector<RegOp>& rl, int K, Pool& pool) {
@@ -144,7 +144,7 @@ void merge_diagonals(std::vector<RegOp>& rl, int K, Pool& pool) {
     while (e < rl.size() && is_diag(rl[e])) e++;
     std::vector<RegOp> fac, rest;
     for (size_t k = i; k < e; k++) (slot_only(rl[k]) ? fac : rest).push_back(rl[k]);
-    if (fac.size() >= 2) {
+    if (!fac.empty()) {   // even a single slot factor: a table multiply avoids per-element selects
       std::vector<cd> tab(D, cd(1, 0));
       for (const RegOp& r : fac) {
         for (int j = 0; j < D; j++) {

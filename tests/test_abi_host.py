@@ -174,3 +174,23 @@ def test_tile_mode_pass_count_beats_per_gate():
     assert st["n_passes"] < 300
     pg = qs.compile(n, circ, mode="pergate").stats()
     assert st["hbm_bytes"] < pg["hbm_bytes"] / 5
+
+
+def test_appendix_b_export_is_the_circuit_on_hardware():
+    """SWAP + Emulated-SWAP export (Appendix B): with RELABEL read as a hardware SWAP every
+    pair cancels, so the exported list simulates to the original circuit."""
+    n, m = 10, 7
+    circ = wc.paper_random_circuit(n, 0.3, seed=3)
+    plan = qs.compile(n, circ, mode="paper", tile_bits=m)
+    ir = plan.export_swaps(circ)
+    assert sum(1 for g in ir if g.kind == "RELABEL") == plan.stats()["n_permutes"] > 0
+    hw = [wc.Gate(g.kind, g.qubits, g.param, g.matrix) for g in ir]
+    np.testing.assert_allclose(sv.simulate(n, hw), sv.simulate(n, circ), atol=1e-12)
+
+
+def test_relabel_only_in_pergate_mode():
+    c = [wc.Gate("H", (0,)), wc.Gate("RELABEL", (0, 1))]
+    assert _compile_status(3, c, mode="pergate") == _lib.QS_OK
+    assert _compile_status(3, c, mode="tile") == _lib.QS_EINVAL
+    p = qs.compile(3, c, mode="pergate")
+    assert p.final_permutation() == [1, 0, 2]

@@ -204,3 +204,17 @@ def test_df_conversion_round_trip():
     # per real component: |err| <= 2^-46 |x| + 2^-120 (the low word flushes below the float range)
     for a, b in ((got.real, psi.real), (got.imag, psi.imag)):
         assert np.all(np.abs(a - b) <= 2.0 ** -46 * np.abs(b) + 2.0 ** -120)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_appendix_b_export_runs_as_permutations(dtype):
+    """The exported SWAP + Emulated-SWAP list run per gate on the GPU: SWAP moves data,
+    RELABEL changes sigma, and the logical state is the original circuit's."""
+    n, m = 11, 8
+    circ = wc.paper_random_circuit(n, 0.3, seed=4)
+    plan = qs.compile(n, circ, mode="paper", tile_bits=m)
+    ir = plan.export_swaps(circ)
+    st = qs.State(n, dtype)
+    st.run(ir, mode="pergate")
+    assert st.permutation() == plan.final_permutation()
+    check(st.amplitudes(), sv.simulate(n, circ), dtype)

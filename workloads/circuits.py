@@ -35,6 +35,7 @@ KINDS = (
     "SWAP",    # exchange of two qubits
     "U2",      # arbitrary 4x4 on (q0, q1), matrix given
     "UK",      # arbitrary 2^k x 2^k on k qubits, matrix given
+    "RELABEL", # Emulated-SWAP (Appendix B): exchange two qubits' storage positions, no data moved
 )
 
 
@@ -238,7 +239,7 @@ def random_mixed_circuit(n: int, ngates: int, seed: int, kinds: Sequence[str] = 
     """Random circuit drawing every gate kind (for parity tests)."""
     rng = np.random.default_rng(seed)
     if kinds is None:
-        kinds = [k for k in KINDS if not (k == "UK" and n < 1)]
+        kinds = [k for k in KINDS if k != "RELABEL"]
     c: Circuit = []
     for _ in range(ngates):
         kind = kinds[int(rng.integers(0, len(kinds)))]
