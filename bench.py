@@ -214,6 +214,29 @@ def measure(qs, st, plan, steps, warmup, torch, stream, profile=False):
     return e0.elapsed_time(e1) / steps, norms, ks
 
 
+def fit_cost_model(dtype, runs):
+    """Per kernel class, least squares t = c_launch*launches + c_byte*bytes + c_alu*instructions
+    over the CUDA-event totals of these runs (one sample per class and run); then each
+    plan's step time predicted from its compile-time statistics (plus the state
+    initialisation and the norm) against the measured one."""
+    from paper_2010_09746_gb300 import tuning
+    m = tuning.CostModel()
+    for _, (_, _, ks, steps) in runs.items():
+        m.add_kernel_stats([dict(k, launches=k["launches"] / steps, total_ms=k["total_ms"] / steps,
+                                 bytes=k["bytes"] / steps, alu=k["alu"] / steps) for k in ks])
+    coef = m.fit()
+    pred = {}
+    for name, (p, ms, _, _) in runs.items():
+        t = m.predict_plan(p, dtype)
+        sb = (1 << p.n) * (16 if dtype == "c128" else 8)
+        for cls in ("init", "norm"):
+            if t is not None and cls in coef:
+                t += m.predict(cls, 1, sb, 0)
+        pred[name] = {"predicted_ms": None if t is None else round(t, 3), "measured_ms": round(ms, 3)}
+    return {"coef_ms_per_launch_byte_instr": {k: [float(f"{x:.4g}") for x in v] for k, v in coef.items()},
+            "plans": pred}
+
+
 def run_ours(args):
     import torch
 
@@ -293,21 +316,30 @@ def run_ours(args):
         per_layer = 2 * n + n // 4 if args.workload == "rzrx30" else len(circ) // 20
         sub = circ[: 4 * per_layer]   # first 4 layers
         p_pg = qs.compile(n, sub, mode="pergate", dtype=args.dtype, arith=args.arith)
-        ms_pg, _, _ = measure(qs, st, p_pg, 1, 1, torch, stream)
+        ms_pg, _, ks_pg = measure(qs, st, p_pg, 1, 1, torch, stream, profile=True)
         modes["pergate"] = {"gates_per_s": round(len(sub) / (ms_pg / 1e3), 2), "sample": f"first {len(sub)} gates",
                             "kernels": p_pg.stats()["n_pergate"]}
         p_pa = qs.compile(n, circ, mode="paper", dtype=args.dtype, arith=args.arith, tile_bits=12)
-        ms_pa, _, _ = measure(qs, st, p_pa, 1, 1, torch, stream)
+        ms_pa, _, ks_pa = measure(qs, st, p_pa, 1, 1, torch, stream, profile=True)
         s_pa = p_pa.stats()
         modes["paper_alg1_m12"] = {"gates_per_s": round(G / (ms_pa / 1e3), 2), "passes": s_pa["n_passes"],
                                    "permutes": s_pa["n_permutes"], "nonlocal_gates": s_pa["n_comm_gates"]}
         out["modes"] = modes
+        out["cost_model"] = fit_cost_model(args.dtype, {"tile": (plan, ms, kstats, args.steps),
+                                                        "pergate": (p_pg, ms_pg, ks_pg, 1),
+                                                        "paper_alg1_m12": (p_pa, ms_pa, ks_pa, 1)})
     if args.small and args.workload == "rzrx30":
         out["haar_cnot_12q"] = measure_small(qs, torch, args)
     if args.qft and args.workload == "rzrx30":
         out["qft_like"] = measure_qft_like(qs, torch, st, stream, args)
     if args.batched:
         out["batched"] = measure_batched(qs, torch, args)
+    if args.dense and args.workload == "rzrx30":
+        out["dense_k"] = measure_dense(qs, torch, args)
+    if args.precision and args.workload == "rzrx30":
+        st.close()
+        torch.cuda.empty_cache()
+        out["precision"] = measure_precision(qs, torch, args)
     if args.serve_requests:
         out["serving"] = measure_serving(args)
     if args.cpu_baseline and rank == 0 and world == 1:
@@ -364,6 +396,121 @@ def measure_small(qs, torch, args):
             entry["graph_gates_per_s"] = round(G / (msg / 1e3), 1)
         res[mode] = entry
         st.close()
+    return res
+
+
+def measure_dense(qs, torch, args):
+    """Dense k-qubit blocks (Haar 2^k x 2^k, seed k) on a 30-qubit complex64 state: the
+    CUDA-core kernel against the tensor-core kernel, qubits on storage bits 0..k-1, and at
+    k = 6 also on high qubits (the tensor path then permutes first).  Per application: CUDA
+    events on the state's stream, best of 3 after a warm-up; HBM fraction of the measured
+    copy bandwidth; tensor TF32 FLOP/s (three split products) against the measured bf16
+    peak x 1.1/2.25 (the nominal tf32 : bf16 ratio)."""
+    n = 30
+    peaks, _ = load_peaks()
+    tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25
+    stream = torch.cuda.Stream()
+    st = qs.State(n, "c64", stream=stream)
+    S = (1 << n) * 8
+    res = {"n_qubits": n, "state": "complex64", "tf32_peak_tflops": round(tf32_peak, 1)}
+
+    def timed_apply(U, qubits, reps=3):
+        st.apply_dense(U, qubits)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st.apply_dense(U, qubits)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    for k in (4, 5, 6):
+        U = wc.haar_unitary(1 << k, np.random.default_rng(k))
+        row = {}
+        for path in ("cuda_cores", "tensor"):
+            st.reset()
+            st.set_dense_path(path)
+            ms = timed_apply(U, list(range(k)))
+            gbs = 2 * S / (ms * 1e-3) / 1e9
+            row[path] = {"ms": round(ms, 3), "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / peaks["hbm_gbs"], 4)}
+            if path == "tensor":
+                tf = 3 * 2 * 128 * 128 * (1 << (n - 6)) / (ms * 1e-3) / 1e12
+                row[path]["tf32_tflops"] = round(tf, 1)
+                row[path]["tensor_frac"] = round(tf / tf32_peak, 4)
+        row["tensor_speedup"] = round(row["cuda_cores"]["ms"] / row["tensor"]["ms"], 2)
+        res[f"k{k}_low"] = row
+    U = wc.haar_unitary(64, np.random.default_rng(6))
+    high = [24, 25, 26, 27, 28, 29]
+    row = {}
+    for path in ("cuda_cores", "tensor"):
+        st.reset()
+        st.set_dense_path(path)
+        # the tensor path permutes these qubits to the bottom on the first call only, so time
+        # alternating qubit sets to include a permutation in every application
+        alt = [high, [18, 19, 20, 21, 22, 23]]
+        st.apply_dense(U, alt[0])
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(4):
+            st.apply_dense(U, alt[(i + 1) % 2])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        row[path] = {"ms": round(e0.elapsed_time(e1) / 4, 3)}
+    row["tensor_speedup"] = round(row["cuda_cores"]["ms"] / row["tensor"]["ms"], 2)
+    res["k6_high_with_permute"] = row
+    st.close()
+    torch.cuda.empty_cache()
+    return res
+
+
+def measure_precision(qs, torch, args):
+    """The precision study: 32 qubits, the same construction at depth 30 (2160 gates), run
+    as complex128 (double-float arithmetic, 64 GiB) and as complex64 (32 GiB, with and without
+    renormalisation after every 4 passes); the full-state fidelity 1 - |<psi64|psi128>|^2 /
+    (norms) and both norms, every reduction in FP64 on the device; then 33 qubits complex64
+    (64 GiB), norm only."""
+    stream = torch.cuda.Stream()
+    n = 32
+    circ = wc.rzrx_cz_circuit(n, 30, seed=0)
+    res = {"circuit": f"rzrx_cz_{n}q_30layers", "gates": len(circ)}
+
+    def timed_run(st, plan):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        st.reset()
+        e0.record(stream)
+        st.execute(plan)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    s128 = qs.State(n, "c128", stream=stream)
+    ms128 = timed_run(s128, qs.compile(n, circ, mode="tile", dtype="c128"))
+    res["c128"] = {"ms": round(ms128, 1), "gates_per_s": round(len(circ) / ms128 * 1e3, 1),
+                   "norm_dev": abs(s128.norm() - 1.0)}
+    s64 = qs.State(n, "c64", stream=stream)
+    for R in (0, 4):
+        ms64 = timed_run(s64, qs.compile(n, circ, mode="tile", dtype="c64", renorm_every=R))
+        key = "c64" if R == 0 else f"c64_renorm_every_{R}"
+        res[key] = {"ms": round(ms64, 1), "gates_per_s": round(len(circ) / ms64 * 1e3, 1),
+                    "norm_dev": abs(s64.norm() - 1.0), "fidelity_loss_vs_c128": 1.0 - s64.fidelity(s128)}
+    s64.close()
+    s128.close()
+    torch.cuda.empty_cache()
+    n = 33
+    circ = wc.rzrx_cz_circuit(n, 30, seed=0)
+    s = qs.State(n, "c64", stream=stream)
+    ms = timed_run(s, qs.compile(n, circ, mode="tile", dtype="c64"))
+    res["c64_33q"] = {"gates": len(circ), "ms": round(ms, 1), "gates_per_s": round(len(circ) / ms * 1e3, 1),
+                      "norm_dev": abs(s.norm() - 1.0)}
+    s.close()
+    torch.cuda.empty_cache()
     return res
 
 
@@ -450,7 +597,9 @@ def measure_serving(args):
     wall = time.perf_counter() - t0
     sat = len(reqs) / wall
     out = {"requests_per_load": len(reqs), "slots": args.serve_slots, "mem_budget_gib": args.serve_mem_gib,
-           "saturation": dict(serve.latency_summary(res, wall), peak_in_flight=srv.peak_in_flight)}
+           "batch_small_n": srv.batch_small_n,
+           "saturation": dict(serve.latency_summary(res, wall), peak_in_flight=srv.peak_in_flight,
+                              batched_requests=srv.batched_requests, batches=srv.batches)}
     for frac in (0.5, 0.9):
         rate = frac * sat
         reqs = wc.serving_workload(args.serve_requests, rate_hz=rate, seed=0)   # same circuits, Poisson times
@@ -459,7 +608,8 @@ def measure_serving(args):
         res = srv.run(reqs, realtime=True)
         wall = time.perf_counter() - t0
         out[f"load_{frac:.1f}"] = dict(serve.latency_summary(res, wall), offered_rate_hz=round(rate, 3),
-                                      peak_in_flight=srv.peak_in_flight)
+                                      peak_in_flight=srv.peak_in_flight, batched_requests=srv.batched_requests,
+                                      batches=srv.batches)
     return out
 
 
@@ -526,6 +676,10 @@ def main(argv=None):
     ap.add_argument("--modes", type=int, default=1, help="also time per-gate and Algorithm 1 modes")
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--qft", type=int, default=1, help="also time Appendix C's QFT-like circuit")
+    ap.add_argument("--dense", type=int, default=1,
+                    help="also time dense k-qubit blocks on CUDA cores vs tensor cores (30q complex64)")
+    ap.add_argument("--precision", type=int, default=1,
+                    help="also run the 32q complex128/complex64 and 33q complex64 precision study")
     ap.add_argument("--small", type=int, default=1, help="also time the 12-qubit Haar + CNOT circuits")
     ap.add_argument("--batched", type=int, default=4096, help="circuits in the batched measurement (0 = skip)")
     ap.add_argument("--serve-requests", type=int, default=32, help="requests per serving load point (0 = skip)")

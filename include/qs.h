@@ -98,6 +98,12 @@ typedef enum {
                            the pass's addressing, so no separate permutation pass is needed */
 } qs_mode;
 
+/* qs_compile_opts.flags.  By default an uncontrolled RX held in registers is applied in the
+ * cheaper tangent form, (I - i tan X) or (cot I - i X), with the dropped cos / sin factors
+ * of a tile pass multiplied into one full-form RX of that pass (same result up to
+ * rounding); this flag keeps every RX in full form. */
+enum { QS_FLAG_FULL_RX = 1 };
+
 typedef struct {
   int32_t mode;       /* qs_mode */
   int32_t dtype;      /* qs_dtype of the states the plan will run on */
@@ -109,10 +115,15 @@ typedef struct {
                          amplitudes); 0 = default */
   int32_t max_ops;    /* cap on gates per tile pass, 0 = none */
   int32_t scoring;    /* Algorithm 1 candidate score: 0 = closure (default), 1 = frontier */
-  int32_t flags;      /* reserved, must be 0 */
+  int32_t flags;      /* QS_FLAG_* bits; others must be 0 */
   int32_t reg_bits;   /* tile bits each thread holds in registers in a register stage (2^reg_bits
                          amplitudes per thread), 1..5 (complex128 1..4); 0 = default (4 for
                          complex128, 5 for complex64) */
+  int32_t renorm_every; /* periodic renormalisation (no counterpart in the paper): after every
+                           `renorm_every` kernels of the plan (tile passes, per-gate kernels,
+                           permutations) the state is divided by the square root of its FP64
+                           norm, as by qs_renormalize; 0 = never.  Each costs one read for the
+                           norm and one read + write for the scaling. */
 } qs_compile_opts;
 
 typedef struct {
@@ -191,8 +202,25 @@ qs_status qs_apply_2q(qs_handle h, const double* U, int q0, int q1);
  * (CNOT is U = X). */
 qs_status qs_apply_controlled(qs_handle h, const double* U, int c, int t);
 
-/* Dense k-qubit gate (1 <= k <= 6, 2*4^k doubles) on distinct logical qubits[0..k-1]. */
+/* Dense k-qubit gate (1 <= k <= 6, 2*4^k doubles) on distinct logical qubits[0..k-1].
+ * Fusing gates into such blocks is the prior work the paper builds on (Sec. 1).  Two
+ * engines (qs_set_dense_path): the strided kernel on the CUDA cores (every dtype), and for
+ * complex64 states with n >= 12 the tensor-core kernel, which applies the block to storage
+ * bits 0..5 as one real 128 x 128 matrix product per row of 64 amplitudes (TF32 operands
+ * with a three-term split, FP32 accumulation: complex64 accuracy).  If the qubits are not
+ * on storage bits 0..k-1 the tensor path first permutes the state so that qubits[t] is on
+ * storage bit t (one permutation kernel, Sec. 2 PermuteQubits; sigma changes). */
 qs_status qs_apply_dense(qs_handle h, const double* U, int k, const int* qubits);
+
+typedef enum {
+  QS_DENSE_AUTO = 0,        /* tensor cores for complex64 when k >= 5 with the qubits already on
+                               storage bits 0..k-1, or k = 6 (after a permutation); else CUDA cores */
+  QS_DENSE_CUDA_CORES = 1,  /* always the strided CUDA-core kernel */
+  QS_DENSE_TENSOR = 2       /* always the tensor-core kernel (QS_EINVAL unless complex64, n >= 12) */
+} qs_dense_path;
+
+/* Engine for this state's later qs_apply_dense calls (default QS_DENSE_AUTO). */
+qs_status qs_set_dense_path(qs_handle h, int path);
 
 /* ---- qubit permutation (Sec. 2 PermuteQubits; Appendix A) -------------------------- */
 
@@ -291,6 +319,28 @@ qs_status qs_set_amplitudes(qs_handle h, const void* in);
 /* sum_i |alpha_i|^2 accumulated in FP64 with a fixed reduction order (deterministic).
  * Synchronises the stream. */
 qs_status qs_norm(qs_handle h, double* out);
+
+/* ---- precision helpers (no counterpart in the paper) ------------------------------- *
+ * A state stored as complex64 drifts from unit norm by rounding, about 2^-24 relative per
+ * gate application; these calls measure that drift against another state and remove it,
+ * with every reduction in FP64. */
+
+/* <a|b> = sum_i conj(alpha_i) beta_i over logical indices i, accumulated in FP64 with a
+ * fixed reduction order; out[0] = real part, out[1] = imaginary part (HOST memory).  The
+ * two states may have different dtypes (complex64 against complex128 is the precision
+ * study) but must have the same n and the same sigma (else QS_EINVAL: permute one of them
+ * first).  Runs on a's stream after b's stream has reached the point of the call (an
+ * event), uses a temporary device buffer of 1216 * 16 + 16 bytes from the allocator, and
+ * synchronises a's stream. */
+qs_status qs_inner(qs_handle a, qs_handle b, double* out);
+
+/* psi <- psi / sqrt(<psi|psi>): the FP64 norm as qs_norm computes it, then an in-place
+ * scaling by a factor read on the device (complex128: each component multiplied in FP64;
+ * complex64: by the factor rounded once to float).  Enqueued on the state's stream.  If
+ * norm_out is not NULL the call synchronises the stream and stores the norm before the
+ * scaling there (HOST memory); with NULL it does not synchronise.  A norm that is zero or
+ * not finite leaves the state unchanged. */
+qs_status qs_renormalize(qs_handle h, double* norm_out);
 
 /* ---- allocation-free read-out (no counterpart in the paper) ------------------------- *
  *

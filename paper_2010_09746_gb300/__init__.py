@@ -74,7 +74,8 @@ def marshal(circuit: Iterable):
     return ops, len(gates), np.ascontiguousarray(buf, dtype=np.float64)
 
 
-def _opts(mode="tile", dtype="c128", arith="auto", tile_bits=0, low_bits=0, max_ops=0, scoring=0, reg_bits=0):
+def _opts(mode="tile", dtype="c128", arith="auto", tile_bits=0, low_bits=0, max_ops=0, scoring=0, reg_bits=0,
+          renorm_every=0, full_rx=False):
     o = _lib.qs_compile_opts()
     o.mode = _MODES[mode]
     o.dtype = _DTYPES[dtype]
@@ -83,8 +84,9 @@ def _opts(mode="tile", dtype="c128", arith="auto", tile_bits=0, low_bits=0, max_
     o.low_bits = low_bits
     o.max_ops = max_ops
     o.scoring = scoring
-    o.flags = 0
+    o.flags = _lib.QS_FLAG_FULL_RX if full_rx else 0
     o.reg_bits = reg_bits
+    o.renorm_every = renorm_every
     return o
 
 
@@ -197,6 +199,11 @@ class State:
         _lib.check(_L().qs_set_arith(self._h, _ARITH[arith]))
         self.arith = _ARITH[arith]
 
+    def set_dense_path(self, path: str):
+        """Engine of apply_dense: "auto", "cuda_cores" or "tensor" (qs_set_dense_path)."""
+        code = {"auto": _lib.QS_DENSE_AUTO, "cuda_cores": _lib.QS_DENSE_CUDA_CORES, "tensor": _lib.QS_DENSE_TENSOR}[path]
+        _lib.check(_L().qs_set_dense_path(self._h, code))
+
     def set_profiling(self, on: bool):
         _lib.check(_L().qs_set_profiling(self._h, 1 if on else 0))
 
@@ -277,6 +284,26 @@ class State:
     def norm(self) -> float:
         out = ctypes.c_double()
         _lib.check(_L().qs_norm(self._h, ctypes.byref(out)))
+        return out.value
+
+    def inner(self, other: "State") -> complex:
+        """<self|other> in FP64 (qs_inner); same n and permutation, any dtypes."""
+        out = np.zeros(2, dtype=np.float64)
+        _lib.check(_L().qs_inner(self._h, other._h, _dp(out)))
+        return complex(out[0], out[1])
+
+    def fidelity(self, other: "State") -> float:
+        """|<self|other>|^2 / (<self|self> <other|other>), every reduction in FP64."""
+        return abs(self.inner(other)) ** 2 / (self.norm() * other.norm())
+
+    def renormalize(self, sync: bool = True) -> Optional[float]:
+        """Divide by the square root of the FP64 norm (qs_renormalize); returns the norm
+        before scaling when sync is true, else enqueues without synchronising."""
+        if not sync:
+            _lib.check(_L().qs_renormalize(self._h, None))
+            return None
+        out = ctypes.c_double()
+        _lib.check(_L().qs_renormalize(self._h, ctypes.byref(out)))
         return out.value
 
 

@@ -15,6 +15,8 @@ QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EBUSY, QS_EUNSUPPORTED = 
 QS_ARITH_AUTO, QS_ARITH_DF, QS_ARITH_F64 = 0, 1, 2
 QS_MODE_PERGATE, QS_MODE_PAPER, QS_MODE_TILE = 0, 1, 2
 QS_ORDER_LOGICAL, QS_ORDER_STORAGE = 0, 1
+QS_DENSE_AUTO, QS_DENSE_CUDA_CORES, QS_DENSE_TENSOR = 0, 1, 2
+QS_FLAG_FULL_RX = 1
 OP_CODES = {"U1": 0, "H": 1, "X": 2, "Y": 3, "Z": 4, "S": 5, "T": 6, "RZ": 7, "RX": 8, "RY": 9, "P": 10,
             "CNOT": 11, "CZ": 12, "CP": 13, "CU": 14, "SWAP": 15, "U2": 16, "UK": 17, "RELABEL": 18}
 STATUS_NAMES = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ECUDA", 4: "QS_ETIMEOUT", 5: "QS_EBUSY",
@@ -29,7 +31,8 @@ class qs_op(ctypes.Structure):
 class qs_compile_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("dtype", ctypes.c_int32), ("arith", ctypes.c_int32),
                 ("tile_bits", ctypes.c_int32), ("low_bits", ctypes.c_int32), ("max_ops", ctypes.c_int32),
-                ("scoring", ctypes.c_int32), ("flags", ctypes.c_int32), ("reg_bits", ctypes.c_int32)]
+                ("scoring", ctypes.c_int32), ("flags", ctypes.c_int32), ("reg_bits", ctypes.c_int32),
+                ("renorm_every", ctypes.c_int32)]
 
 
 class qs_plan_stats(ctypes.Structure):
@@ -96,6 +99,9 @@ SIGNATURES = {
     "qs_set_amplitudes": (_I, [_H, _P]),
     "qs_norm": (_I, [_H, _DP]),
     "qs_norm_noalloc": (_I, [_P, _I, _I, _P, _P]),
+    "qs_inner": (_I, [_H, _H, _DP]),
+    "qs_set_dense_path": (_I, [_H, _I]),
+    "qs_renormalize": (_I, [_H, _DP]),
     "qs_batch_create": (_I, [_I, _IP, ctypes.POINTER(qs_op), ctypes.POINTER(ctypes.c_int64), _DP, ctypes.c_size_t,
                              ctypes.POINTER(qs_compile_opts), ctypes.POINTER(_H)]),
     "qs_batch_set_stream": (_I, [_H, _P]),

@@ -58,6 +58,11 @@ struct AF32 {
   static __device__ __forceinline__ reg_t rx(mat_t cs, reg_t a, reg_t b) {
     return make_float2(fmaf(cs.x, a.x, cs.y * b.y), fmaf(cs.x, a.y, -cs.y * b.x));
   }
+  // u + t v with the real t in t.x (tangent-form RX), and -i b
+  static __device__ __forceinline__ reg_t axpy(mat_t t, reg_t v, reg_t u) {
+    return make_float2(fmaf(t.x, v.x, u.x), fmaf(t.x, v.y, u.y));
+  }
+  static __device__ __forceinline__ reg_t mul_mi(reg_t b) { return make_float2(b.y, -b.x); }
   static __device__ __forceinline__ reg_t neg(reg_t a) { return make_float2(-a.x, -a.y); }
   static __device__ __forceinline__ double norm2(reg_t a) {
     return (double)a.x * (double)a.x + (double)a.y * (double)a.y;
@@ -99,6 +104,10 @@ struct AF64 {
   static __device__ __forceinline__ reg_t rx(mat_t cs, reg_t a, reg_t b) {
     return make_double2(fma(cs.x, a.x, cs.y * b.y), fma(cs.x, a.y, -cs.y * b.x));
   }
+  static __device__ __forceinline__ reg_t axpy(mat_t t, reg_t v, reg_t u) {
+    return make_double2(fma(t.x, v.x, u.x), fma(t.x, v.y, u.y));
+  }
+  static __device__ __forceinline__ reg_t mul_mi(reg_t b) { return make_double2(b.y, -b.x); }
   static __device__ __forceinline__ reg_t neg(reg_t a) { return make_double2(-a.x, -a.y); }
   static __device__ __forceinline__ double norm2(reg_t a) { return a.x * a.x + a.y * a.y; }
 };
@@ -270,6 +279,23 @@ struct ADF {
     dfl im = dot2(cs.x, cs.y, a.z, a.w, -cs.z, -cs.w, b.x, b.y);
     return make_float4(re.hi, re.lo, im.hi, im.lo);
   }
+  // u + t v for a real double-float t = (t.x, t.y): TwoProduct of the high parts, the two
+  // first-order cross terms, TwoSum with u's high part (12 instructions per component
+  // against 16 for a two-term dot product).  Used by the tangent-form RX, which applies
+  // (I - i t X) or (t I - i X) and leaves the factor cos or sin to one full-form RX of the
+  // pass.
+  static __device__ __forceinline__ reg_t axpy(mat_t t, reg_t v, reg_t u) {
+    const dfl pr = two_prod(t.x, v.x);
+    float er = __fmaf_rn(t.x, v.y, pr.lo);
+    er = __fmaf_rn(t.y, v.x, er);
+    const dfl sr = two_sum(u.x, pr.hi);
+    const dfl pi = two_prod(t.x, v.z);
+    float ei = __fmaf_rn(t.x, v.w, pi.lo);
+    ei = __fmaf_rn(t.y, v.z, ei);
+    const dfl si = two_sum(u.z, pi.hi);
+    return make_float4(sr.hi, __fadd_rn(sr.lo, __fadd_rn(u.y, er)), si.hi, __fadd_rn(si.lo, __fadd_rn(u.w, ei)));
+  }
+  static __device__ __forceinline__ reg_t mul_mi(reg_t b) { return make_float4(b.z, b.w, -b.x, -b.y); }
   static __device__ __forceinline__ reg_t neg(reg_t a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
   static __device__ __forceinline__ double norm2(reg_t a) {
     double r = (double)a.x + (double)a.y, i = (double)a.z + (double)a.w;

@@ -71,6 +71,8 @@ struct KernelRecord {
   double alu;
 };
 
+constexpr size_t kDenseWBytes = 2 * 128 * 128 * sizeof(float);
+
 struct qs_state {
   int n = 0;
   qs_dtype dtype = QS_C128;
@@ -85,6 +87,9 @@ struct qs_state {
   double* norm_buf = nullptr;     // norm partials + result
   void* gate_pool = nullptr;      // matrix entries of qs_apply_* calls
   size_t gate_pool_bytes = 0;
+  int dense_path = QS_DENSE_AUTO; // qs_apply_dense engine (qs_set_dense_path)
+  float* dense_w = nullptr;       // 2 x 128 x 128 floats: W^T split for the tensor-core kernel
+  int num_sms = 0;
   bool profiling = false;
   std::vector<KernelRecord> pending;
   std::vector<cudaEvent_t> free_events;
@@ -236,6 +241,100 @@ qs_status do_permute(qs_state* h, const std::vector<int>& src_of, const std::vec
   return QS_OK;
 }
 
+// The real 128 x 128 matrix of a dense k-qubit block on storage bits bits[0..k-1] (a
+// permutation of 0..k-1), replicated over storage bits k..5, transposed (row j = output
+// float j of a 64-amplitude row) and split into its nearest TF32 values and the TF32-rounded
+// remainders.
+void dense_mma_weights(const double* U, int k, const int* bits, float* out) {
+  const int kdim = 1 << k;
+  const int mask = kdim - 1;
+  auto mat_index = [&](int x) {
+    int r = 0;
+    for (int t = 0; t < k; t++) r |= ((x >> bits[t]) & 1) << t;
+    return r;
+  };
+  std::vector<double> wt(128 * 128, 0.0);
+  for (int xr = 0; xr < 64; xr++)
+    for (int xc = 0; xc < 64; xc++) {
+      if ((xr & ~mask) != (xc & ~mask)) continue;
+      const int r = mat_index(xr & mask), c = mat_index(xc & mask);
+      const double a = U[2 * (r * kdim + c)], b = U[2 * (r * kdim + c) + 1];
+      wt[(2 * xr) * 128 + 2 * xc] = a;
+      wt[(2 * xr) * 128 + 2 * xc + 1] = -b;
+      wt[(2 * xr + 1) * 128 + 2 * xc] = b;
+      wt[(2 * xr + 1) * 128 + 2 * xc + 1] = a;
+    }
+  auto tf32_rna = [](double v) {   // nearest TF32 value (ties away from zero), as a float
+    const float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+  };
+  for (int i = 0; i < 128 * 128; i++) {
+    const float big = tf32_rna(wt[i]);
+    out[i] = big;
+    out[128 * 128 + i] = tf32_rna(wt[i] - (double)big);
+  }
+}
+
+// Which engine QS_DENSE_AUTO picks for a complex64 block of k qubits (the CUDA-core
+// kernel is arithmetic-bound from k = 5 on; the tensor-core kernel is bandwidth-bound for
+// every k, and worth a permutation pass first only at k = 6).
+bool dense_auto_tensor(int k, bool low) { return low ? k >= 5 : k >= 6; }
+
+qs_status apply_dense_tensor(qs_state* h, const double* U, int k, const int* qubits, bool low) {
+  if (!low) {   // PermuteQubits: qubits[t] -> storage bit t, displaced qubits take the freed bits
+    std::vector<int> ns = h->sigma;
+    for (int t = 0; t < k; t++) {
+      const int q = qubits[t];
+      if (ns[q] == t) continue;
+      for (int q2 = 0; q2 < h->n; q2++)
+        if (ns[q2] == t) {
+          std::swap(ns[q], ns[q2]);
+          break;
+        }
+    }
+    std::vector<int> src_of(h->n);
+    for (int q = 0; q < h->n; q++) src_of[ns[q]] = h->sigma[q];
+    qs_status st = do_permute(h, src_of, ns, 2.0 * (double)h->bytes);
+    if (st != QS_OK) return st;
+  }
+  int bits[6];
+  for (int t = 0; t < k; t++) bits[t] = h->sigma[qubits[t]];
+  std::vector<float> w(2 * 128 * 128);
+  dense_mma_weights(U, k, bits, w.data());
+  if (!h->dense_w) {
+    h->dense_w = (float*)dev_alloc(kDenseWBytes, h->stream);
+    if (!h->dense_w) return fail(QS_ENOMEM, "dense weight buffer allocation failed");
+  }
+  if (!h->num_sms) {
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev), "device query");
+    CUDA_TRY(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  }
+  CUDA_TRY(cudaMemcpyAsync(h->dense_w, w.data(), kDenseWBytes, cudaMemcpyHostToDevice, h->stream), "weight upload");
+  CUDA_TRY(timed(h, "dense_mma_c64", 2.0 * (double)h->bytes,
+                 [&] { return launch_dense_mma(h->psi, h->n, h->dense_w, h->status_dev, h->num_sms, h->stream); }),
+           "dense MMA launch");
+  return QS_OK;
+}
+
+// FP64 norm into norm_buf[np], then scale by it on the device (no host round trip).
+qs_status renormalize(qs_state* h) {
+  const int np = norm_num_partials();
+  CUDA_TRY(timed(h, "norm", (double)h->bytes,
+                 [&] { return launch_norm_partials(h->psi, h->n, h->dtype == QS_C128, h->norm_buf, np, h->stream); }),
+           "norm partials");
+  CUDA_TRY(launch_norm_final(h->norm_buf, np, h->norm_buf + np, h->stream), "norm final");
+  CUDA_TRY(timed(h, "scale", 2.0 * (double)h->bytes,
+                 [&] { return launch_scale(h->psi, h->n, h->dtype == QS_C128, h->norm_buf + np, h->stream); }),
+           "scale launch");
+  return QS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -295,6 +394,7 @@ qs_status qs_destroy(qs_handle h) {
   dev_free(h->status_dev, 256, h->stream);
   dev_free(h->norm_buf, sizeof(double) * (norm_num_partials() + 1), h->stream);
   dev_free(h->gate_pool, h->gate_pool_bytes, h->stream);
+  dev_free(h->dense_w, kDenseWBytes, h->stream);
   cudaStreamSynchronize(h->stream);
   delete h;
   return QS_OK;
@@ -399,9 +499,32 @@ qs_status qs_apply_controlled(qs_handle h, const double* U, int c, int t) {
   return apply_op(h, op, U, 8);
 }
 
+qs_status qs_set_dense_path(qs_handle h, int path) {
+  if (!h) return fail(QS_EINVAL, "null handle");
+  if (path < QS_DENSE_AUTO || path > QS_DENSE_TENSOR) return fail(QS_EINVAL, "unknown dense path");
+  h->dense_path = path;
+  return QS_OK;
+}
+
 qs_status qs_apply_dense(qs_handle h, const double* U, int k, const int* qubits) {
   if (!h || !U || !qubits) return fail(QS_EINVAL, "null argument");
   if (k < 1 || k > kMaxDenseK) return fail(QS_EINVAL, "k must be in [1, 6]");
+  for (int t = 0; t < k; t++) {
+    if (qubits[t] < 0 || qubits[t] >= h->n) return fail(QS_EINVAL, "qubit out of range");
+    for (int u = 0; u < t; u++)
+      if (qubits[u] == qubits[t]) return fail(QS_EINVAL, "repeated qubit");
+  }
+  bool low = true;   // qubits already on storage bits 0..k-1 (any order)
+  for (int t = 0; t < k; t++) low &= h->sigma[qubits[t]] < k;
+  const bool tensor_ok = h->dtype == QS_C64 && h->n >= dense_mma_min_qubits();
+  bool use_tensor = false;
+  if (h->dense_path == QS_DENSE_TENSOR) {
+    if (!tensor_ok) return fail(QS_EINVAL, "tensor-core dense path needs complex64 and n >= 12");
+    use_tensor = true;
+  } else if (h->dense_path == QS_DENSE_AUTO) {
+    use_tensor = tensor_ok && dense_auto_tensor(k, low);
+  }
+  if (use_tensor) return apply_dense_tensor(h, U, k, qubits, low);
   qs_op op{};
   op.kind = QS_OP_UK;
   op.nq = k;
@@ -438,8 +561,9 @@ qs_status qs_compile(int n, const qs_op* ops, size_t nops, const double* mats, s
   if (opts) o = *opts;
   if (o.dtype != QS_C64 && o.dtype != QS_C128) return fail(QS_EINVAL, "unknown dtype");
   if (o.mode < QS_MODE_PERGATE || o.mode > QS_MODE_TILE) return fail(QS_EINVAL, "unknown mode");
-  if (o.flags != 0) return fail(QS_EINVAL, "flags must be 0");
+  if (o.flags & ~QS_FLAG_FULL_RX) return fail(QS_EINVAL, "unknown flags");
   if (o.reg_bits < 0 || o.reg_bits > 5) return fail(QS_EINVAL, "reg_bits must be in [0, 5]");
+  if (o.renorm_every < 0) return fail(QS_EINVAL, "renorm_every must be >= 0");
   if (o.tile_bits == 0) o.tile_bits = default_tile_bits(o.dtype);
   if (o.low_bits == 0) o.low_bits = default_low_bits(o.dtype);
   if (o.tile_bits < 1 || (o.mode != QS_MODE_PAPER && o.tile_bits > kMaxTileBits))
@@ -558,6 +682,9 @@ qs_status qs_execute(qs_handle h, qs_plan_t p) {
       CUDA_TRY(timed(h, name, s.bytes, [&] { return launch_gate(p->pol, h->psi, h->n, s.op, p->pool_dev, h->stream); },
                      s.alu),
                "gate launch");
+    } else if (s.kind == ST_RENORM) {
+      qs_status st = renormalize(h);
+      if (st != QS_OK) return st;
     } else {
       qs_status st = do_permute(h, s.src_of, s.perm, s.bytes);
       if (st != QS_OK) return st;
@@ -635,6 +762,46 @@ qs_status qs_norm(qs_handle h, double* out) {
   CUDA_TRY(cudaMemcpyAsync(out, h->norm_buf + np, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "norm read");
   CUDA_TRY(cudaStreamSynchronize(h->stream), "norm sync");
   return check_status(h);
+}
+
+qs_status qs_renormalize(qs_handle h, double* norm_out) {
+  if (!h) return fail(QS_EINVAL, "null handle");
+  qs_status st = renormalize(h);
+  if (st != QS_OK) return st;
+  if (!norm_out) return QS_OK;
+  CUDA_TRY(cudaMemcpyAsync(norm_out, h->norm_buf + norm_num_partials(), sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream),
+           "norm read");
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "renormalize sync");
+  return check_status(h);
+}
+
+qs_status qs_inner(qs_handle a, qs_handle b, double* out) {
+  if (!a || !b || !out) return fail(QS_EINVAL, "null argument");
+  if (a->n != b->n) return fail(QS_EINVAL, "states have different n");
+  if (a->sigma != b->sigma) return fail(QS_EINVAL, "states have different permutations (qs_permute one of them first)");
+  if (a != b && a->stream != b->stream) {   // a's stream waits for b's work up to now
+    cudaEvent_t ev;
+    CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event create");
+    cudaError_t e = cudaEventRecord(ev, b->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(a->stream, ev, 0);
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return cuda_fail(e, "stream ordering");
+  }
+  const int np = inner_num_partials();
+  const size_t nb = sizeof(double) * 2 * (np + 1);
+  double* d = (double*)dev_alloc(nb, a->stream);
+  if (!d) return fail(QS_ENOMEM, "inner-product buffer allocation failed");
+  cudaError_t e = cudaSuccess;
+  timed(a, "inner", (double)(a->bytes + b->bytes), [&] {
+    e = launch_inner(a->psi, a->dtype == QS_C128, b->psi, b->dtype == QS_C128, a->n, d, d + 2 * np, a->stream);
+    return e;
+  });
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d + 2 * np, 2 * sizeof(double), cudaMemcpyDeviceToHost, a->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(a->stream);
+  dev_free(d, nb, a->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "inner product");
+  return check_status(a);
 }
 
 }  // extern "C"

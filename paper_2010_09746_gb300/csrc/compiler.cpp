@@ -428,6 +428,7 @@ bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<i
   const int store_bytes = (o.dtype == QS_C128) ? 16 : 8;
   out->store_bytes = store_bytes;
   out->reg_bits = o.reg_bits;
+  out->full_rx = (o.flags & QS_FLAG_FULL_RX) != 0;
   out->pol = (o.dtype == QS_C64) ? POL_F32 : (o.arith == QS_ARITH_F64 ? POL_F64 : POL_DF);
   out->stats = qs_plan_stats{};
   out->stats.n_gates = (int64_t)gates.size();
@@ -458,6 +459,21 @@ bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<i
     return false;
   }
   if (!ok) return false;
+  if (o.renorm_every > 0) {   // FP64 norm (read) + scaling (read + write) after every R kernels
+    std::vector<Step> with;
+    int since = 0;
+    for (Step& s : out->steps) {
+      with.push_back(std::move(s));
+      if (++since == o.renorm_every) {
+        Step r;
+        r.kind = ST_RENORM;
+        r.bytes = 3.0 * (double)store_bytes * (double)(1ull << n);
+        with.push_back(std::move(r));
+        since = 0;
+      }
+    }
+    out->steps = std::move(with);
+  }
   double bytes = 0, alu = 0;
   for (const Step& s : out->steps) {
     bytes += s.bytes;

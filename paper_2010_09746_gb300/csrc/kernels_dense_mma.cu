@@ -1,0 +1,350 @@
+// K4: a dense k-qubit block (k <= 6) on the lowest storage bits of a complex64 state, on
+// the 5th-generation tensor cores (tcgen05, accumulators in tensor memory).
+//
+// The block acts on storage bits 0..k-1.  Seen as rows of 64 complex64 amplitudes (storage
+// bits 0..5 inside a row), the state is a row-major matrix Psi with 2^(n-6) rows of 128
+// floats (re, im interleaved), and the gate is Psi' = Psi W with one 128 x 128 real matrix W
+// (the complex 2^k x 2^k block, replicated on the diagonal over storage bits k..5 when k < 6,
+// written as a real matrix that maps interleaved (re, im) inputs to interleaved outputs).
+//
+// Each MMA computes D[j][r] = sum_c W^T[j][c] Psi[r][c] for the 128 output columns j and a
+// tile of 64 rows r: A = W^T lives in tensor memory for the whole launch, B = the state tile
+// is read from shared memory (K-major, no swizzle), D (128 lanes x 64 columns FP32) is read
+// back by the four warps, one output column per thread.  Near-FP32 accuracy from TF32
+// operands with the three-term split x = x_big + x_small (x_big = x rounded to TF32,
+// x_small = x - x_big rounded to TF32, so each factor is kept to about 2^-22 relative):
+// W^T_big x_big + W^T_small x_big + W^T_big x_small, accumulated in FP32.  The tensor core
+// rounds each accumulation toward zero, which biases magnitudes downward by about half an
+// ulp per MMA; the big x big products therefore go to two accumulators of 8 MMAs each and
+// the cross terms (2^-11 smaller) to a third, summed with round-to-nearest in the epilogue.
+//
+// Persistent grid, one CTA per SM (the 205 KiB of shared memory admit one), 128 threads:
+// row tiles of 32 KiB move between HBM and a ring of 4 row-major staging buffers with bulk
+// copies (mbarrier completion, loads issued 3 tiles ahead); the threads split each tile into
+// the two operand buffers; thread 0 issues the 48 MMAs and commits them to an mbarrier; the
+// epilogue writes D row-major into the tile's staging buffer, which a bulk store sends back.
+// Every wait is bounded by a 2 s %globaltimer deadline; on expiry the CTA records
+// QS_ETIMEOUT, waits (bounded) for its copies and MMAs in flight, frees its tensor memory
+// and returns.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qs_internal.h"
+
+namespace qs {
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kRowFloats = 128;                      // 64 complex64 amplitudes
+constexpr int kRows = 64;                            // rows per tile = MMA N
+constexpr int kTileFloats = kRows * kRowFloats;      // 8192
+constexpr uint32_t kTileBytes = kTileFloats * 4;     // 32 KiB
+constexpr int kStages = 4;
+constexpr int kOffBig = kStages * (int)kTileBytes;
+constexpr int kOffSmall = kOffBig + (int)kTileBytes;
+constexpr int kGuardBytes = 8192;                    // reads of a mis-strided descriptor stay inside the allocation
+constexpr int kOffBar = kOffSmall + (int)kTileBytes + kGuardBytes;
+constexpr int kSmemUsed = kOffBar + 128;
+constexpr int kSmemAlloc = kSmemUsed + 1024;         // slack for aligning the base to 1 KiB
+// tensor memory columns: [0,128) W^T big, [128,256) W^T small, then three 64-column FP32
+// accumulators: the big x big products of K columns 0..63 and of 64..127, and the two
+// small cross-term products
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kColWBig = 0, kColWSmall = 128, kColD0 = 256, kColD1 = 320, kColDs = 384;
+constexpr uint32_t kLBO = kRows * 16;                // K-direction stride between 8x16 B core matrices
+constexpr uint32_t kSBO = 128;                       // N-direction stride between 8-row groups
+// instruction descriptor, kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (bits 7-9 and
+// 10-12 = 2), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kRows >> 3) << 17) |
+                            ((uint32_t)(128 >> 4) << 24);
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long deadline) {
+  uint32_t spins = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++spins & 255u) == 0 && globaltimer() > deadline) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst_smem, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst_smem),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_store(void* dst, uint32_t src_smem, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src_smem), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// ---- tensor memory and MMA ---------------------------------------------------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t slot_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot_smem), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
+               ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+               : "r"(taddr)
+               : "memory");
+}
+
+// D[d] (+)= A[a] (tensor memory) * B (shared-memory descriptor)
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+      "r"(a), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+// shared-memory matrix descriptor: start address, leading (K) and stride (N) byte offsets
+// in 16-byte units, the fixed 0b001 at bits 46-48, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(kLBO >> 4) << 16) | ((uint64_t)(kSBO >> 4) << 32) |
+         (1ull << 46);
+}
+
+// round to the nearest TF32 value (10 significand bits), ties away from zero; the result
+// has its low 13 bits clear, so the tensor core reads it exactly
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ void tf32_split(float x, float& big, float& small) {
+  big = tf32_rna(x);
+  small = tf32_rna(x - big);   // x - big is exact; |x - big| <= 2^-11 |x|
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_dense_mma(float* __restrict__ psi, uint64_t ntiles, const float* __restrict__ wT, int* __restrict__ status) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float* stg = (float*)smem;
+  unsigned char* big = smem + kOffBig;
+  unsigned char* small = smem + kOffSmall;
+  const uint32_t bar0 = smem_u32(smem + kOffBar);             // full[s] at bar0 + 8 s
+  const uint32_t mma_bar = bar0 + 8 * kStages;
+  uint32_t* tmem_slot = (uint32_t*)(smem + kOffBar + 64);
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; s++) mbar_init(bar0 + 8 * s, 1);
+    mbar_init(mma_bar, 1);
+    fence_async_smem();
+  }
+  if (warp == 0) tmem_alloc(smem_u32(tmem_slot), kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+
+  // W^T (big, small) into tensor memory: thread j holds row j of both, 128 columns each
+  for (int part = 0; part < 2; part++)
+    for (int c0 = 0; c0 < 128; c0 += 32) {
+      uint32_t v[32];
+      const float4* src = (const float4*)(wT + part * 16384 + tid * 128 + c0);
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        const float4 f = __ldg(src + q);
+        v[4 * q] = __float_as_uint(f.x);
+        v[4 * q + 1] = __float_as_uint(f.y);
+        v[4 * q + 2] = __float_as_uint(f.z);
+        v[4 * q + 3] = __float_as_uint(f.w);
+      }
+      tmem_st32(tmem + lane_base + (part ? kColWSmall : kColWBig) + c0, v);
+    }
+  tmem_wait_st();
+
+  // loads issued by thread 0: the tiles of iterations < issued
+  uint64_t issued = 0;
+  if (tid == 0) {
+    for (int s = 0; s < kStages - 1; s++) {
+      const uint64_t t = blockIdx.x + (uint64_t)s * gridDim.x;
+      if (t >= ntiles) break;
+      mbar_arrive_expect_tx(bar0 + 8 * s, kTileBytes);
+      bulk_load(smem_u32(stg + s * kTileFloats), psi + t * kTileFloats, kTileBytes, bar0 + 8 * s);
+      issued = s + 1;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+
+  int fail = 0;
+  bool mma_pending = false;
+  uint32_t mma_phase = 0;
+  uint64_t i = 0;
+  for (;; i++) {
+    const uint64_t t = blockIdx.x + i * gridDim.x;
+    if (t >= ntiles) break;
+    const int s = (int)(i % kStages);
+    if (tid == 0) {   // refill the stage of iteration i - 1 with the tile of iteration i + kStages - 1
+      const uint64_t inext = i + kStages - 1;
+      const uint64_t tn = blockIdx.x + inext * gridDim.x;
+      if (tn < ntiles) {
+        const int sn = (int)(inext % kStages);
+        bulk_wait_read0();   // the store from that stage has read its shared memory
+        mbar_arrive_expect_tx(bar0 + 8 * sn, kTileBytes);
+        bulk_load(smem_u32(stg + sn * kTileFloats), psi + tn * kTileFloats, kTileBytes, bar0 + 8 * sn);
+        issued = inext + 1;
+      }
+    }
+    const bool ok_load = mbar_wait(bar0 + 8 * s, (uint32_t)((i / kStages) & 1), globaltimer() + kWaitNs);
+    if (__syncthreads_or(!ok_load)) {
+      fail = 1;
+      break;
+    }
+
+    // split the row-major tile into the K-major operand layout: element group (row r,
+    // 4-float panel p) goes to p * kLBO + r * 16.  The 8 threads of each shared-memory
+    // phase take distinct r mod 8 and distinct p mod 8, so reads and writes are
+    // conflict-free.
+    {
+      const float4* src = (const float4*)(stg + s * kTileFloats);
+#pragma unroll 4
+      for (int it = 0; it < kTileFloats / 4 / kThreads; it++) {
+        const int g = it * kThreads + tid;
+        const int i8 = g & 7, rest = g >> 3;
+        const int r = ((rest & 7) << 3) | i8;
+        const int p = ((rest >> 3) + i8) & 31;
+        const float4 x = src[r * 32 + p];
+        float4 hb, lo;
+        tf32_split(x.x, hb.x, lo.x);
+        tf32_split(x.y, hb.y, lo.y);
+        tf32_split(x.z, hb.z, lo.z);
+        tf32_split(x.w, hb.w, lo.w);
+        const uint32_t off = (uint32_t)p * kLBO + (uint32_t)r * 16u;
+        *(float4*)(big + off) = hb;
+        *(float4*)(small + off) = lo;
+      }
+    }
+    fence_async_smem();
+    __syncthreads();
+
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t bb = smem_u32(big), sb = smem_u32(small);
+#pragma unroll
+      for (int kk = 0; kk < 16; kk++) {
+        const uint64_t db = smem_desc(bb + kk * 2 * kLBO), ds = smem_desc(sb + kk * 2 * kLBO);
+        mma_tf32(tmem + (kk < 8 ? kColD0 : kColD1), tmem + kColWBig + kk * 8, db, (kk & 7) ? 1u : 0u);
+        mma_tf32(tmem + kColDs, tmem + kColWSmall + kk * 8, db, kk > 0 ? 1u : 0u);
+        mma_tf32(tmem + kColDs, tmem + kColWBig + kk * 8, ds, 1u);
+      }
+      mma_commit(mma_bar);
+    }
+    mma_pending = true;
+    const bool ok_mma = mbar_wait(mma_bar, mma_phase, globaltimer() + kWaitNs);
+    if (__syncthreads_or(!ok_mma)) {
+      fail = 1;
+      break;
+    }
+    mma_pending = false;
+    mma_phase ^= 1u;
+    tc_fence_after();
+
+    // epilogue: thread j = output column j of rows 0..63, written row-major into the stage
+    float* out = stg + s * kTileFloats;
+#pragma unroll 1
+    for (int c0 = 0; c0 < kRows; c0 += 32) {
+      uint32_t v0[32], v1[32], vs[32];
+      tmem_ld32(tmem + lane_base + kColD0 + c0, v0);
+      tmem_ld32(tmem + lane_base + kColD1 + c0, v1);
+      tmem_ld32(tmem + lane_base + kColDs + c0, vs);
+      tmem_wait_ld();
+#pragma unroll
+      for (int c = 0; c < 32; c++)
+        out[(c0 + c) * kRowFloats + tid] =
+            __fadd_rn(__fadd_rn(__uint_as_float(v0[c]), __uint_as_float(v1[c])), __uint_as_float(vs[c]));
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      bulk_store(psi + t * kTileFloats, smem_u32(out), kTileBytes);
+      bulk_commit();
+    }
+  }
+
+  if (tid == 0) {
+    if (fail) {
+      atomicExch(status, (int)QS_ETIMEOUT);
+      // loads issued for iterations >= i are still owed to their barriers
+      const unsigned long long dl = globaltimer() + kWaitNs;
+      for (uint64_t j = i + (mma_pending ? 1 : 0); j < issued; j++)
+        mbar_wait(bar0 + 8 * (int)(j % kStages), (uint32_t)((j / kStages) & 1), dl);
+      if (mma_pending) mbar_wait(mma_bar, mma_phase, dl);
+    }
+    bulk_wait0();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+}  // namespace
+
+int dense_mma_min_qubits() { return 12; }
+
+cudaError_t launch_dense_mma(void* psi, int n, const float* wT_dev, int* status, int num_sms, cudaStream_t s) {
+  if (n < 12) return cudaErrorInvalidValue;
+  static bool attr_set = false;   // per process; the attribute is per function, not per device
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_dense_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAlloc);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const uint64_t ntiles = 1ull << (n - 12);   // 2^(n-6) rows of 64 amplitudes, 64 rows per tile
+  const uint64_t g = ntiles < (uint64_t)num_sms ? ntiles : (uint64_t)num_sms;
+  k_dense_mma<<<(unsigned)g, kThreads, kSmemAlloc, s>>>((float*)psi, ntiles, wT_dev, status);
+  return cudaGetLastError();
+}
+
+}  // namespace qs

@@ -303,6 +303,29 @@ __device__ __forceinline__ void r_rx(typename A::reg_t (&x)[1 << K], const typen
     x[j | (1 << S)] = A::rx(cs, b, a);
   }
 }
+// tangent-form RX on slot S: mode 0 applies I - i t X, mode 1 applies t I - i X (the
+// compiler moves the dropped factor cos or sin into one full-form RX of the same pass)
+template <class A, int K, int S>
+__device__ __forceinline__ void r_rxt(typename A::reg_t (&x)[1 << K], const typename A::mat_t* m, uint32_t mode) {
+  const typename A::mat_t t = m[0];
+  if (mode == 0) {
+#pragma unroll
+    for (int j = 0; j < (1 << K); j++) {
+      if (j & (1 << S)) continue;
+      const typename A::reg_t a = x[j], b = x[j | (1 << S)];
+      x[j] = A::axpy(t, A::mul_mi(b), a);
+      x[j | (1 << S)] = A::axpy(t, A::mul_mi(a), b);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < (1 << K); j++) {
+      if (j & (1 << S)) continue;
+      const typename A::reg_t a = x[j], b = x[j | (1 << S)];
+      x[j] = A::axpy(t, a, A::mul_mi(b));
+      x[j | (1 << S)] = A::axpy(t, b, A::mul_mi(a));
+    }
+  }
+}
 template <class A, int K, int S>
 __device__ __forceinline__ void r_x(typename A::reg_t (&x)[1 << K], const typename A::mat_t*, uint32_t csl) {
 #pragma unroll
@@ -371,6 +394,7 @@ __device__ __forceinline__ void apply_regop(typename A::reg_t (&x)[1 << K], cons
   switch (op.type) {
     case OP_U1: QS_SLOT_DISPATCH(r_u1, op.s0, x, m, csl); break;
     case OP_RX: QS_SLOT_DISPATCH(r_rx, op.s0, x, m, csl); break;
+    case OP_RXT: QS_SLOT_DISPATCH(r_rxt, op.s0, x, m, (uint32_t)op.s1); break;
     case OP_X: QS_SLOT_DISPATCH(r_x, op.s0, x, m, csl); break;
     case OP_U2: {
       if constexpr (K >= 2) {

@@ -35,6 +35,9 @@ enum OpType : int32_t {
   OP_DENSE = 7,  // general 2^nk x 2^nk on bits kq[0..nk-1]
   OP_SWAP = 8,   // exchange bits k0 and k1 (controls cmask)
   OP_DTAB = 9,   // register stages only: multiply register element j by table entry j
+  OP_RXT = 10,   // register stages only: tangent-form RX, (I - i t X) if s1 == 0 else
+                 // (t I - i X); one pool entry (t, 0).  The factor it drops is applied by
+                 // a full-form OP_RX of the same pass
 };
 
 struct DevOp {
@@ -53,8 +56,8 @@ static_assert(sizeof(DevOp) == 64, "DevOp layout");
 // stage's register bits; controls are split into register slots (csl) and tile bits
 // outside the registers (cot); gmask is the block predicate (storage bits outside the tile).
 struct alignas(16) RegOp {
-  int32_t type;       // OP_U1, OP_RX, OP_X, OP_DIAG, OP_PHASE, OP_U2, OP_DTAB
-  int8_t s0, s1;      // register slots of the target bit(s), -1 if none
+  int32_t type;       // OP_U1, OP_RX, OP_RXT, OP_X, OP_DIAG, OP_PHASE, OP_U2, OP_DTAB
+  int8_t s0, s1;      // register slots of the target bit(s), -1 if none (OP_RXT: s1 = form)
   int8_t tb;          // OP_DIAG on a tile bit outside the registers, -1 if none
   int8_t neg;         // OP_PHASE: exact sign flip
   uint32_t csl;       // control mask over register slots
@@ -94,7 +97,7 @@ struct BatchPass {
 };
 
 // One plan step.
-enum StepKind : int32_t { ST_PASS = 0, ST_GATE = 1, ST_PERMUTE = 2 };
+enum StepKind : int32_t { ST_PASS = 0, ST_GATE = 1, ST_PERMUTE = 2, ST_RENORM = 3 };
 struct Step {
   StepKind kind;
   TilePass pass{};           // ST_PASS
@@ -130,6 +133,17 @@ cudaError_t launch_gather_amplitudes(const void* psi, int n, int store_bytes, vo
 int tile_pass_smem_bytes(Policy pol, int L);
 int tile_pass_ctas_per_sm(Policy pol, int L);
 int norm_num_partials();
+// <a|b> in FP64 into out2[0..1] (device); partials2 holds inner_num_partials() double pairs.
+cudaError_t launch_inner(const void* a, int a_c128, const void* b, int b_c128, int n, double* partials2,
+                         double* out2, cudaStream_t s);
+int inner_num_partials();
+// Dense block on storage bits 0..5 of a complex64 state on the tensor cores: every row of
+// 64 amplitudes times the 128 x 128 real matrix whose transpose's TF32 split (big, small;
+// 2 x 128 x 128 floats) is at wT_dev.  n >= dense_mma_min_qubits().
+cudaError_t launch_dense_mma(void* psi, int n, const float* wT_dev, int* status, int num_sms, cudaStream_t s);
+int dense_mma_min_qubits();
+// psi *= 1 / sqrt(*norm_dev), skipped on the device if *norm_dev is not positive and finite.
+cudaError_t launch_scale(void* psi, int n, int is_c128, const double* norm_dev, cudaStream_t s);
 
 // ------------------------------------------------------------------------------------------
 // Host gate model shared by the runtime and the compiler.
@@ -179,6 +193,7 @@ struct CompileResult {
   int store_bytes = 16;
   Policy pol = POL_DF;
   int reg_bits = 0;              // requested register bits (0 = default)
+  bool full_rx = false;          // QS_FLAG_FULL_RX: no tangent-form RX in register stages
   std::vector<Step> steps;
   std::vector<std::pair<int, int>> trace;   // QS_MODE_PAPER: (0 local gate | 1 non-local gate | 2 permute, value)
   std::vector<DevOp> tile_ops;   // shared-memory ops of all passes, concatenated

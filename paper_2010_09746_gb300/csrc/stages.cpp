@@ -13,6 +13,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <cmath>
+
 #include "qs_internal.h"
 
 namespace qs {
@@ -185,6 +187,11 @@ int register_bits(int dtype, int L, int requested) {
 
 void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* out, int* st0, int* nst) {
   const int N = (int)ops.size();
+  // tangent-form RX: every uncontrolled register-stage RX after the pass's first one is
+  // applied as (I - i t X) or (t I - i X) (|t| <= 1); the product of the dropped factors
+  // (cos or sin, a real scalar that commutes with every op) goes into the first one
+  int first_rx = -1;
+  double rx_scale = 1.0;
   std::vector<OpInfo> info(N);
   for (int i = 0; i < N; i++) info[i] = classify_op(ops[i]);
   // dependency DAG over tile bits (same grouping rule as the circuit DAG)
@@ -393,6 +400,27 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
         rl.push_back(r);
       }
       merge_diagonals(rl, K, out->pool);
+      if (!out->full_rx)
+        for (RegOp& r : rl) {
+          if (r.type != OP_RX || r.csl != 0 || r.cot != 0 || r.gmask != 0) continue;
+          if (first_rx < 0) {
+            first_rx = r.mat;
+            continue;
+          }
+          double* e = &out->pool.f64[2 * (size_t)r.mat];
+          const double c = e[0], sn = e[1];
+          r.type = OP_RXT;
+          if (std::fabs(c) >= std::fabs(sn)) {
+            r.s1 = 0;
+            e[0] = sn / c;
+            rx_scale *= c;
+          } else {
+            r.s1 = 1;
+            e[0] = c / sn;
+            rx_scale *= sn;
+          }
+          e[1] = 0.0;
+        }
       st.op0 = (int)out->reg_ops.size();
       out->reg_ops.insert(out->reg_ops.end(), rl.begin(), rl.end());
       st.nops = (int)rl.size();
@@ -406,6 +434,10 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
     for (size_t r = 0; r < rem.size(); r++)
       if (!done[rem[r]]) rem[w++] = rem[r];
     rem.resize(w);
+  }
+  if (first_rx >= 0) {
+    out->pool.f64[2 * (size_t)first_rx] *= rx_scale;
+    out->pool.f64[2 * (size_t)first_rx + 1] *= rx_scale;
   }
   *nst = (int)out->stages.size() - *st0;
 }
@@ -423,6 +455,7 @@ struct Cost {
 double pick(const Cost& c, Policy p) { return p == POL_F32 ? c.f32 : (p == POL_F64 ? c.f64 : c.df); }
 
 const Cost kRX{4, 4, 32};       // two real products and a sum per component
+const Cost kRXT{2, 2, 24};      // one real product and a sum per component (tangent form)
 const Cost kMUL{4, 4, 32};      // complex multiply (diagonal factor, table entry)
 const Cost kU1{8, 8, 80};       // two complex products and a sum
 const Cost kNEG{0, 0, 0};       // sign flips
@@ -460,6 +493,7 @@ double stage_alu_per_amp(const CompileResult& cr, int st0, int nst) {
       const int ctl = __builtin_popcount(r.csl) + __builtin_popcount(r.cot) + __builtin_popcountll(r.gmask);
       switch (r.type) {
         case OP_RX: a += pick(kRX, cr.pol) * fraction(ctl); break;
+        case OP_RXT: a += pick(kRXT, cr.pol) * fraction(ctl); break;
         case OP_U1: a += pick(kU1, cr.pol) * fraction(ctl); break;
         case OP_DIAG: case OP_DTAB: a += pick(kMUL, cr.pol) * fraction(ctl); break;
         case OP_PHASE: a += (r.neg ? pick(kNEG, cr.pol) : pick(kMUL, cr.pol)) * fraction(ctl); break;

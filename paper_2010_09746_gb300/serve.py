@@ -4,10 +4,14 @@ Requests (a circuit, its qubit count and dtype) arrive over time.  The server ad
 waiting request as soon as a slot and enough device memory are free -- it does not wait
 for the requests already on the GPU -- compiles its plan on the host, and enqueues
 state preparation and the plan on the slot's own CUDA stream, so
-work of different requests overlaps on the device.  Completion is detected with CUDA
-events; the result (the FP64 norm and the first amplitudes) is read out, the state is
-released and the next request takes the slot.  Every request runs the same kernels on its
-own state whatever else is in flight, so its result does not depend on the mix.
+work of different requests overlaps on the device.  Small requests (n <= batch_small_n)
+waiting together with others of the same dtype share one slot: they are compiled into one
+batch (qs_batch_*), whose tile passes run as persistent launches over all of their states.
+Completion is detected with CUDA events; the result (the FP64 norm and the first
+amplitudes) is read out, the state is released and the next request takes the slot.  Every
+request runs the same per-tile code on its own state whatever else is in flight (a batched
+circuit's amplitudes are bitwise those of its solo run), so its result does not depend on
+the mix.
 """
 from __future__ import annotations
 
@@ -18,7 +22,7 @@ from typing import Dict, List, Optional
 
 import numpy as np
 
-from . import Plan, State
+from . import Batch, Plan, State
 
 
 @dataclass
@@ -45,13 +49,12 @@ class _Slot:
 
 @dataclass
 class _Flight:
-    rid: int
-    req: object
+    members: List[tuple]          # (rid, req, arrival_s) of every request in this flight
     slot: int
-    state: State
-    plan: Plan
+    state: Optional[State]        # one request
+    plan: Optional[Plan]
+    batch: Optional[Batch]        # several small requests
     event: object
-    arrival_s: float
     admit_s: float
     bytes: int
 
@@ -60,7 +63,8 @@ class Server:
     """slots: requests in flight at once; mem_budget: device bytes for resident states;
     readout: amplitudes copied back per request (first min(2^n, readout))."""
 
-    def __init__(self, slots: int = 8, mem_budget: int = 64 << 30, readout: int = 256, tile_bits: int = 0):
+    def __init__(self, slots: int = 8, mem_budget: int = 64 << 30, readout: int = 256, tile_bits: int = 0,
+                 batch_small_n: int = 16, batch_max: int = 64):
         import torch
 
         self.torch = torch
@@ -69,6 +73,10 @@ class Server:
         self.mem_used = 0
         self.readout = readout
         self.tile_bits = tile_bits
+        self.batch_small_n = batch_small_n
+        self.batch_max = batch_max
+        self.batched_requests = 0
+        self.batches = 0
         self.waiting: deque = deque()
         self.flights: List[_Flight] = []
         self.results: Dict[int, Result] = {}
@@ -92,19 +100,44 @@ class Server:
             free = [i for i, s in enumerate(self.slots) if not s.busy]
             if not free or self.mem_used + need > self.mem_budget:
                 break
-            self.waiting.popleft()
             si = free[0]
             slot = self.slots[si]
+            group = []
+            if req.n <= self.batch_small_n and self.batch_max > 1:
+                # the small requests of this dtype now waiting, in arrival order, that fit
+                mem = 0
+                for item in self.waiting:
+                    r2 = item[1]
+                    b2 = self.state_bytes(r2.n, r2.dtype)
+                    if (r2.n <= self.batch_small_n and r2.dtype == req.dtype and len(group) < self.batch_max
+                            and self.mem_used + mem + b2 <= self.mem_budget):
+                        group.append(item)
+                        mem += b2
+            if len(group) > 1:
+                ids = {id(item) for item in group}
+                self.waiting = deque(item for item in self.waiting if id(item) not in ids)
+                b = Batch([(r.n, r.circuit) for _, r, _ in group], dtype=req.dtype, stream=slot.stream, graph=False,
+                          tile_bits=self.tile_bits)
+                b.run()
+                ev = self.torch.cuda.Event()
+                ev.record(slot.stream)
+                self.flights.append(_Flight(group, si, None, None, b, ev, now_s, mem))
+                self.mem_used += mem
+                self.batched_requests += len(group)
+                self.batches += 1
+                admitted += len(group)
+            else:
+                self.waiting.popleft()
+                plan = Plan(req.n, req.circuit, mode="tile", dtype=req.dtype, tile_bits=self.tile_bits)
+                st = State(req.n, req.dtype, stream=slot.stream)
+                st.execute(plan)
+                ev = self.torch.cuda.Event()
+                ev.record(slot.stream)
+                self.flights.append(_Flight([(rid, req, arr)], si, st, plan, None, ev, now_s, need))
+                self.mem_used += need
+                admitted += 1
             slot.busy = True
-            self.mem_used += need
-            plan = Plan(req.n, req.circuit, mode="tile", dtype=req.dtype, tile_bits=self.tile_bits)
-            st = State(req.n, req.dtype, stream=slot.stream)
-            st.execute(plan)
-            ev = self.torch.cuda.Event()
-            ev.record(slot.stream)
-            self.flights.append(_Flight(rid, req, si, st, plan, ev, arr, now_s, need))
-            admitted += 1
-        self.peak_in_flight = max(self.peak_in_flight, len(self.flights))
+        self.peak_in_flight = max(self.peak_in_flight, sum(len(f.members) for f in self.flights))
         self.peak_mem = max(self.peak_mem, self.mem_used)
         return admitted
 
@@ -115,15 +148,23 @@ class Server:
             if not f.event.query():
                 keep.append(f)
                 continue
-            count = min(1 << f.req.n, self.readout)
-            amps = f.state.amplitudes(0, count)
-            norm = f.state.norm()
-            t = clock()
-            self.results[f.rid] = Result(f.rid, f.req.n, f.req.dtype, norm, amps, f.arrival_s, f.admit_s, t)
-            f.state.close()
+            if f.batch is not None:
+                norms = f.batch.norms()
+                t = clock()
+                for i, (rid, req, arr) in enumerate(f.members):
+                    amps = f.batch.amplitudes(i, 0, min(1 << req.n, self.readout))
+                    self.results[rid] = Result(rid, req.n, req.dtype, float(norms[i]), amps, arr, f.admit_s, t)
+                del f.batch
+            else:
+                rid, req, arr = f.members[0]
+                amps = f.state.amplitudes(0, min(1 << req.n, self.readout))
+                norm = f.state.norm()
+                t = clock()
+                self.results[rid] = Result(rid, req.n, req.dtype, norm, amps, arr, f.admit_s, t)
+                f.state.close()
             self.slots[f.slot].busy = False
             self.mem_used -= f.bytes
-            done += 1
+            done += len(f.members)
         self.flights = keep
         return done
 

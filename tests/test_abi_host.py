@@ -34,7 +34,7 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_layout():
     assert ctypes.sizeof(_lib.qs_op) == 48
-    assert ctypes.sizeof(_lib.qs_compile_opts) == 36
+    assert ctypes.sizeof(_lib.qs_compile_opts) == 40
 
 
 def test_version():
@@ -194,3 +194,37 @@ def test_relabel_only_in_pergate_mode():
     assert _compile_status(3, c, mode="tile") == _lib.QS_EINVAL
     p = qs.compile(3, c, mode="pergate")
     assert p.final_permutation() == [1, 0, 2]
+
+
+def test_renorm_every_schedule():
+    """Periodic renormalisation adds one norm + scaling (3 state sweeps) after every R kernels."""
+    n = 12
+    circ = wc.rzrx_cz_circuit(n, 6, seed=3)
+    base = qs.compile(n, circ, mode="pergate", dtype="c64").stats()
+    S = (1 << n) * 8
+    for R in (1, 5, 7):
+        s = qs.compile(n, circ, mode="pergate", dtype="c64", renorm_every=R).stats()
+        k = base["n_pergate"] // R
+        assert s["hbm_bytes"] == pytest.approx(base["hbm_bytes"] + 3 * S * k)
+        assert s["n_pergate"] == base["n_pergate"]
+    with pytest.raises(qs.QSError):
+        qs.compile(n, circ, mode="tile", dtype="c64", renorm_every=-1)
+
+
+def test_tangent_rx_lowers_the_count():
+    """Uncontrolled register-stage RX after a pass's first one use the tangent form (24
+    double-float / 2 FP32 instructions per amplitude instead of 32 / 4); QS_FLAG_FULL_RX
+    keeps the full form; unknown flags are rejected."""
+    n = 20
+    circ = wc.rzrx_cz_circuit(n, 10, seed=2)
+    for dt in ("c128", "c64"):
+        a = qs.compile(n, circ, mode="tile", dtype=dt).stats()
+        b = qs.compile(n, circ, mode="tile", dtype=dt, full_rx=True).stats()
+        assert a["alu_instr"] < b["alu_instr"]
+        assert a["hbm_bytes"] == b["hbm_bytes"] and a["n_passes"] == b["n_passes"]
+    o = qs._opts()
+    o.flags = 2
+    h = ctypes.c_void_p()
+    ops, nops, mats = qs.marshal(circ[:3])
+    assert _lib.load().qs_compile(n, ops, nops, mats.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), mats.size,
+                                  None, ctypes.byref(o), ctypes.byref(h)) == _lib.QS_EINVAL

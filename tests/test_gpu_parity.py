@@ -218,3 +218,25 @@ def test_appendix_b_export_runs_as_permutations(dtype):
     st.run(ir, mode="pergate")
     assert st.permutation() == plan.final_permutation()
     check(st.amplitudes(), sv.simulate(n, circ), dtype)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_tangent_rx_matches_full_form(dtype):
+    """The tangent-form RX (default) and the full form (QS_FLAG_FULL_RX) agree to rounding
+    and both meet the tolerance against the oracle, on circuits with RX at every angle
+    range (|tan| above and below 1)."""
+    n = 16
+    circ = wc.rzrx_cz_circuit(n, 12, seed=11)
+    ref = sv.simulate(n, circ)
+    out = {}
+    for full in (False, True):
+        st = qs.State(n, dtype)
+        st.execute(qs.compile(n, circ, mode="tile", dtype=dtype, full_rx=full))
+        out[full] = st.amplitudes().astype(np.complex128)
+    if dtype == "c128":
+        for v in out.values():
+            assert np.max(np.abs(v - ref)) <= 1e-12 and sv.fidelity_loss(v, ref) <= 1e-10
+        assert np.max(np.abs(out[True] - out[False])) <= 1e-13
+    else:
+        for v in out.values():
+            assert sv.fidelity_loss(v, ref) <= 1e-5

@@ -29,6 +29,7 @@ def test_mix_equals_alone_and_oracle():
     res = srv.run(reqs, realtime=True, timeout_s=120)
     assert len(res) == len(reqs)
     assert srv.peak_in_flight > 1, "no overlap happened"
+    assert srv.batched_requests > 0, "no small requests were batched"
     assert srv.peak_mem <= budget
     for rid, r in enumerate(reqs):
         got = res[rid]
@@ -41,6 +42,14 @@ def test_mix_equals_alone_and_oracle():
         assert abs(got.norm - 1.0) <= TOL[r.dtype]
     summ = serve.latency_summary(res)
     assert summ["p99_ms"] >= summ["p50_ms"] > 0
+
+
+def test_unbatched_server_gives_the_same_bits():
+    reqs = make_requests(12, seed=6)
+    a = serve.Server(slots=4, readout=1 << 15).run(reqs, realtime=False)
+    b = serve.Server(slots=4, readout=1 << 15, batch_max=1).run(reqs, realtime=False)
+    for rid in range(len(reqs)):
+        assert a[rid].amplitudes.tobytes() == b[rid].amplitudes.tobytes()
 
 
 def test_oversized_request_rejected():
