@@ -423,19 +423,21 @@ __device__ __forceinline__ void apply_regop(typename A::reg_t (&x)[1 << K], cons
       }
       break;
     }
-    case OP_DTAB: {
+    case OP_DTAB: {   // csl: the entries that are not exactly 1
       if constexpr (sizeof(M) == 8 && K >= 1) {
         // 8-byte entries: the compiler aligns every table to 16 bytes, load two at a time
         const float4* t4 = reinterpret_cast<const float4*>(m);
 #pragma unroll
         for (int j = 0; j < (1 << K); j += 2) {
+          if (!((csl >> j) & 3u)) continue;
           const float4 v = t4[j >> 1];
-          x[j] = A::mul(M{v.x, v.y}, x[j]);
-          x[j + 1] = A::mul(M{v.z, v.w}, x[j + 1]);
+          if ((csl >> j) & 1u) x[j] = A::mul(M{v.x, v.y}, x[j]);
+          if ((csl >> (j + 1)) & 1u) x[j + 1] = A::mul(M{v.z, v.w}, x[j + 1]);
         }
       } else {
 #pragma unroll
-        for (int j = 0; j < (1 << K); j++) x[j] = A::mul(m[j], x[j]);
+        for (int j = 0; j < (1 << K); j++)
+          if ((csl >> j) & 1u) x[j] = A::mul(m[j], x[j]);
       }
       break;
     }

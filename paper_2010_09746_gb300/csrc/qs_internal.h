@@ -35,6 +35,7 @@ enum OpType : int32_t {
   OP_DENSE = 7,  // general 2^nk x 2^nk on bits kq[0..nk-1]
   OP_SWAP = 8,   // exchange bits k0 and k1 (controls cmask)
   OP_DTAB = 9,   // register stages only: multiply register element j by table entry j
+                 // where bit j of csl is set (the other entries are exactly 1)
   OP_RXT = 10,   // register stages only: tangent-form RX, (I - i t X) if s1 == 0 else
                  // (t I - i X); one pool entry (t, 0).  The factor it drops is applied by
                  // a full-form OP_RX of the same pass

@@ -147,26 +147,39 @@ void merge_diagonals(std::vector<RegOp>& rl, int K, Pool& pool) {
     std::vector<RegOp> fac, rest;
     for (size_t k = i; k < e; k++) (slot_only(rl[k]) ? fac : rest).push_back(rl[k]);
     if (!fac.empty()) {   // even a single slot factor: a table multiply avoids per-element selects
+      // entry j = product of the run's factors at register index j, divided by entry 0; the
+      // entries whose factors all equal their value at index 0 are exactly 1 and skipped
+      // (mask), and entry 0's value (a phase of the whole tile) is kept after the table for
+      // the pass-level fold
       std::vector<cd> tab(D, cd(1, 0));
+      uint32_t mask = 0;
       for (const RegOp& r : fac) {
         for (int j = 0; j < D; j++) {
           if (((uint32_t)j & r.csl) != r.csl) continue;
           if (r.type == OP_DIAG) {
             const int m = r.mat + (((j >> r.s0) & 1) ? 1 : 0);
             tab[j] *= cd(pool.f64[2 * m], pool.f64[2 * m + 1]);
+            if (((j >> r.s0) & 1) && (pool.f64[2 * (r.mat + 1)] != pool.f64[2 * r.mat] ||
+                                      pool.f64[2 * (r.mat + 1) + 1] != pool.f64[2 * r.mat + 1]))
+              mask |= 1u << j;
           } else {
             tab[j] *= r.neg ? cd(-1, 0) : cd(pool.f64[2 * r.mat], pool.f64[2 * r.mat + 1]);
+            if (r.csl != 0) mask |= 1u << j;   // differs from index 0, where the control is 0
           }
         }
       }
+      // a phase without slot controls multiplies every entry alike: it only changes entry 0
+      const cd t0 = tab[0];
       RegOp t;
       memset(&t, 0, sizeof(t));
       t.type = OP_DTAB;
       t.s0 = t.s1 = t.tb = -1;
       t.gbit = -1;
+      t.csl = mask;
       if (pool.entries() & 1) pool.add(cd(0, 0));   // tables start at an even entry (16-byte aligned)
       t.mat = (int)pool.entries();
-      for (int j = 0; j < D; j++) pool.add(tab[j]);
+      for (int j = 0; j < D; j++) pool.add(((mask >> j) & 1u) ? tab[j] / t0 : cd(1, 0));
+      pool.add(t0);
       out.push_back(t);
     } else {
       rest.insert(rest.begin(), fac.begin(), fac.end());
@@ -179,6 +192,65 @@ void merge_diagonals(std::vector<RegOp>& rl, int K, Pool& pool) {
 
 }  // namespace
 
+// Pass-level scalars.  Every uncontrolled register-stage RX may run in tangent form,
+// (I - i t X) or (t I - i X) with |t| <= 1, dropping a real factor cos or sin; every phase
+// table dropped its entry-0 phase.  Both are scalars on the whole tile, so they commute with
+// every op of the pass: their product multiplies the first table of the pass (all of its
+// entries then get multiplied), or, in a pass without tables, the first RX, which keeps
+// the full form.
+void fold_pass_factors(CompileResult* out, int st0, int nst, int K) {
+  Pool& pool = out->pool;
+  const int Dn = 1 << K;   // table entries
+  std::vector<int> tabs, rxs;   // indices into out->reg_ops, in execution order
+  for (int k = st0; k < st0 + nst; k++) {
+    const StageRec& st = out->stages[k];
+    if (st.kind != 0) continue;
+    for (int i = st.op0; i < st.op0 + st.nops; i++) {
+      const RegOp& r = out->reg_ops[i];
+      if (r.type == OP_DTAB) tabs.push_back(i);
+      else if (r.type == OP_RX && r.csl == 0 && r.cot == 0 && r.gmask == 0) rxs.push_back(i);
+    }
+  }
+  cd factor(1, 0);
+  for (int i : tabs) {
+    const RegOp& r = out->reg_ops[i];
+    factor *= cd(pool.f64[2 * (size_t)(r.mat + Dn)], pool.f64[2 * (size_t)(r.mat + Dn) + 1]);
+  }
+  const size_t first_rx_kept = (!tabs.empty() || rxs.empty()) ? rxs.size() : 0;   // index in rxs kept full
+  double scale = 1.0;
+  for (size_t q = 0; q < rxs.size(); q++) {
+    if (out->full_rx || q == first_rx_kept) continue;
+    RegOp& r = out->reg_ops[rxs[q]];
+    double* e = &pool.f64[2 * (size_t)r.mat];
+    const double c = e[0], sn = e[1];
+    r.type = OP_RXT;
+    if (std::fabs(c) >= std::fabs(sn)) {
+      r.s1 = 0;
+      e[0] = sn / c;
+      scale *= c;
+    } else {
+      r.s1 = 1;
+      e[0] = c / sn;
+      scale *= sn;
+    }
+    e[1] = 0.0;
+  }
+  factor *= scale;
+  if (!tabs.empty()) {
+    RegOp& r = out->reg_ops[tabs[0]];
+    for (int j = 0; j < Dn; j++) {
+      const cd v = cd(pool.f64[2 * (size_t)(r.mat + j)], pool.f64[2 * (size_t)(r.mat + j) + 1]) * factor;
+      pool.f64[2 * (size_t)(r.mat + j)] = v.real();
+      pool.f64[2 * (size_t)(r.mat + j) + 1] = v.imag();
+    }
+    r.csl = (Dn >= 32) ? 0xFFFFFFFFu : ((1u << Dn) - 1u);
+  } else if (!rxs.empty() && first_rx_kept < rxs.size()) {
+    double* e = &pool.f64[2 * (size_t)out->reg_ops[rxs[first_rx_kept]].mat];
+    e[0] *= factor.real();
+    e[1] *= factor.real();
+  }
+}
+
 int register_bits(int dtype, int L, int requested) {
   const int kmax = (dtype == QS_C128) ? 4 : 5;
   const int k = (requested > 0) ? std::min(requested, kmax) : kmax;
@@ -187,11 +259,7 @@ int register_bits(int dtype, int L, int requested) {
 
 void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* out, int* st0, int* nst) {
   const int N = (int)ops.size();
-  // tangent-form RX: every uncontrolled register-stage RX after the pass's first one is
-  // applied as (I - i t X) or (t I - i X) (|t| <= 1); the product of the dropped factors
-  // (cos or sin, a real scalar that commutes with every op) goes into the first one
-  int first_rx = -1;
-  double rx_scale = 1.0;
+
   std::vector<OpInfo> info(N);
   for (int i = 0; i < N; i++) info[i] = classify_op(ops[i]);
   // dependency DAG over tile bits (same grouping rule as the circuit DAG)
@@ -400,27 +468,6 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
         rl.push_back(r);
       }
       merge_diagonals(rl, K, out->pool);
-      if (!out->full_rx)
-        for (RegOp& r : rl) {
-          if (r.type != OP_RX || r.csl != 0 || r.cot != 0 || r.gmask != 0) continue;
-          if (first_rx < 0) {
-            first_rx = r.mat;
-            continue;
-          }
-          double* e = &out->pool.f64[2 * (size_t)r.mat];
-          const double c = e[0], sn = e[1];
-          r.type = OP_RXT;
-          if (std::fabs(c) >= std::fabs(sn)) {
-            r.s1 = 0;
-            e[0] = sn / c;
-            rx_scale *= c;
-          } else {
-            r.s1 = 1;
-            e[0] = c / sn;
-            rx_scale *= sn;
-          }
-          e[1] = 0.0;
-        }
       st.op0 = (int)out->reg_ops.size();
       out->reg_ops.insert(out->reg_ops.end(), rl.begin(), rl.end());
       st.nops = (int)rl.size();
@@ -435,11 +482,8 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
       if (!done[rem[r]]) rem[w++] = rem[r];
     rem.resize(w);
   }
-  if (first_rx >= 0) {
-    out->pool.f64[2 * (size_t)first_rx] *= rx_scale;
-    out->pool.f64[2 * (size_t)first_rx + 1] *= rx_scale;
-  }
   *nst = (int)out->stages.size() - *st0;
+  fold_pass_factors(out, *st0, *nst, K);
 }
 
 }  // namespace qs
@@ -495,7 +539,10 @@ double stage_alu_per_amp(const CompileResult& cr, int st0, int nst) {
         case OP_RX: a += pick(kRX, cr.pol) * fraction(ctl); break;
         case OP_RXT: a += pick(kRXT, cr.pol) * fraction(ctl); break;
         case OP_U1: a += pick(kU1, cr.pol) * fraction(ctl); break;
-        case OP_DIAG: case OP_DTAB: a += pick(kMUL, cr.pol) * fraction(ctl); break;
+        case OP_DIAG: a += pick(kMUL, cr.pol) * fraction(ctl); break;
+        case OP_DTAB:   // only the entries that are not exactly 1 (mask in csl) are multiplied
+          a += pick(kMUL, cr.pol) * (double)__builtin_popcount(r.csl) / (double)(1u << __builtin_popcount((uint32_t)st.rmask));
+          break;
         case OP_PHASE: a += (r.neg ? pick(kNEG, cr.pol) : pick(kMUL, cr.pol)) * fraction(ctl); break;
         case OP_U2: a += pick(kU2, cr.pol) * fraction(ctl); break;
         default: break;
