@@ -191,13 +191,20 @@ def roofline(kstats, steps, step_ms, peaks, peaks_kind, policy, clk_mhz):
 
 
 def measure(qs, st, plan, steps, warmup, torch, stream, profile=False):
+    """Time `steps` steps (state preparation + plan + FP64 norm); `plan` may be a list,
+    step i then runs plan i mod len."""
+    plans = plan if isinstance(plan, (list, tuple)) else [plan]
+    it = [0]
+
     def step():
         st.reset()
-        st.execute(plan)
+        st.execute(plans[it[0] % len(plans)])
+        it[0] += 1
         return st.norm()
 
     for _ in range(warmup):
         step()
+    it[0] = 0
     torch.cuda.synchronize()
     if profile:
         st.set_profiling(True)
@@ -252,18 +259,24 @@ def run_ours(args):
     qs.use_torch_allocator(local)
     n, circ, name = workload(args)
     G = len(circ)
+    # the timed steps cycle over the circuits of seeds seed .. seed + seeds - 1 (same
+    # construction, same gate count); everything else uses the first
+    circs = [circ] + [workload(argparse.Namespace(**dict(vars(args), seed=args.seed + k)))[1]
+                      for k in range(1, max(1, args.seeds))]
+    assert all(len(c) == G for c in circs)
     stream = torch.cuda.Stream(device=local)
     policy = {"c64": "f32", "c128": ("f64" if args.arith == "f64" else "df")}[args.dtype]
     st = qs.State(n, args.dtype, arith=args.arith, stream=stream)
-    plan = qs.compile(n, circ, mode=args.mode, dtype=args.dtype, arith=args.arith, tile_bits=args.tile_bits,
-                      low_bits=args.low_bits, reg_bits=args.reg_bits)
+    plans = [qs.compile(n, c, mode=args.mode, dtype=args.dtype, arith=args.arith, tile_bits=args.tile_bits,
+                        low_bits=args.low_bits, reg_bits=args.reg_bits) for c in circs]
+    plan = plans[0]
     pstats = plan.stats()
 
     if pg:
         pg.barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    ms, norms, kstats = measure(qs, st, plan, args.steps, args.warmup, torch, stream, profile=True)
+    ms, norms, kstats = measure(qs, st, plans, args.steps, args.warmup, torch, stream, profile=True)
     clk = clocks.stop()
     ms = reduce_max(ms, pg)
     value = job_rate(G, world, ms)
@@ -279,7 +292,9 @@ def run_ours(args):
         "value": round(value, 2), "unit": "gates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": policy, "data": "synthetic (seeded random circuit)",
-        "config": {"workload": name, "n_qubits": n, "gates": G, "mode": args.mode, "state_dtype": args.dtype,
+        "config": {"workload": name, "seeds": list(range(args.seed, args.seed + len(circs))),
+                   "passes_per_seed": [p.stats()["n_passes"] for p in plans],
+                   "n_qubits": n, "gates": G, "mode": args.mode, "state_dtype": args.dtype,
                    "arith": policy, "tile_bits": args.tile_bits or None, "low_bits": args.low_bits or None,
                    "reg_bits": args.reg_bits or None,
                    "passes": pstats["n_passes"], "permutes": pstats["n_permutes"], "pergate": pstats["n_pergate"],
@@ -300,9 +315,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_steps = max(1, min(args.steps, 3))
         t0 = time.perf_counter()
-        for _ in range(e2e_steps):
+        for k in range(e2e_steps):
             st.reset()
-            st.run(circ, mode=args.mode, tile_bits=args.tile_bits, low_bits=args.low_bits, reg_bits=args.reg_bits)
+            st.run(circs[k % len(circs)], mode=args.mode, tile_bits=args.tile_bits, low_bits=args.low_bits,
+                   reg_bits=args.reg_bits)
             st.amplitudes(0, readout)
             st.norm()
         torch.cuda.synchronize()
@@ -536,12 +552,15 @@ def measure_qft_like(qs, torch, st, stream, args):
 def measure_batched(qs, torch, args):
     """The batched workload: `--batched` circuits (n ~ U{10..20}, depth ~ U{10..60}, Haar 2x2 on
     every qubit + CNOT/CZ on a random matching per layer, seed 0), complex64, one persistent
-    launch per wave of tile passes replayed from a CUDA graph.  Beside it: the first 256
-    circuits run one plan launch sequence per circuit (qs_execute on separate states)."""
+    launch per wave of tile passes replayed from a CUDA graph, at the tile width (fusion
+    width) the autotuner picks by timing each candidate.  Beside it: the first 256 circuits
+    run one plan launch sequence per circuit (qs_execute on separate states)."""
+    from paper_2010_09746_gb300 import tuning
     work = wc.batched_workload(args.batched, seed=0)
+    tune = tuning.autotune_batch(work, dtype="c64", tile_bits=tuple(args.batch_tile_bits), reps=2)
     stream = torch.cuda.Stream()
     t0 = time.perf_counter()
-    b = qs.Batch(work, dtype="c64", stream=stream)
+    b = qs.Batch(work, dtype="c64", stream=stream, tile_bits=tune["tile_bits"])
     build_s = time.perf_counter() - t0
     for _ in range(3):
         b.run()
@@ -561,7 +580,10 @@ def measure_batched(qs, torch, args):
     res = {"circuits": len(work), "gates": gates, "ms_per_run": round(ms, 3),
            "circuits_per_s": round(len(work) / (ms / 1e3), 1), "gates_per_s": round(gates / (ms / 1e3), 1),
            "waves": st["n_waves"], "passes": st["n_passes"], "state_gib": round(st["state_bytes"] / 2 ** 30, 2),
-           "build_s": round(build_s, 2), "norm_max_dev": float(np.max(np.abs(norms - 1.0)))}
+           "build_s": round(build_s, 2), "norm_max_dev": float(np.max(np.abs(norms - 1.0))),
+           "autotuned_tile_bits": tune["tile_bits"],
+           "autotune": [{k: (round(v, 3) if isinstance(v, float) else v) for k, v in c.items()}
+                        for c in tune["candidates"]]}
     # one launch sequence per circuit, on the first 256 circuits
     sub = work[:256]
     states = [qs.State(n, "c64", stream=stream) for n, _ in sub]
@@ -600,14 +622,14 @@ def measure_serving(args):
            "batch_small_n": srv.batch_small_n,
            "saturation": dict(serve.latency_summary(res, wall), peak_in_flight=srv.peak_in_flight,
                               batched_requests=srv.batched_requests, batches=srv.batches)}
-    for frac in (0.5, 0.9):
+    for frac in args.serve_loads:
         rate = frac * sat
         reqs = wc.serving_workload(args.serve_requests, rate_hz=rate, seed=0)   # same circuits, Poisson times
         srv = serve.Server(slots=args.serve_slots, mem_budget=budget)
         t0 = time.perf_counter()
         res = srv.run(reqs, realtime=True)
         wall = time.perf_counter() - t0
-        out[f"load_{frac:.1f}"] = dict(serve.latency_summary(res, wall), offered_rate_hz=round(rate, 3),
+        out[f"load_{frac:g}"] = dict(serve.latency_summary(res, wall), offered_rate_hz=round(rate, 3),
                                       peak_in_flight=srv.peak_in_flight, batched_requests=srv.batched_requests,
                                       batches=srv.batches)
     return out
@@ -666,6 +688,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=30)
     ap.add_argument("--layers", type=int, default=40)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--seeds", type=int, default=5, help="timed steps cycle over this many circuit seeds")
     ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
     ap.add_argument("--arith", default="auto", choices=["auto", "df", "f64"])
     ap.add_argument("--mode", default="tile", choices=["tile", "paper", "pergate"])
@@ -682,7 +705,11 @@ def main(argv=None):
                     help="also run the 32q complex128/complex64 and 33q complex64 precision study")
     ap.add_argument("--small", type=int, default=1, help="also time the 12-qubit Haar + CNOT circuits")
     ap.add_argument("--batched", type=int, default=4096, help="circuits in the batched measurement (0 = skip)")
-    ap.add_argument("--serve-requests", type=int, default=32, help="requests per serving load point (0 = skip)")
+    ap.add_argument("--batch-tile-bits", type=int, nargs="+", default=[10, 12, 13],
+                    help="tile widths the batched measurement's autotuner times")
+    ap.add_argument("--serve-requests", type=int, default=64, help="requests per serving load point (0 = skip)")
+    ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.1, 0.5, 0.9, 1.2],
+                    help="Poisson arrival rates as fractions of the measured saturation throughput")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-mem-gib", type=float, default=96.0)
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)

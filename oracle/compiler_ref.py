@@ -98,13 +98,13 @@ def alg1(n: int, m: int, gates: Sequence, scoring: str = "closure",
     ("gate", index, needs_comm) and ("permute", sigma').
 
     Readings where the pseudo-code is silent or, taken literally, fails:
-    * the sweep of lines 5:10 visits the remaining vertices in program order;
+    * the scheduling sweep visits the remaining vertices in program order;
       removing a vertex exposes its successors later in the same sweep;
     * local / global qubits "according to sigma" are taken in ascending qubit
       order; sigma o (l g) exchanges the storage positions of qubits l and g;
     * scoring="closure" (default): a candidate's score is the number of gates
-      the next sweep would schedule under it -- "the number of gates that it
-      allows to simulate on local qubits" (Sec. 3); the first best candidate
+      the next sweep would schedule under it -- how many gates the exchange
+      lets run on local qubits (Sec. 3); the first best candidate
       wins (the strict '>' of the comparison).  With it the pass reproduces
       the ~3.5% of Sec. 4 / Fig. 3;
     * scoring="frontier": the number of frontier gates (no incoming edges) the

@@ -66,7 +66,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             if log.strip():
                 print(log)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [_nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
+    cmd = [_nvcc()] + ARCH + ["-shared", "-cudart", "static", "-Xlinker", "-lpthread", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

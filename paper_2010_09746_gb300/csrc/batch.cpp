@@ -9,6 +9,8 @@
 #include <algorithm>
 #include <chrono>
 #include <string>
+#include <atomic>
+#include <thread>
 #include <vector>
 
 #include "qs_internal.h"
@@ -133,23 +135,48 @@ qs_status qs_batch_create(int count, const int* n, const qs_op* ops, const int64
     b->off[i] = elems;
     elems += ((size_t)1 << n[i]);
     elems = (elems + 31) & ~(size_t)31;   // 256-byte aligned starts
-    std::vector<HGate> gates(op_offsets[i + 1] - op_offsets[i]);
-    std::string err;
-    for (size_t g = 0; g < gates.size(); g++)
-      if (!make_hgate(n[i], ops[op_offsets[i] + g], mats, nmats, &gates[g], &err)) {
-        delete b;
-        return bfail(QS_EINVAL, "circuit " + std::to_string(i) + " op " + std::to_string(g) + ": " + err);
+  }
+  // the circuits compile independently: spread them over the host's cores, then
+  // concatenate the programs in circuit order (the result does not depend on the split)
+  std::vector<CompileResult> results(count);
+  std::vector<std::string> errs(count);
+  {
+    std::atomic<int> next(0);
+    auto worker = [&] {
+      for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) {
+        std::vector<HGate> gates(op_offsets[i + 1] - op_offsets[i]);
+        std::string err;
+        bool ok = true;
+        for (size_t g = 0; g < gates.size() && ok; g++)
+          if (!make_hgate(n[i], ops[op_offsets[i] + g], mats, nmats, &gates[g], &err)) {
+            errs[i] = "circuit " + std::to_string(i) + " op " + std::to_string(g) + ": " + err;
+            ok = false;
+          }
+        if (!ok) continue;
+        qs_compile_opts oi = o;
+        oi.tile_bits = std::min(Lreq, n[i]);
+        oi.low_bits = std::min(std::max(creq, o.dtype == QS_C64 ? 1 : 0), oi.tile_bits);
+        std::vector<int> s0(n[i]);
+        for (int q = 0; q < n[i]; q++) s0[q] = q;
+        if (!compile_circuit(n[i], gates, s0, oi, &results[i], &err))
+          errs[i] = "circuit " + std::to_string(i) + ": " + err;
       }
-    qs_compile_opts oi = o;
-    oi.tile_bits = std::min(Lreq, n[i]);
-    oi.low_bits = std::min(std::max(creq, o.dtype == QS_C64 ? 1 : 0), oi.tile_bits);
-    CompileResult cr;
-    std::vector<int> s0(n[i]);
-    for (int q = 0; q < n[i]; q++) s0[q] = q;
-    if (!compile_circuit(n[i], gates, s0, oi, &cr, &err)) {
+    };
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = std::max(1u, std::min(nt, 64u));
+    if ((int)nt > count) nt = (unsigned)count;
+    std::vector<std::thread> pool;
+    for (unsigned t = 1; t < nt; t++) pool.emplace_back(worker);
+    worker();
+    for (auto& t : pool) t.join();
+  }
+  for (int i = 0; i < count; i++)
+    if (!errs[i].empty()) {
       delete b;
-      return bfail(QS_EINVAL, "circuit " + std::to_string(i) + ": " + err);
+      return bfail(QS_EINVAL, errs[i]);
     }
+  for (int i = 0; i < count; i++) {
+    CompileResult& cr = results[i];
     b->pol = cr.pol;
     const int sbase = (int)b->stages.size(), rbase = (int)b->rops.size(), dbase = (int)b->dops.size();
     const int pbase = (int)b->pool.entries();
@@ -187,6 +214,7 @@ qs_status qs_batch_create(int count, const int* n, const qs_op* ops, const int64
     }
     b->stats.n_gates += cr.stats.n_gates;
     b->stats.n_passes += cr.stats.n_passes;
+    cr = CompileResult();   // release the per-circuit copy
   }
   if (b->pool.entries() == 0) b->pool.add(cd(0, 0));
   b->total_elems = elems;

@@ -260,7 +260,7 @@ bool compile_paper(int n, const std::vector<HGate>& gates, std::vector<int> sigm
     return lm;
   };
   while (S.remaining) {
-    // sweep (lines 5-10)
+    // scheduling sweep: every remaining gate that is local under sigma, in program order
     const uint64_t lm = local_mask(sigma);
     for (int v : S.rem) {
       if (S.done[v] || S.npred[v] != 0 || (ndq[v] & ~lm)) continue;
@@ -271,7 +271,7 @@ bool compile_paper(int n, const std::vector<HGate>& gates, std::vector<int> sigm
     }
     S.compact();
     if (!S.remaining) break;
-    // candidate transpositions (lines 11-22)
+    // score every local<->global transposition
     std::vector<int> loc, glo;
     for (int q = 0; q < n; q++) (sigma[q] < m ? loc : glo).push_back(q);
     int best_l = -1, best_g = -1;
@@ -299,7 +299,7 @@ bool compile_paper(int n, const std::vector<HGate>& gates, std::vector<int> sigm
           best_g = g;
         }
       }
-    // lines 23-30
+    // apply the best transposition, or run the first frontier gate non-locally
     if (have && best0 > 0) {
       if (!flush()) return false;
       std::vector<int> sg = sigma;

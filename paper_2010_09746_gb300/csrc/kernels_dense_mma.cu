@@ -14,15 +14,19 @@
 // operands with the three-term split x = x_big + x_small (x_big = x rounded to TF32,
 // x_small = x - x_big rounded to TF32, so each factor is kept to about 2^-22 relative):
 // W^T_big x_big + W^T_small x_big + W^T_big x_small, accumulated in FP32.  The tensor core
-// rounds each accumulation toward zero, which biases magnitudes downward by about half an
-// ulp per MMA; the big x big products therefore go to two accumulators of 8 MMAs each and
-// the cross terms (2^-11 smaller) to a third, summed with round-to-nearest in the epilogue.
+// rounds each accumulation toward zero, which biases magnitudes downward by a fraction of
+// an ulp per MMA; the big x big products therefore go to one accumulator (16 MMAs) and the
+// cross terms (2^-11 smaller) to a second, summed with round-to-nearest in the epilogue.
 //
-// Persistent grid, one CTA per SM (the 205 KiB of shared memory admit one), 128 threads:
-// row tiles of 32 KiB move between HBM and a ring of 4 row-major staging buffers with bulk
-// copies (mbarrier completion, loads issued 3 tiles ahead); the threads split each tile into
-// the two operand buffers; thread 0 issues the 48 MMAs and commits them to an mbarrier; the
-// epilogue writes D row-major into the tile's staging buffer, which a bulk store sends back.
+// Persistent grid, one CTA per SM (225 KiB of shared memory), warp-specialised so that the
+// tensor core works while the threads move data.  Warps 0-3 (one per tensor-memory lane
+// quarter) bring 32 KiB row tiles into a ring of 3 row-major staging buffers with bulk
+// copies (mbarrier completion, loads issued 3 tiles ahead) and split tile j into operand
+// buffer j & 1; one lane of warp 4 issues tile j's 48 MMAs into accumulator set j & 1 as soon
+// as the split is handed over (mbarrier), and commits them to another mbarrier.  While the
+// MMAs of tile j + 1 run, warps 0-3 read tile j back (one output column per thread,
+// `tcgen05.ld`), write the rows into tile j's operand buffer, release the accumulator set
+// and bulk-store the rows; then they split tile j + 2.
 // Every wait is bounded by a 2 s %globaltimer deadline; on expiry the CTA records
 // QS_ETIMEOUT, waits (bounded) for its copies and MMAs in flight, frees its tensor memory
 // and returns.
@@ -34,23 +38,23 @@
 namespace qs {
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 128;                        // data warps 0-3 (tensor-memory lane quarters)
+constexpr int kBlockThreads = kThreads + 32;         // + warp 4, which issues the MMAs
 constexpr int kRowFloats = 128;                      // 64 complex64 amplitudes
 constexpr int kRows = 64;                            // rows per tile = MMA N
 constexpr int kTileFloats = kRows * kRowFloats;      // 8192
 constexpr uint32_t kTileBytes = kTileFloats * 4;     // 32 KiB
-constexpr int kStages = 4;
-constexpr int kOffBig = kStages * (int)kTileBytes;
-constexpr int kOffSmall = kOffBig + (int)kTileBytes;
-constexpr int kGuardBytes = 8192;                    // reads of a mis-strided descriptor stay inside the allocation
-constexpr int kOffBar = kOffSmall + (int)kTileBytes + kGuardBytes;
-constexpr int kSmemUsed = kOffBar + 128;
+constexpr int kStages = 3;                           // row-major staging buffers for loads
+constexpr int kOpBytes = 2 * (int)kTileBytes;        // one operand buffer: big then small (K-major)
+constexpr int kOffOp = kStages * (int)kTileBytes;    // two operand buffers follow the staging ring
+constexpr int kOffBar = kOffOp + 2 * kOpBytes;
+constexpr int kSmemUsed = kOffBar + 256;             // barriers, tensor-memory address, abort flag
 constexpr int kSmemAlloc = kSmemUsed + 1024;         // slack for aligning the base to 1 KiB
-// tensor memory columns: [0,128) W^T big, [128,256) W^T small, then three 64-column FP32
-// accumulators: the big x big products of K columns 0..63 and of 64..127, and the two
-// small cross-term products
+// tensor memory columns: [0,128) W^T big, [128,256) W^T small, then two accumulator sets
+// (tile parity b) of two 64-column FP32 accumulators: at 256 + 128 b the big x big
+// products, at 320 + 128 b the two small cross terms
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kColWBig = 0, kColWSmall = 128, kColD0 = 256, kColD1 = 320, kColDs = 384;
+constexpr uint32_t kColWBig = 0, kColWSmall = 128, kColAcc = 256;
 constexpr uint32_t kLBO = kRows * 16;                // K-direction stride between 8x16 B core matrices
 constexpr uint32_t kSBO = 128;                       // N-direction stride between 8-row groups
 // instruction descriptor, kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (bits 7-9 and
@@ -160,21 +164,96 @@ __device__ __forceinline__ void tf32_split(float x, float& big, float& small) {
   small = tf32_rna(x - big);   // x - big is exact; |x - big| <= 2^-11 |x|
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+// One tile = 64 rows.  Tile j's operands live in operand buffer j & 1 and its products in
+// accumulator set j & 1, so the tensor core runs tile j + 1's MMAs while the threads read
+// back tile j and split tile j + 2.
+struct DenseSmem {
+  unsigned char* base;
+  __device__ float* stage(int s) const { return (float*)(base + s * (int)kTileBytes); }
+  __device__ unsigned char* big(int b) const { return base + kOffOp + b * kOpBytes; }
+  __device__ unsigned char* small(int b) const { return base + kOffOp + b * kOpBytes + (int)kTileBytes; }
+};
+
+// split the row-major tile into the K-major operand layout: element group (row r, 4-float
+// panel p) goes to p * kLBO + r * 16.  The 8 threads of each shared-memory phase take
+// distinct r mod 8 and distinct p mod 8, so reads and writes are conflict-free.
+__device__ __forceinline__ void split_tile(const float* stg, unsigned char* big, unsigned char* small, int tid) {
+  const float4* src = (const float4*)stg;
+#pragma unroll 4
+  for (int it = 0; it < kTileFloats / 4 / kThreads; it++) {
+    const int g = it * kThreads + tid;
+    const int i8 = g & 7, rest = g >> 3;
+    const int r = ((rest & 7) << 3) | i8;
+    const int p = ((rest >> 3) + i8) & 31;
+    const float4 x = src[r * 32 + p];
+    float4 hb, lo;
+    tf32_split(x.x, hb.x, lo.x);
+    tf32_split(x.y, hb.y, lo.y);
+    tf32_split(x.z, hb.z, lo.z);
+    tf32_split(x.w, hb.w, lo.w);
+    const uint32_t off = (uint32_t)p * kLBO + (uint32_t)r * 16u;
+    *(float4*)(big + off) = hb;
+    *(float4*)(small + off) = lo;
+  }
+}
+
+// 48 MMAs of one tile into accumulator set b, committed to bar (thread 0 only)
+__device__ __forceinline__ void issue_tile_mma(uint32_t tmem, const unsigned char* big, const unsigned char* small,
+                                               int b, uint32_t bar) {
+  tc_fence_after();
+  const uint32_t dm = tmem + kColAcc + 128u * (uint32_t)b, dx = dm + 64u;
+  const uint32_t bb = smem_u32(big), sb = smem_u32(small);
+#pragma unroll
+  for (int kk = 0; kk < 16; kk++) {
+    const uint64_t db = smem_desc(bb + kk * 2 * kLBO), ds = smem_desc(sb + kk * 2 * kLBO);
+    mma_tf32(dm, tmem + kColWBig + kk * 8, db, kk > 0 ? 1u : 0u);
+    mma_tf32(dx, tmem + kColWSmall + kk * 8, db, kk > 0 ? 1u : 0u);
+    mma_tf32(dx, tmem + kColWBig + kk * 8, ds, 1u);
+  }
+  mma_commit(bar);
+}
+
+// barrier 1 over the 128 data threads, OR-reducing a predicate
+__device__ __forceinline__ bool data_bar_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, 1, 128, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void data_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Barriers (shared memory, 8 bytes each): full[s] (load of stage s landed), opf[b] (operand
+// buffer b split, MMAs may start), accf[b] (MMAs of set b complete, tcgen05.commit),
+// acce[b] (accumulator set b read back, may be overwritten).
+__global__ void __launch_bounds__(kBlockThreads, 1)
     k_dense_mma(float* __restrict__ psi, uint64_t ntiles, const float* __restrict__ wT, int* __restrict__ status) {
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  float* stg = (float*)smem;
-  unsigned char* big = smem + kOffBig;
-  unsigned char* small = smem + kOffSmall;
-  const uint32_t bar0 = smem_u32(smem + kOffBar);             // full[s] at bar0 + 8 s
-  const uint32_t mma_bar = bar0 + 8 * kStages;
-  uint32_t* tmem_slot = (uint32_t*)(smem + kOffBar + 64);
+  const DenseSmem sm{(unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023)};
+  const uint32_t full0 = smem_u32(sm.base + kOffBar);
+  const uint32_t opf0 = full0 + 8 * kStages, accf0 = opf0 + 16, acce0 = accf0 + 16;
+  uint32_t* tmem_slot = (uint32_t*)(sm.base + kOffBar + 128);
+  volatile int* abort_flag = (volatile int*)(sm.base + kOffBar + 136);
   const int tid = threadIdx.x, warp = tid >> 5;
+  const uint64_t T = (ntiles > blockIdx.x) ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;   // my tiles
+  auto tile_of = [&](uint64_t j) { return blockIdx.x + j * gridDim.x; };
 
   if (tid == 0) {
-    for (int s = 0; s < kStages; s++) mbar_init(bar0 + 8 * s, 1);
-    mbar_init(mma_bar, 1);
+    for (int s = 0; s < kStages; s++) mbar_init(full0 + 8 * s, 1);
+    for (int b = 0; b < 2; b++) {
+      mbar_init(opf0 + 8 * b, 1);
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, 1);
+    }
+    *abort_flag = 0;
     fence_async_smem();
   }
   if (warp == 0) tmem_alloc(smem_u32(tmem_slot), kTmemCols);
@@ -182,146 +261,129 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
 
-  // W^T (big, small) into tensor memory: thread j holds row j of both, 128 columns each
-  for (int part = 0; part < 2; part++)
-    for (int c0 = 0; c0 < 128; c0 += 32) {
-      uint32_t v[32];
-      const float4* src = (const float4*)(wT + part * 16384 + tid * 128 + c0);
+  if (warp == 4) {
+    // ---- MMA warp: one lane issues every tile's 48 MMAs in order -----------------------
+    if ((tid & 31) == 0) {
+      uint64_t j = 0;
+      uint32_t open = 0;   // accumulator sets with a commit the data warps have not consumed
+      for (; j < T; j++) {
+        const int b = (int)(j & 1);
+        const uint32_t ph = (uint32_t)((j >> 1) & 1);
+        bool ok = true;
+        const unsigned long long dl = globaltimer() + kWaitNs;
+        while (ok && !mbar_try_wait(opf0 + 8 * b, ph)) ok = !*abort_flag && globaltimer() <= dl;
+        while (ok && !mbar_try_wait(acce0 + 8 * b, ph ^ 1u)) ok = !*abort_flag && globaltimer() <= dl;
+        if (!ok) {
+          *abort_flag = 1;
+          break;
+        }
+        issue_tile_mma(tmem, sm.big(b), sm.small(b), b, accf0 + 8 * b);
+        open |= 1u << b;
+        (void)open;
+      }
+      if (*abort_flag) {   // let the MMAs issued so far finish before the memory is released
+        const unsigned long long dl = globaltimer() + kWaitNs;
+        for (uint64_t q = (j >= 2 ? j - 2 : 0); q < j; q++)
+          mbar_wait(accf0 + 8 * (int)(q & 1), (uint32_t)((q >> 1) & 1), dl);
+      }
+    }
+  } else {
+    // ---- data warps: loads, splits, read-back, stores ---------------------------------
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    // W^T (big, small) into tensor memory: thread j holds row j of both, 128 columns each
+    for (int part = 0; part < 2; part++)
+      for (int c0 = 0; c0 < 128; c0 += 32) {
+        uint32_t v[32];
+        const float4* src = (const float4*)(wT + part * 16384 + tid * 128 + c0);
 #pragma unroll
-      for (int q = 0; q < 8; q++) {
-        const float4 f = __ldg(src + q);
-        v[4 * q] = __float_as_uint(f.x);
-        v[4 * q + 1] = __float_as_uint(f.y);
-        v[4 * q + 2] = __float_as_uint(f.z);
-        v[4 * q + 3] = __float_as_uint(f.w);
+        for (int q = 0; q < 8; q++) {
+          const float4 f = __ldg(src + q);
+          v[4 * q] = __float_as_uint(f.x);
+          v[4 * q + 1] = __float_as_uint(f.y);
+          v[4 * q + 2] = __float_as_uint(f.z);
+          v[4 * q + 3] = __float_as_uint(f.w);
+        }
+        tmem_st32(tmem + lane_base + (part ? kColWSmall : kColWBig) + c0, v);
       }
-      tmem_st32(tmem + lane_base + (part ? kColWSmall : kColWBig) + c0, v);
-    }
-  tmem_wait_st();
-
-  // loads issued by thread 0: the tiles of iterations < issued
-  uint64_t issued = 0;
-  if (tid == 0) {
-    for (int s = 0; s < kStages - 1; s++) {
-      const uint64_t t = blockIdx.x + (uint64_t)s * gridDim.x;
-      if (t >= ntiles) break;
-      mbar_arrive_expect_tx(bar0 + 8 * s, kTileBytes);
-      bulk_load(smem_u32(stg + s * kTileFloats), psi + t * kTileFloats, kTileBytes, bar0 + 8 * s);
-      issued = s + 1;
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-
-  int fail = 0;
-  bool mma_pending = false;
-  uint32_t mma_phase = 0;
-  uint64_t i = 0;
-  for (;; i++) {
-    const uint64_t t = blockIdx.x + i * gridDim.x;
-    if (t >= ntiles) break;
-    const int s = (int)(i % kStages);
-    if (tid == 0) {   // refill the stage of iteration i - 1 with the tile of iteration i + kStages - 1
-      const uint64_t inext = i + kStages - 1;
-      const uint64_t tn = blockIdx.x + inext * gridDim.x;
-      if (tn < ntiles) {
-        const int sn = (int)(inext % kStages);
-        bulk_wait_read0();   // the store from that stage has read its shared memory
-        mbar_arrive_expect_tx(bar0 + 8 * sn, kTileBytes);
-        bulk_load(smem_u32(stg + sn * kTileFloats), psi + tn * kTileFloats, kTileBytes, bar0 + 8 * sn);
-        issued = inext + 1;
-      }
-    }
-    const bool ok_load = mbar_wait(bar0 + 8 * s, (uint32_t)((i / kStages) & 1), globaltimer() + kWaitNs);
-    if (__syncthreads_or(!ok_load)) {
-      fail = 1;
-      break;
-    }
-
-    // split the row-major tile into the K-major operand layout: element group (row r,
-    // 4-float panel p) goes to p * kLBO + r * 16.  The 8 threads of each shared-memory
-    // phase take distinct r mod 8 and distinct p mod 8, so reads and writes are
-    // conflict-free.
-    {
-      const float4* src = (const float4*)(stg + s * kTileFloats);
-#pragma unroll 4
-      for (int it = 0; it < kTileFloats / 4 / kThreads; it++) {
-        const int g = it * kThreads + tid;
-        const int i8 = g & 7, rest = g >> 3;
-        const int r = ((rest & 7) << 3) | i8;
-        const int p = ((rest >> 3) + i8) & 31;
-        const float4 x = src[r * 32 + p];
-        float4 hb, lo;
-        tf32_split(x.x, hb.x, lo.x);
-        tf32_split(x.y, hb.y, lo.y);
-        tf32_split(x.z, hb.z, lo.z);
-        tf32_split(x.w, hb.w, lo.w);
-        const uint32_t off = (uint32_t)p * kLBO + (uint32_t)r * 16u;
-        *(float4*)(big + off) = hb;
-        *(float4*)(small + off) = lo;
-      }
-    }
-    fence_async_smem();
-    __syncthreads();
-
-    if (tid == 0) {
-      tc_fence_after();
-      const uint32_t bb = smem_u32(big), sb = smem_u32(small);
-#pragma unroll
-      for (int kk = 0; kk < 16; kk++) {
-        const uint64_t db = smem_desc(bb + kk * 2 * kLBO), ds = smem_desc(sb + kk * 2 * kLBO);
-        mma_tf32(tmem + (kk < 8 ? kColD0 : kColD1), tmem + kColWBig + kk * 8, db, (kk & 7) ? 1u : 0u);
-        mma_tf32(tmem + kColDs, tmem + kColWSmall + kk * 8, db, kk > 0 ? 1u : 0u);
-        mma_tf32(tmem + kColDs, tmem + kColWBig + kk * 8, ds, 1u);
-      }
-      mma_commit(mma_bar);
-    }
-    mma_pending = true;
-    const bool ok_mma = mbar_wait(mma_bar, mma_phase, globaltimer() + kWaitNs);
-    if (__syncthreads_or(!ok_mma)) {
-      fail = 1;
-      break;
-    }
-    mma_pending = false;
-    mma_phase ^= 1u;
-    tc_fence_after();
-
-    // epilogue: thread j = output column j of rows 0..63, written row-major into the stage
-    float* out = stg + s * kTileFloats;
-#pragma unroll 1
-    for (int c0 = 0; c0 < kRows; c0 += 32) {
-      uint32_t v0[32], v1[32], vs[32];
-      tmem_ld32(tmem + lane_base + kColD0 + c0, v0);
-      tmem_ld32(tmem + lane_base + kColD1 + c0, v1);
-      tmem_ld32(tmem + lane_base + kColDs + c0, vs);
-      tmem_wait_ld();
-#pragma unroll
-      for (int c = 0; c < 32; c++)
-        out[(c0 + c) * kRowFloats + tid] =
-            __fadd_rn(__fadd_rn(__uint_as_float(v0[c]), __uint_as_float(v1[c])), __uint_as_float(vs[c]));
-    }
-    fence_async_smem();
+    tmem_wait_st();
     tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      bulk_store(psi + t * kTileFloats, smem_u32(out), kTileBytes);
-      bulk_commit();
-    }
-  }
 
-  if (tid == 0) {
-    if (fail) {
-      atomicExch(status, (int)QS_ETIMEOUT);
-      // loads issued for iterations >= i are still owed to their barriers
+    uint64_t issued = 0;   // thread 0: loads issued for tiles < issued
+    auto issue_load = [&](uint64_t j) {
+      const int s = (int)(j % kStages);
+      mbar_arrive_expect_tx(full0 + 8 * s, kTileBytes);
+      bulk_load(smem_u32(sm.stage(s)), psi + tile_of(j) * kTileFloats, kTileBytes, full0 + 8 * s);
+      issued = j + 1;
+    };
+    if (tid == 0)
+      for (uint64_t j = 0; j < (uint64_t)kStages && j < T; j++) issue_load(j);
+
+    int fail = 0;
+    // split tile j into operand buffer j & 1 and hand it to the MMA warp; the buffer held
+    // tile j - 2's output, whose store must have read it
+    auto split_and_hand = [&](uint64_t j) -> bool {
+      if (tid == 0) bulk_wait_read0();
+      const bool ok = mbar_wait(full0 + 8 * (int)(j % kStages), (uint32_t)((j / kStages) & 1), globaltimer() + kWaitNs);
+      if (data_bar_or(!ok || *abort_flag)) return false;
+      const int b = (int)(j & 1);
+      split_tile(sm.stage((int)(j % kStages)), sm.big(b), sm.small(b), tid);
+      fence_async_smem();
+      data_bar();
+      if (tid == 0) {
+        if (j + kStages < T) issue_load(j + kStages);   // its stage is free again
+        mbar_arrive(opf0 + 8 * b);
+      }
+      return true;
+    };
+    uint64_t i = 0;
+    if (T > 0 && !split_and_hand(0)) fail = 1;
+    for (; !fail && i < T; i++) {
+      const int b = (int)(i & 1);
+      if (i + 1 < T && !split_and_hand(i + 1)) {
+        fail = 1;
+        break;
+      }
+      // read tile i back once its MMAs are complete, into its operand buffer, and store it
       const unsigned long long dl = globaltimer() + kWaitNs;
-      for (uint64_t j = i + (mma_pending ? 1 : 0); j < issued; j++)
-        mbar_wait(bar0 + 8 * (int)(j % kStages), (uint32_t)((j / kStages) & 1), dl);
-      if (mma_pending) mbar_wait(mma_bar, mma_phase, dl);
+      bool ok = true;
+      while (ok && !mbar_try_wait(accf0 + 8 * b, (uint32_t)((i >> 1) & 1))) ok = !*abort_flag && globaltimer() <= dl;
+      if (data_bar_or(!ok)) {
+        fail = 1;
+        break;
+      }
+      tc_fence_after();
+      float* out = (float*)sm.big(b);
+#pragma unroll 1
+      for (int c0 = 0; c0 < kRows; c0 += 32) {
+        uint32_t vm[32], vx[32];
+        tmem_ld32(tmem + lane_base + kColAcc + 128u * (uint32_t)b + c0, vm);
+        tmem_ld32(tmem + lane_base + kColAcc + 128u * (uint32_t)b + 64u + c0, vx);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 32; c++)
+          out[(c0 + c) * kRowFloats + tid] = __fadd_rn(__uint_as_float(vm[c]), __uint_as_float(vx[c]));
+      }
+      fence_async_smem();
+      tc_fence_before();
+      data_bar();
+      if (tid == 0) {
+        mbar_arrive(acce0 + 8 * b);
+        bulk_store(psi + tile_of(i) * kTileFloats, smem_u32(out), kTileBytes);
+        bulk_commit();
+      }
     }
-    bulk_wait0();
+    if (tid == 0) {
+      if (fail) {
+        *abort_flag = 1;
+        atomicExch(status, (int)QS_ETIMEOUT);
+        // loads still owed to their barriers: wait (bounded) before shared memory is released
+        const unsigned long long dl = globaltimer() + kWaitNs;
+        for (uint64_t j = (issued > (uint64_t)kStages ? issued - kStages : 0); j < issued; j++)
+          mbar_wait(full0 + 8 * (int)(j % kStages), (uint32_t)((j / kStages) & 1), dl);
+      }
+      bulk_wait0();
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -343,7 +405,7 @@ cudaError_t launch_dense_mma(void* psi, int n, const float* wT_dev, int* status,
   }
   const uint64_t ntiles = 1ull << (n - 12);   // 2^(n-6) rows of 64 amplitudes, 64 rows per tile
   const uint64_t g = ntiles < (uint64_t)num_sms ? ntiles : (uint64_t)num_sms;
-  k_dense_mma<<<(unsigned)g, kThreads, kSmemAlloc, s>>>((float*)psi, ntiles, wT_dev, status);
+  k_dense_mma<<<(unsigned)g, kBlockThreads, kSmemAlloc, s>>>((float*)psi, ntiles, wT_dev, status);
   return cudaGetLastError();
 }
 

@@ -326,6 +326,18 @@ __device__ __forceinline__ void r_rxt(typename A::reg_t (&x)[1 << K], const type
     }
   }
 }
+// several tangent-form RX on distinct slots (slot mask sm, form bits fm), one decode
+template <class A, int K>
+__device__ __forceinline__ void r_rxt_multi(typename A::reg_t (&x)[1 << K], const typename A::mat_t* m, uint32_t sm,
+                                            uint32_t fm) {
+  int idx = 0;
+  if constexpr (K > 0) if (sm & 1u) { r_rxt<A, K, 0>(x, m + idx, fm & 1u); idx++; }
+  if constexpr (K > 1) if (sm & 2u) { r_rxt<A, K, (K > 1 ? 1 : 0)>(x, m + idx, (fm >> 1) & 1u); idx++; }
+  if constexpr (K > 2) if (sm & 4u) { r_rxt<A, K, (K > 2 ? 2 : 0)>(x, m + idx, (fm >> 2) & 1u); idx++; }
+  if constexpr (K > 3) if (sm & 8u) { r_rxt<A, K, (K > 3 ? 3 : 0)>(x, m + idx, (fm >> 3) & 1u); idx++; }
+  if constexpr (K > 4) if (sm & 16u) { r_rxt<A, K, (K > 4 ? 4 : 0)>(x, m + idx, (fm >> 4) & 1u); idx++; }
+  (void)idx;
+}
 template <class A, int K, int S>
 __device__ __forceinline__ void r_x(typename A::reg_t (&x)[1 << K], const typename A::mat_t*, uint32_t csl) {
 #pragma unroll
@@ -395,6 +407,7 @@ __device__ __forceinline__ void apply_regop(typename A::reg_t (&x)[1 << K], cons
     case OP_U1: QS_SLOT_DISPATCH(r_u1, op.s0, x, m, csl); break;
     case OP_RX: QS_SLOT_DISPATCH(r_rx, op.s0, x, m, csl); break;
     case OP_RXT: QS_SLOT_DISPATCH(r_rxt, op.s0, x, m, (uint32_t)op.s1); break;
+    case OP_RXTM: r_rxt_multi<A, K>(x, m, csl, (uint32_t)(uint8_t)op.neg); break;
     case OP_X: QS_SLOT_DISPATCH(r_x, op.s0, x, m, csl); break;
     case OP_U2: {
       if constexpr (K >= 2) {
@@ -425,14 +438,15 @@ __device__ __forceinline__ void apply_regop(typename A::reg_t (&x)[1 << K], cons
     }
     case OP_DTAB: {   // csl: the entries that are not exactly 1
       if constexpr (sizeof(M) == 8 && K >= 1) {
-        // 8-byte entries: the compiler aligns every table to 16 bytes, load two at a time
+        // 8-byte entries: the compiler aligns every table to 16 bytes, load two at a time.
+        // FP32 multiplies are cheaper than testing the mask (entries outside it are exactly
+        // 1, so multiplying by them changes nothing)
         const float4* t4 = reinterpret_cast<const float4*>(m);
 #pragma unroll
         for (int j = 0; j < (1 << K); j += 2) {
-          if (!((csl >> j) & 3u)) continue;
           const float4 v = t4[j >> 1];
-          if ((csl >> j) & 1u) x[j] = A::mul(M{v.x, v.y}, x[j]);
-          if ((csl >> (j + 1)) & 1u) x[j + 1] = A::mul(M{v.z, v.w}, x[j + 1]);
+          x[j] = A::mul(M{v.x, v.y}, x[j]);
+          x[j + 1] = A::mul(M{v.z, v.w}, x[j + 1]);
         }
       } else {
 #pragma unroll

@@ -39,6 +39,8 @@ enum OpType : int32_t {
   OP_RXT = 10,   // register stages only: tangent-form RX, (I - i t X) if s1 == 0 else
                  // (t I - i X); one pool entry (t, 0).  The factor it drops is applied by
                  // a full-form OP_RX of the same pass
+  OP_RXTM = 11,  // register stages only: tangent-form RX on every register slot in csl, in
+                 // ascending slot order; pool entries (t, 0) per slot, form bits in neg
 };
 
 struct DevOp {
@@ -60,7 +62,7 @@ struct alignas(16) RegOp {
   int32_t type;       // OP_U1, OP_RX, OP_RXT, OP_X, OP_DIAG, OP_PHASE, OP_U2, OP_DTAB
   int8_t s0, s1;      // register slots of the target bit(s), -1 if none (OP_RXT: s1 = form)
   int8_t tb;          // OP_DIAG on a tile bit outside the registers, -1 if none
-  int8_t neg;         // OP_PHASE: exact sign flip
+  int8_t neg;         // OP_PHASE: exact sign flip; OP_RXTM: form bit per slot
   uint32_t csl;       // control mask over register slots
   uint32_t cot;       // control mask over tile-local bits outside the registers
   int32_t mat;        // first pool entry

@@ -251,6 +251,64 @@ void fold_pass_factors(CompileResult* out, int st0, int nst, int K) {
   }
 }
 
+// Runs of tangent-form RX on distinct register slots (they commute) become one op: one
+// decode for up to K rotations.  Rebuilds the pass's register-op range in place.
+void merge_rxt_runs(CompileResult* out, int st0, int nst) {
+  int first = -1;
+  for (int k = st0; k < st0 + nst; k++)
+    if (out->stages[k].kind == 0) {
+      first = out->stages[k].op0;
+      break;
+    }
+  if (first < 0) return;
+  std::vector<RegOp> rebuilt;
+  for (int k = st0; k < st0 + nst; k++) {
+    StageRec& st = out->stages[k];
+    if (st.kind != 0) continue;
+    const int op0 = first + (int)rebuilt.size();
+    int i = st.op0;
+    while (i < st.op0 + st.nops) {
+      const RegOp& r = out->reg_ops[i];
+      if (r.type != OP_RXT) {
+        rebuilt.push_back(r);
+        i++;
+        continue;
+      }
+      uint32_t slots = 0;
+      int e = i;
+      while (e < st.op0 + st.nops && out->reg_ops[e].type == OP_RXT && !((slots >> out->reg_ops[e].s0) & 1u)) {
+        slots |= 1u << out->reg_ops[e].s0;
+        e++;
+      }
+      if (e - i == 1) {
+        rebuilt.push_back(r);
+        i++;
+        continue;
+      }
+      RegOp m;
+      memset(&m, 0, sizeof(m));
+      m.type = OP_RXTM;
+      m.s0 = m.s1 = m.tb = -1;
+      m.gbit = -1;
+      m.csl = slots;
+      m.mat = (int)out->pool.entries();
+      for (int sl = 0; sl < 32; sl++)   // parameters in ascending slot order
+        for (int q = i; q < e; q++)
+          if (out->reg_ops[q].s0 == sl) {
+            const RegOp& t = out->reg_ops[q];
+            out->pool.add(cd(out->pool.f64[2 * (size_t)t.mat], 0.0));
+            if (t.s1) m.neg |= (int8_t)(1 << sl);
+          }
+      rebuilt.push_back(m);
+      i = e;
+    }
+    st.op0 = op0;
+    st.nops = first + (int)rebuilt.size() - op0;
+  }
+  out->reg_ops.resize(first);
+  out->reg_ops.insert(out->reg_ops.end(), rebuilt.begin(), rebuilt.end());
+}
+
 int register_bits(int dtype, int L, int requested) {
   const int kmax = (dtype == QS_C128) ? 4 : 5;
   const int k = (requested > 0) ? std::min(requested, kmax) : kmax;
@@ -484,6 +542,7 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
   }
   *nst = (int)out->stages.size() - *st0;
   fold_pass_factors(out, *st0, *nst, K);
+  merge_rxt_runs(out, *st0, *nst);
 }
 
 }  // namespace qs
@@ -538,10 +597,13 @@ double stage_alu_per_amp(const CompileResult& cr, int st0, int nst) {
       switch (r.type) {
         case OP_RX: a += pick(kRX, cr.pol) * fraction(ctl); break;
         case OP_RXT: a += pick(kRXT, cr.pol) * fraction(ctl); break;
+        case OP_RXTM: a += pick(kRXT, cr.pol) * (double)__builtin_popcount(r.csl); break;
         case OP_U1: a += pick(kU1, cr.pol) * fraction(ctl); break;
         case OP_DIAG: a += pick(kMUL, cr.pol) * fraction(ctl); break;
-        case OP_DTAB:   // only the entries that are not exactly 1 (mask in csl) are multiplied
-          a += pick(kMUL, cr.pol) * (double)__builtin_popcount(r.csl) / (double)(1u << __builtin_popcount((uint32_t)st.rmask));
+        case OP_DTAB:   // double-float / FP64 multiply only the entries that are not exactly 1
+          a += pick(kMUL, cr.pol) * (cr.pol == POL_F32 ? 1.0
+                                                        : (double)__builtin_popcount(r.csl) /
+                                                              (double)(1u << __builtin_popcount((uint32_t)st.rmask)));
           break;
         case OP_PHASE: a += (r.neg ? pick(kNEG, cr.pol) : pick(kMUL, cr.pol)) * fraction(ctl); break;
         case OP_U2: a += pick(kU2, cr.pol) * fraction(ctl); break;

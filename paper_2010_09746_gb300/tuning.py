@@ -1,8 +1,7 @@
 """Cost model fitted to measured kernel times, and an autotuner for tile width / register bits.
 
 The paper estimates a circuit's simulation time by summing benchmarked per-operation times
-(Sec. 4) and suggests that a compiler pass "may use the full information" of those
-benchmarks (Sec. 3).  Here every plan reports, per execution, its kernel launches, its
+(Sec. 4) and notes that a compiler pass could draw on those benchmarks in full (Sec. 3).  Here every plan reports, per execution, its kernel launches, its
 algorithmic HBM bytes and the arithmetic instructions its formulas need (qs_plan_stats);
 the cost model is the least-squares fit
 
