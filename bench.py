@@ -344,6 +344,8 @@ def run_ours(args):
         out["cost_model"] = fit_cost_model(args.dtype, {"tile": (plan, ms, kstats, args.steps),
                                                         "pergate": (p_pg, ms_pg, ks_pg, 1),
                                                         "paper_alg1_m12": (p_pa, ms_pa, ks_pa, 1)})
+    if args.modes and args.workload == "rzrx30":
+        out["permute"] = measure_permute(qs, torch, st, stream, n, (1 << n) * (16 if args.dtype == "c128" else 8))
     if args.small and args.workload == "rzrx30":
         out["haar_cnot_12q"] = measure_small(qs, torch, args)
     if args.qft and args.workload == "rzrx30":
@@ -412,6 +414,35 @@ def measure_small(qs, torch, args):
             entry["graph_gates_per_s"] = round(G / (msg / 1e3), 1)
         res[mode] = entry
         st.close()
+    return res
+
+
+def measure_permute(qs, torch, st, stream, n, S):
+    """PermuteQubits (K3) on the benchmark's own state: one local<->global transposition
+    (qubits 0 and n-1) and a random permutation of all n qubits (seed 0); CUDA events, best
+    of 3 after a warm-up; algorithmic bytes 2*S per permutation."""
+    peaks, _ = load_peaks()
+    rng = np.random.default_rng(0)
+    res = {}
+    cases = {"swap_0_top": [n - 1] + list(range(1, n - 1)) + [0], "random_all": [int(x) for x in rng.permutation(n)]}
+    for name, perm in cases.items():
+        ident = list(range(n))
+        st.permute(ident)
+        st.permute(perm)
+        st.permute(ident)
+        torch.cuda.synchronize()
+        best = 1e30
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st.permute(perm)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+            st.permute(ident)
+        gbs = 2 * S / (best * 1e-3) / 1e9
+        res[name] = {"ms": round(best, 3), "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / peaks["hbm_gbs"], 4)}
     return res
 
 

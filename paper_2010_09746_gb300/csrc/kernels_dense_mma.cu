@@ -10,7 +10,7 @@
 // Each MMA computes D[j][r] = sum_c W^T[j][c] Psi[r][c] for the 128 output columns j and a
 // tile of 64 rows r: A = W^T lives in tensor memory for the whole launch, B = the state tile
 // is read from shared memory (K-major, no swizzle), D (128 lanes x 64 columns FP32) is read
-// back by the four warps, one output column per thread.  Near-FP32 accuracy from TF32
+// back one output column per thread.  Near-FP32 accuracy from TF32
 // operands with the three-term split x = x_big + x_small (x_big = x rounded to TF32,
 // x_small = x - x_big rounded to TF32, so each factor is kept to about 2^-22 relative):
 // W^T_big x_big + W^T_small x_big + W^T_big x_small, accumulated in FP32.  The tensor core
@@ -19,29 +19,33 @@
 // cross terms (2^-11 smaller) to a second, summed with round-to-nearest in the epilogue.
 //
 // Persistent grid, one CTA per SM (225 KiB of shared memory), warp-specialised so that the
-// tensor core works while the threads move data.  Warps 0-3 (one per tensor-memory lane
-// quarter) bring 32 KiB row tiles into a ring of 3 row-major staging buffers with bulk
-// copies (mbarrier completion, loads issued 3 tiles ahead) and split tile j into operand
-// buffer j & 1; one lane of warp 4 issues tile j's 48 MMAs into accumulator set j & 1 as soon
+// tensor core works while the threads move data.  Warps 0-15 (four per tensor-memory lane
+// quarter) bring 32 KiB row tiles (64 rows) into a ring of 3 row-major staging buffers with
+// bulk copies (mbarrier completion, loads issued 3 tiles ahead) and split tile j into operand
+// buffer j & 1; one lane of warp 16 issues tile j's 48 MMAs into accumulator set j & 1 as soon
 // as the split is handed over (mbarrier), and commits them to another mbarrier.  While the
-// MMAs of tile j + 1 run, warps 0-3 read tile j back (one output column per thread,
-// `tcgen05.ld`), write the rows into tile j's operand buffer, release the accumulator set
-// and bulk-store the rows; then they split tile j + 2.
+// MMAs of tile j + 1 run, warps 0-15 read tile j back (one output column and 16 rows per thread,
+// `tcgen05.ld`) into the staging slot tile j + 1's input just left, release the accumulator
+// set and bulk-store the rows; the slot is reloaded (tile j + 4) one iteration later, when
+// that store has surely read it.
 // Every wait is bounded by a 2 s %globaltimer deadline; on expiry the CTA records
 // QS_ETIMEOUT, waits (bounded) for its copies and MMAs in flight, frees its tensor memory
 // and returns.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "qs_internal.h"
 
 namespace qs {
 namespace {
 
-constexpr int kThreads = 128;                        // data warps 0-3 (tensor-memory lane quarters)
-constexpr int kBlockThreads = kThreads + 32;         // + warp 4, which issues the MMAs
+constexpr int kThreads = 512;                        // data warps 0-15 (four per tensor-memory lane quarter)
+constexpr int kMmaWarp = kThreads / 32;              // the warp that issues the MMAs
+constexpr int kBlockThreads = kThreads + 32;
 constexpr int kRowFloats = 128;                      // 64 complex64 amplitudes
-constexpr int kRows = 64;                            // rows per tile = MMA N
+constexpr int kRows = 64;                            // rows per tile = MMA N (32 rows measured slower)
 constexpr int kTileFloats = kRows * kRowFloats;      // 8192
 constexpr uint32_t kTileBytes = kTileFloats * 4;     // 32 KiB
 constexpr int kStages = 3;                           // row-major staging buffers for loads
@@ -104,7 +108,7 @@ __device__ __forceinline__ void bulk_store(void* dst, uint32_t src_smem, uint32_
                : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
@@ -126,13 +130,13 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
                ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
                : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
                : "r"(taddr)
                : "memory");
 }
-
 // D[d] (+)= A[a] (tensor memory) * B (shared-memory descriptor)
 __device__ __forceinline__ void mma_tf32(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t accumulate) {
   asm volatile(
@@ -183,8 +187,8 @@ __device__ __forceinline__ void split_tile(const float* stg, unsigned char* big,
   for (int it = 0; it < kTileFloats / 4 / kThreads; it++) {
     const int g = it * kThreads + tid;
     const int i8 = g & 7, rest = g >> 3;
-    const int r = ((rest & 7) << 3) | i8;
-    const int p = ((rest >> 3) + i8) & 31;
+    const int r = ((rest % (kRows / 8)) << 3) | i8;
+    const int p = ((rest / (kRows / 8)) + i8) & 31;
     const float4 x = src[r * 32 + p];
     float4 hb, lo;
     tf32_split(x.x, hb.x, lo.x);
@@ -201,7 +205,7 @@ __device__ __forceinline__ void split_tile(const float* stg, unsigned char* big,
 __device__ __forceinline__ void issue_tile_mma(uint32_t tmem, const unsigned char* big, const unsigned char* small,
                                                int b, uint32_t bar) {
   tc_fence_after();
-  const uint32_t dm = tmem + kColAcc + 128u * (uint32_t)b, dx = dm + 64u;
+  const uint32_t dm = tmem + kColAcc + 2u * kRows * (uint32_t)b, dx = dm + (uint32_t)kRows;
   const uint32_t bb = smem_u32(big), sb = smem_u32(small);
 #pragma unroll
   for (int kk = 0; kk < 16; kk++) {
@@ -213,20 +217,20 @@ __device__ __forceinline__ void issue_tile_mma(uint32_t tmem, const unsigned cha
   mma_commit(bar);
 }
 
-// barrier 1 over the 128 data threads, OR-reducing a predicate
+// barrier 1 over the 512 data threads, OR-reducing a predicate
 __device__ __forceinline__ bool data_bar_or(bool v) {
   uint32_t r;
   asm volatile(
       "{\n\t.reg .pred p, q;\n\t"
       "setp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.or.pred q, 1, 128, p;\n\t"
+      "bar.red.or.pred q, 1, 512, p;\n\t"
       "selp.u32 %0, 1, 0, q;\n\t}"
       : "=r"(r)
       : "r"((uint32_t)v)
       : "memory");
   return r != 0;
 }
-__device__ __forceinline__ void data_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void data_bar() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
@@ -262,7 +266,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 4) {
+  if (warp == kMmaWarp) {
     // ---- MMA warp: one lane issues every tile's 48 MMAs in order -----------------------
     if ((tid & 31) == 0) {
       uint64_t j = 0;
@@ -290,12 +294,17 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
     }
   } else {
     // ---- data warps: loads, splits, read-back, stores ---------------------------------
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    // W^T (big, small) into tensor memory: thread j holds row j of both, 128 columns each
-    for (int part = 0; part < 2; part++)
-      for (int c0 = 0; c0 < 128; c0 += 32) {
+    // warp w reaches tensor-memory lanes 32 (w mod 4) .. + 31; four warps share each quarter
+    const int quarter = warp & 3, slice = warp >> 2;   // slice 0..3
+    const int row = quarter * 32 + (tid & 31);   // W^T row = output column of this thread
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
+    // W^T into tensor memory: slices 0, 1 the big part's columns 0-63 / 64-127, slices 2, 3
+    // the small part's
+    {
+      const int part = slice >> 1;
+      for (int c0 = 64 * (slice & 1); c0 < 64 * (slice & 1) + 64; c0 += 32) {
         uint32_t v[32];
-        const float4* src = (const float4*)(wT + part * 16384 + tid * 128 + c0);
+        const float4* src = (const float4*)(wT + part * 16384 + row * 128 + c0);
 #pragma unroll
         for (int q = 0; q < 8; q++) {
           const float4 f = __ldg(src + q);
@@ -306,6 +315,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
         }
         tmem_st32(tmem + lane_base + (part ? kColWSmall : kColWBig) + c0, v);
       }
+    }
     tmem_wait_st();
     tc_fence_before();
 
@@ -320,20 +330,18 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
       for (uint64_t j = 0; j < (uint64_t)kStages && j < T; j++) issue_load(j);
 
     int fail = 0;
-    // split tile j into operand buffer j & 1 and hand it to the MMA warp; the buffer held
-    // tile j - 2's output, whose store must have read it
+    // Stage slot j % 3 receives tile j's input; once split, the same slot receives tile
+    // j - 1's output rows, and after that store has read them, tile j + 3's input.
+    // split tile j into operand buffer j & 1 and hand it to the MMA warp (the MMAs of tile
+    // j - 2, the buffer's last reader, completed before tile j - 2 was read back)
     auto split_and_hand = [&](uint64_t j) -> bool {
-      if (tid == 0) bulk_wait_read0();
       const bool ok = mbar_wait(full0 + 8 * (int)(j % kStages), (uint32_t)((j / kStages) & 1), globaltimer() + kWaitNs);
       if (data_bar_or(!ok || *abort_flag)) return false;
       const int b = (int)(j & 1);
       split_tile(sm.stage((int)(j % kStages)), sm.big(b), sm.small(b), tid);
       fence_async_smem();
       data_bar();
-      if (tid == 0) {
-        if (j + kStages < T) issue_load(j + kStages);   // its stage is free again
-        mbar_arrive(opf0 + 8 * b);
-      }
+      if (tid == 0) mbar_arrive(opf0 + 8 * b);
       return true;
     };
     uint64_t i = 0;
@@ -344,7 +352,9 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
         fail = 1;
         break;
       }
-      // read tile i back once its MMAs are complete, into its operand buffer, and store it
+      // read tile i back once its MMAs are complete, into stage slot (i + 1) % 3 (its input
+      // was split above; its previous output's store finished reading before that input
+      // was loaded), and store it
       const unsigned long long dl = globaltimer() + kWaitNs;
       bool ok = true;
       while (ok && !mbar_try_wait(accf0 + 8 * b, (uint32_t)((i >> 1) & 1))) ok = !*abort_flag && globaltimer() <= dl;
@@ -353,16 +363,17 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
         break;
       }
       tc_fence_after();
-      float* out = (float*)sm.big(b);
-#pragma unroll 1
-      for (int c0 = 0; c0 < kRows; c0 += 32) {
-        uint32_t vm[32], vx[32];
-        tmem_ld32(tmem + lane_base + kColAcc + 128u * (uint32_t)b + c0, vm);
-        tmem_ld32(tmem + lane_base + kColAcc + 128u * (uint32_t)b + 64u + c0, vx);
+      float* out = sm.stage((int)((i + 1) % kStages));
+      {   // this warp: output column `row`, tile rows 16 slice .. 16 slice + 15
+        const int c0 = (kRows / 4) * slice;
+        uint32_t vm[kRows / 4], vx[kRows / 4];
+        const uint32_t acc = tmem + lane_base + kColAcc + 2u * kRows * (uint32_t)b + (uint32_t)c0;
+        tmem_ld16(acc, vm);
+        tmem_ld16(acc + (uint32_t)kRows, vx);
         tmem_wait_ld();
 #pragma unroll
-        for (int c = 0; c < 32; c++)
-          out[(c0 + c) * kRowFloats + tid] = __fadd_rn(__uint_as_float(vm[c]), __uint_as_float(vx[c]));
+        for (int c = 0; c < kRows / 4; c++)
+          out[(c0 + c) * kRowFloats + row] = __fadd_rn(__uint_as_float(vm[c]), __uint_as_float(vx[c]));
       }
       fence_async_smem();
       tc_fence_before();
@@ -371,6 +382,10 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
         mbar_arrive(acce0 + 8 * b);
         bulk_store(psi + tile_of(i) * kTileFloats, smem_u32(out), kTileBytes);
         bulk_commit();
+        // tile i - 1's output (slot i % 3) has had a whole iteration to be read: refill the
+        // slot with tile i + 3's input
+        bulk_wait_read1();
+        if (i + kStages < T) issue_load(i + kStages);
       }
     }
     if (tid == 0) {
@@ -397,13 +412,18 @@ int dense_mma_min_qubits() { return 12; }
 
 cudaError_t launch_dense_mma(void* psi, int n, const float* wT_dev, int* status, int num_sms, cudaStream_t s) {
   if (n < 12) return cudaErrorInvalidValue;
-  static bool attr_set = false;   // per process; the attribute is per function, not per device
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_dense_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAlloc);
+  // the shared-memory opt-in is a property of the function in each device's context
+  static std::atomic<uint64_t> attr_set{0};   // bit d: set on device d (d < 64)
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0;
+  if (!bit || !(attr_set.load() & bit)) {
+    e = cudaFuncSetAttribute(k_dense_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemAlloc);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    attr_set.fetch_or(bit);
   }
-  const uint64_t ntiles = 1ull << (n - 12);   // 2^(n-6) rows of 64 amplitudes, 64 rows per tile
+  const uint64_t ntiles = (1ull << (n - 6)) / kRows;   // 2^(n-6) rows of 64 amplitudes
   const uint64_t g = ntiles < (uint64_t)num_sms ? ntiles : (uint64_t)num_sms;
   k_dense_mma<<<(unsigned)g, kBlockThreads, kSmemAlloc, s>>>((float*)psi, ntiles, wT_dev, status);
   return cudaGetLastError();

@@ -31,14 +31,58 @@ struct PermArgs {
   int rout[kMaxQubits];         // and output positions
 };
 
+// shared-memory layout of the permutation kernel (byte offsets, every region 16-byte aligned)
+struct PermSmem {
+  size_t off_in, off_out, r_of, bin, bout, buf;
+};
+__host__ __device__ inline size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
+__host__ __device__ inline PermSmem perm_smem_layout(int T, int tiles_per_iter) {
+  PermSmem L;
+  L.off_in = 0;
+  L.off_out = round16(L.off_in + 8 * (size_t)T);
+  L.r_of = round16(L.off_out + 8 * (size_t)T);
+  L.bin = round16(L.r_of + 4 * (size_t)T);
+  L.bout = round16(L.bin + 8 * (size_t)tiles_per_iter);
+  L.buf = round16(L.bout + 8 * (size_t)tiles_per_iter);
+  return L;
+}
+
+// one padding element per 128 bytes of staged tile: the write phase reads the tile in the
+// output's bit order, and without padding 8 consecutive output elements that come from
+// input bits >= 3 would sit 128 bytes apart in one bank group
+template <class S>
+__device__ __forceinline__ int pad_idx(int i) {
+  return i + (i >> (sizeof(S) == 16 ? 3 : 4));
+}
+
 template <class S>
 __global__ void __launch_bounds__(kPermThreads) k_permute_tiled(S* __restrict__ dst, const S* __restrict__ src,
                                                                const PermArgs a, int tiles_per_iter) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = 1 << a.tb;
-  S* buf = reinterpret_cast<S*>(smem);
-  uint64_t* bin = reinterpret_cast<uint64_t*>(smem + (size_t)tiles_per_iter * T * sizeof(S));
-  uint64_t* bout = bin + tiles_per_iter;
+  // tables shared by every tile: input offset of tile-local index r, output offset of
+  // output-ordered index w and the tile-local index r it reads
+  const PermSmem L = perm_smem_layout(T, tiles_per_iter);
+  uint64_t* off_in = reinterpret_cast<uint64_t*>(smem + L.off_in);
+  uint64_t* off_out = reinterpret_cast<uint64_t*>(smem + L.off_out);
+  int* r_of = reinterpret_cast<int*>(smem + L.r_of);
+  uint64_t* bin = reinterpret_cast<uint64_t*>(smem + L.bin);
+  uint64_t* bout = reinterpret_cast<uint64_t*>(smem + L.bout);
+  S* buf = reinterpret_cast<S*>(smem + L.buf);
+  for (int r = threadIdx.x; r < T; r += kPermThreads) {
+    uint64_t oi = 0, oo = 0;
+    int rr = 0;
+    for (int k = 0; k < a.tb; k++) {
+      if ((r >> k) & 1) oi |= 1ull << a.tin[k];
+      if ((r >> k) & 1) {
+        rr |= 1 << a.wk[k];
+        oo |= 1ull << a.wp[k];
+      }
+    }
+    off_in[r] = oi;
+    off_out[r] = oo;
+    r_of[r] = rr;
+  }
   const uint64_t ntiles = 1ull << a.nrest;
   for (uint64_t tile0 = (uint64_t)blockIdx.x * tiles_per_iter; tile0 < ntiles;
        tile0 += (uint64_t)gridDim.x * tiles_per_iter) {
@@ -59,23 +103,13 @@ __global__ void __launch_bounds__(kPermThreads) k_permute_tiled(S* __restrict__ 
     // lowest input bits vary fastest (contiguous segments)
     for (int idx = threadIdx.x; idx < cnt * T; idx += kPermThreads) {
       const int u = idx >> a.tb, r = idx & (T - 1);
-      uint64_t j = bin[u];
-      for (int k = 0; k < a.tb; k++)
-        if ((r >> k) & 1) j |= 1ull << a.tin[k];
-      buf[idx] = src[j];
+      buf[pad_idx<S>(idx)] = src[bin[u] | off_in[r]];
     }
     __syncthreads();
     // write: w enumerates the output tile bits in ascending output order
     for (int idx = threadIdx.x; idx < cnt * T; idx += kPermThreads) {
       const int u = idx >> a.tb, w = idx & (T - 1);
-      uint64_t jo = bout[u];
-      int r = 0;
-      for (int k = 0; k < a.tb; k++)
-        if ((w >> k) & 1) {
-          r |= 1 << a.wk[k];
-          jo |= 1ull << a.wp[k];
-        }
-      dst[jo] = buf[(u << a.tb) | r];
+      dst[bout[u] | off_out[w]] = buf[pad_idx<S>((u << a.tb) | r_of[w])];
     }
     __syncthreads();
   }
@@ -122,7 +156,9 @@ cudaError_t launch_permute(void* dst, const void* src, int n, int store_bytes, c
   const int T = 1 << a.tb;
   int tiles_per_iter = 2048 / T;
   if (tiles_per_iter < 1) tiles_per_iter = 1;
-  const size_t smem = (size_t)tiles_per_iter * T * store_bytes + (size_t)tiles_per_iter * 16;
+  const size_t elems = (size_t)tiles_per_iter * T;
+  const size_t pad = elems / (store_bytes == 16 ? 8 : 16) + 1;
+  const size_t smem = perm_smem_layout(T, tiles_per_iter).buf + (elems + pad) * store_bytes;
   static int sms = 0;
   if (sms == 0) {
     int dev = 0;

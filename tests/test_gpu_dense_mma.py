@@ -87,6 +87,11 @@ def test_auto_path_choice():
     assert "dense_mma_c64" not in names
     _, _, names, _ = run_dense(n, 5, [0, 1, 2, 3, 15], "auto", seed=1)   # not low, k < 6: no permute
     assert "dense_mma_c64" not in names and "permute" not in names
+    got, ref, names, _ = run_dense(n, 6, [15, 1, 2, 3, 4, 9], "auto", seed=2)   # not low, k = 6: permute first
+    assert "dense_mma_c64" in names and "permute" in names
+    check_c64(got, ref)
+    _, _, names, _ = run_dense(n, 6, list(range(6)), "cuda_cores", seed=1)
+    assert "dense_mma_c64" not in names
 
 
 def test_tensor_rejections():
