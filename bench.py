@@ -291,11 +291,12 @@ def run_ours(args):
         "metric": "30q random-circuit gates/s & % HBM roofline",
         "value": round(value, 2), "unit": "gates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": policy, "data": "synthetic (seeded random circuit)",
+        "dtype": {"df": "f32x2", "f32": "f32", "f64": "f64"}[policy], "data": "synthetic (seeded random circuit)",
         "config": {"workload": name, "seeds": list(range(args.seed, args.seed + len(circs))),
                    "passes_per_seed": [p.stats()["n_passes"] for p in plans],
                    "n_qubits": n, "gates": G, "mode": args.mode, "state_dtype": args.dtype,
-                   "arith": policy, "tile_bits": args.tile_bits or None, "low_bits": args.low_bits or None,
+                   "arith": {"df": "double-float (pairs of f32), f64 storage", "f32": "f32", "f64": "f64"}[policy],
+                   "tile_bits": args.tile_bits or None, "low_bits": args.low_bits or None,
                    "reg_bits": args.reg_bits or None,
                    "passes": pstats["n_passes"], "permutes": pstats["n_permutes"], "pergate": pstats["n_pergate"],
                    "parallelism": f"replicas{world}",

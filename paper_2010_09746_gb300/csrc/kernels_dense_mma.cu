@@ -25,9 +25,9 @@
 // buffer j & 1; one lane of warp 16 issues tile j's 48 MMAs into accumulator set j & 1 as soon
 // as the split is handed over (mbarrier), and commits them to another mbarrier.  While the
 // MMAs of tile j + 1 run, warps 0-15 read tile j back (one output column and 16 rows per thread,
-// `tcgen05.ld`) into the staging slot tile j + 1's input just left, release the accumulator
-// set and bulk-store the rows; the slot is reloaded (tile j + 4) one iteration later, when
-// that store has surely read it.
+// `tcgen05.ld`), store the rows to HBM straight from the registers (each warp store
+// instruction writes one full 128-byte line) and release the accumulator set.  A staging
+// slot is refilled as soon as its tile is split.
 // Every wait is bounded by a 2 s %globaltimer deadline; on expiry the CTA records
 // QS_ETIMEOUT, waits (bounded) for its copies and MMAs in flight, frees its tensor memory
 // and returns.
@@ -103,13 +103,6 @@ __device__ __forceinline__ void bulk_load(uint32_t dst_smem, const void* src, ui
       "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
-__device__ __forceinline__ void bulk_store(void* dst, uint32_t src_smem, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src_smem), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // ---- tensor memory and MMA ---------------------------------------------------------------
@@ -156,12 +149,11 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
          (1ull << 46);
 }
 
-// round to the nearest TF32 value (10 significand bits), ties away from zero; the result
-// has its low 13 bits clear, so the tensor core reads it exactly
+// round to the nearest TF32 value (10 significand bits), ties away from zero in magnitude,
+// with two integer operations on the binary32 fields (finite inputs of magnitude below
+// 2^127); the result has its low 13 bits clear, so the tensor core reads it exactly
 __device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 __device__ __forceinline__ void tf32_split(float x, float& big, float& small) {
   big = tf32_rna(x);
@@ -330,10 +322,9 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
       for (uint64_t j = 0; j < (uint64_t)kStages && j < T; j++) issue_load(j);
 
     int fail = 0;
-    // Stage slot j % 3 receives tile j's input; once split, the same slot receives tile
-    // j - 1's output rows, and after that store has read them, tile j + 3's input.
     // split tile j into operand buffer j & 1 and hand it to the MMA warp (the MMAs of tile
-    // j - 2, the buffer's last reader, completed before tile j - 2 was read back)
+    // j - 2, the buffer's last reader, completed before tile j - 2 was read back); its stage
+    // slot is refilled at once with tile j + kStages's input
     auto split_and_hand = [&](uint64_t j) -> bool {
       const bool ok = mbar_wait(full0 + 8 * (int)(j % kStages), (uint32_t)((j / kStages) & 1), globaltimer() + kWaitNs);
       if (data_bar_or(!ok || *abort_flag)) return false;
@@ -341,7 +332,10 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
       split_tile(sm.stage((int)(j % kStages)), sm.big(b), sm.small(b), tid);
       fence_async_smem();
       data_bar();
-      if (tid == 0) mbar_arrive(opf0 + 8 * b);
+      if (tid == 0) {
+        mbar_arrive(opf0 + 8 * b);
+        if (j + kStages < T) issue_load(j + kStages);
+      }
       return true;
     };
     uint64_t i = 0;
@@ -352,9 +346,9 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
         fail = 1;
         break;
       }
-      // read tile i back once its MMAs are complete, into stage slot (i + 1) % 3 (its input
-      // was split above; its previous output's store finished reading before that input
-      // was loaded), and store it
+      // read tile i back once its MMAs are complete and write it to HBM straight from the
+      // registers: for each row, the 32 lanes of a warp hold 32 consecutive output floats,
+      // so every store instruction writes one full 128-byte line
       const unsigned long long dl = globaltimer() + kWaitNs;
       bool ok = true;
       while (ok && !mbar_try_wait(accf0 + 8 * b, (uint32_t)((i >> 1) & 1))) ok = !*abort_flag && globaltimer() <= dl;
@@ -363,7 +357,7 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
         break;
       }
       tc_fence_after();
-      float* out = sm.stage((int)((i + 1) % kStages));
+      float* out = psi + tile_of(i) * kTileFloats;
       {   // this warp: output column `row`, tile rows 16 slice .. 16 slice + 15
         const int c0 = (kRows / 4) * slice;
         uint32_t vm[kRows / 4], vx[kRows / 4];
@@ -375,18 +369,9 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
         for (int c = 0; c < kRows / 4; c++)
           out[(c0 + c) * kRowFloats + row] = __fadd_rn(__uint_as_float(vm[c]), __uint_as_float(vx[c]));
       }
-      fence_async_smem();
       tc_fence_before();
       data_bar();
-      if (tid == 0) {
-        mbar_arrive(acce0 + 8 * b);
-        bulk_store(psi + tile_of(i) * kTileFloats, smem_u32(out), kTileBytes);
-        bulk_commit();
-        // tile i - 1's output (slot i % 3) has had a whole iteration to be read: refill the
-        // slot with tile i + 3's input
-        bulk_wait_read1();
-        if (i + kStages < T) issue_load(i + kStages);
-      }
+      if (tid == 0) mbar_arrive(acce0 + 8 * b);
     }
     if (tid == 0) {
       if (fail) {
@@ -397,7 +382,6 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
         for (uint64_t j = (issued > (uint64_t)kStages ? issued - kStages : 0); j < issued; j++)
           mbar_wait(full0 + 8 * (int)(j % kStages), (uint32_t)((j / kStages) & 1), dl);
       }
-      bulk_wait0();
     }
   }
   tc_fence_before();

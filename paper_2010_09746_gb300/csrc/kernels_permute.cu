@@ -19,6 +19,10 @@ namespace qs {
 namespace {
 
 constexpr int kPermThreads = 256;
+// elements staged per CTA and iteration, and resident CTAs per SM: 8 CTAs of ~20 KiB keep
+// about 128 KiB of reads in flight per SM
+constexpr int kPermElems = 1024;
+constexpr int kPermCtasPerSm = 8;
 
 struct PermArgs {
   int n;
@@ -154,7 +158,7 @@ cudaError_t launch_permute(void* dst, const void* src, int n, int store_bytes, c
         rank++;
       }
   const int T = 1 << a.tb;
-  int tiles_per_iter = 2048 / T;
+  int tiles_per_iter = kPermElems / T;
   if (tiles_per_iter < 1) tiles_per_iter = 1;
   const size_t elems = (size_t)tiles_per_iter * T;
   const size_t pad = elems / (store_bytes == 16 ? 8 : 16) + 1;
@@ -167,7 +171,7 @@ cudaError_t launch_permute(void* dst, const void* src, int n, int store_bytes, c
   }
   const uint64_t ntiles = 1ull << a.nrest;
   uint64_t grid = (ntiles + tiles_per_iter - 1) / tiles_per_iter;
-  const uint64_t cap = (uint64_t)sms * 4;
+  const uint64_t cap = (uint64_t)sms * kPermCtasPerSm;
   if (grid > cap) grid = cap;
   if (store_bytes == 16) {
     cudaFuncSetAttribute(k_permute_tiled<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
