@@ -221,6 +221,16 @@ def measure(qs, st, plan, steps, warmup, torch, stream, profile=False):
     return e0.elapsed_time(e1) / steps, norms, ks
 
 
+def per_gate_bound(qs, n, circ, args, peaks, gates_per_s):
+    """What a simulator that moves the state through HBM once per gate could reach at best:
+    the per-gate plan's algorithmic bytes (2 S per gate, less for controlled and diagonal
+    two-qubit gates) at the measured copy bandwidth; `ratio` = this path's gates/s over it."""
+    p = qs.compile(n, circ, mode="pergate", dtype=args.dtype, arith=args.arith)
+    b = p.stats()["hbm_bytes"]
+    ideal = len(circ) / (b / (peaks["hbm_gbs"] * 1e9))
+    return {"bytes_per_circuit": b, "ideal_gates_per_s": round(ideal, 2), "ratio": round(gates_per_s / ideal, 3)}
+
+
 def fit_cost_model(dtype, runs):
     """Per kernel class, least squares t = c_launch*launches + c_byte*bytes + c_alu*instructions
     over the CUDA-event totals of these runs (one sample per class and run); then each
@@ -302,6 +312,7 @@ def run_ours(args):
                    "parallelism": f"replicas{world}",
                    "l2": "state 16 GiB >> 129 MB L2, no flush needed" if n >= 27 else "state small vs L2"},
         "hbm_frac_step": round(total_bytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+        "per_gate_hbm_bound": per_gate_bound(qs, n, circ, args, peaks, value / world),
         "norm_max_dev": max(abs(x - 1.0) for x in norms),
         "compile_ms": round(pstats["compile_ms"], 2),
         "roofline": roof, "gpu_launches": launches, "kernels": kstats, "clocks": clk,

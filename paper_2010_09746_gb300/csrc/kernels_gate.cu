@@ -38,13 +38,10 @@ __device__ __forceinline__ uint64_t expand(uint64_t t, const Expand& e) {
 }
 
 int grid_for(uint64_t work) {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-  }
+  int sms = 0, dev = 0;   // the current device's SM count (the runtime answers from a cache)
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms <= 0)
+    sms = 152;
   uint64_t blocks = (work + kThreads - 1) / kThreads;
   uint64_t cap = (uint64_t)sms * 8;
   if (blocks > cap) blocks = cap;

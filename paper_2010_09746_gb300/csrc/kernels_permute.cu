@@ -163,12 +163,10 @@ cudaError_t launch_permute(void* dst, const void* src, int n, int store_bytes, c
   const size_t elems = (size_t)tiles_per_iter * T;
   const size_t pad = elems / (store_bytes == 16 ? 8 : 16) + 1;
   const size_t smem = perm_smem_layout(T, tiles_per_iter).buf + (elems + pad) * store_bytes;
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
+  int sms = 0, dev = 0;   // per device: the SM count of the current one
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
   const uint64_t ntiles = 1ull << a.nrest;
   uint64_t grid = (ntiles + tiles_per_iter - 1) / tiles_per_iter;
   const uint64_t cap = (uint64_t)sms * kPermCtasPerSm;

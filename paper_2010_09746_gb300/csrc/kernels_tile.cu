@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <type_traits>
 
 #include "arith.cuh"
@@ -687,25 +688,33 @@ __global__ void __launch_bounds__(kTileThreads, 2)
   bulk_wait0();
 }
 
+// The shared-memory opt-in and the SM count belong to each device's context: one bit per
+// device records that the attribute is set, the SM count is read on every launch (cheap).
+template <class F>
+cudaError_t tile_kernel_setup(F* kernel, std::atomic<uint64_t>& configured, int* sms) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0;
+  if (!bit || !(configured.load() & bit)) {
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return e;
+    configured.fetch_or(bit);
+  }
+  return cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+}
+
 template <class A, int K>
 cudaError_t launch_staged(void* psi, const TilePass& tp, const StageRec* stages, const RegOp* rops,
                           const DevOp* dops, const void* pool, int* status, cudaStream_t st) {
   using S = typename A::store_t;
   const size_t smem = kTileSmemOffset + ((size_t)1 << (tp.L - tp.c)) * (((size_t)sizeof(S) << tp.c) + 16);
-  static bool configured = false;
-  static int sms = 0;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_tile_staged<A, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
+  static std::atomic<uint64_t> configured{0};
+  int sms = 0;
+  cudaError_t e = tile_kernel_setup(k_tile_staged<A, K>, configured, &sms);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_staged<A, K>, kTileThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_staged<A, K>, kTileThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const uint64_t nblocks = 1ull << (tp.n - tp.L);
@@ -722,20 +731,12 @@ cudaError_t launch_batched_t(void* psi, const BatchPass* passes, const uint64_t*
                              const void* pool, int* status, cudaStream_t st) {
   using S = typename A::store_t;
   const size_t smem = kTileSmemOffset + ((size_t)1 << (maxL - minc)) * (((size_t)sizeof(S) << minc) + 16);
-  static bool configured = false;
-  static int sms = 0;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_tile_batched<A, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  if (sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  }
+  static std::atomic<uint64_t> configured{0};
+  int sms = 0;
+  cudaError_t e = tile_kernel_setup(k_tile_batched<A, K>, configured, &sms);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_batched<A, K>, kTileThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_batched<A, K>, kTileThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   uint64_t grid = (uint64_t)sms * per_sm;
