@@ -395,6 +395,28 @@ __device__ __forceinline__ void r_u2_s1(typename A::reg_t (&x)[1 << K], int s1, 
   if constexpr (K > 4 && S0 != 4) if (s1 == 4) { r_u2<A, K, S0, (K > 4 ? 4 : 0)>(x, m, csl); return; }
 }
 
+// multiply register element j by table entry j where bit j of csl is set (the others are 1)
+template <class A, int K>
+__device__ __forceinline__ void r_dtab(typename A::reg_t (&x)[1 << K], const typename A::mat_t* m, uint32_t csl) {
+  using M = typename A::mat_t;
+  if constexpr (sizeof(M) == 8 && K >= 1) {
+    // 8-byte entries: the compiler aligns every table to 16 bytes, load two at a time.
+    // FP32 multiplies are cheaper than testing the mask (entries outside it are exactly
+    // 1, so multiplying by them changes nothing)
+    const float4* t4 = reinterpret_cast<const float4*>(m);
+#pragma unroll
+    for (int j = 0; j < (1 << K); j += 2) {
+      const float4 v = t4[j >> 1];
+      x[j] = A::mul(M{v.x, v.y}, x[j]);
+      x[j + 1] = A::mul(M{v.z, v.w}, x[j + 1]);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < (1 << K); j++)
+      if ((csl >> j) & 1u) x[j] = A::mul(m[j], x[j]);
+  }
+}
+
 template <class A, int K>
 __device__ __forceinline__ void apply_regop(typename A::reg_t (&x)[1 << K], const RegOp& op,
                                             const typename A::mat_t* __restrict__ pool, uint32_t gidx,
@@ -437,25 +459,7 @@ __device__ __forceinline__ void apply_regop(typename A::reg_t (&x)[1 << K], cons
       }
       break;
     }
-    case OP_DTAB: {   // csl: the entries that are not exactly 1
-      if constexpr (sizeof(M) == 8 && K >= 1) {
-        // 8-byte entries: the compiler aligns every table to 16 bytes, load two at a time.
-        // FP32 multiplies are cheaper than testing the mask (entries outside it are exactly
-        // 1, so multiplying by them changes nothing)
-        const float4* t4 = reinterpret_cast<const float4*>(m);
-#pragma unroll
-        for (int j = 0; j < (1 << K); j += 2) {
-          const float4 v = t4[j >> 1];
-          x[j] = A::mul(M{v.x, v.y}, x[j]);
-          x[j + 1] = A::mul(M{v.z, v.w}, x[j + 1]);
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < (1 << K); j++)
-          if ((csl >> j) & 1u) x[j] = A::mul(m[j], x[j]);
-      }
-      break;
-    }
+    case OP_DTAB: r_dtab<A, K>(x, m, csl); break;
     case OP_PHASE: {
       if (op.neg) {
 #pragma unroll
@@ -524,7 +528,15 @@ __device__ __forceinline__ void run_reg_stage(typename A::reg_t* T, const StageR
     for (int k = 0; k < sr.nops; k++) {
       const RegOp op = load_regop(rops + sr.op0 + k);
       if ((base & op.gmask) != op.gmask) continue;
-      apply_regop<A, K>(x, op, pool, gidx, base);
+      // the two most frequent ops (merged tangent-form RX runs and phase tables) skip the
+      // general dispatch; neither carries controls outside the registers
+      if (op.type == OP_RXTM) {
+        r_rxt_multi<A, K>(x, pool + op.mat, op.csl, (uint32_t)(uint8_t)op.neg);
+      } else if (op.type == OP_DTAB) {
+        r_dtab<A, K>(x, pool + op.mat, op.csl);
+      } else {
+        apply_regop<A, K>(x, op, pool, gidx, base);
+      }
     }
     // recompute the store addresses from a value the compiler cannot equate with the load
     // addresses, so that 2^K addresses are not kept live across the op loop
