@@ -7,7 +7,8 @@ state preparation and the plan on the slot's own CUDA stream, so
 work of different requests overlaps on the device.  Small requests (n <= batch_small_n)
 waiting together with others of the same dtype share one slot: they are compiled into one
 batch (qs_batch_*), whose tile passes run as persistent launches over all of their states.
-Completion is detected with CUDA events; the result (the FP64 norm and the first
+Admission order is first-come or shortest-estimated-work first (with a maximum wait that
+lets long-waiting requests go first).  Completion is detected with CUDA events; the result (the FP64 norm and the first
 amplitudes) is read out, the state is released and the next request takes the slot.  Every
 request runs the same per-tile code on its own state whatever else is in flight (a batched
 circuit's amplitudes are bitwise those of its solo run), so its result does not depend on
@@ -64,7 +65,7 @@ class Server:
     readout: amplitudes copied back per request (first min(2^n, readout))."""
 
     def __init__(self, slots: int = 8, mem_budget: int = 64 << 30, readout: int = 256, tile_bits: int = 0,
-                 batch_small_n: int = 16, batch_max: int = 64):
+                 batch_small_n: int = 16, batch_max: int = 64, order: str = "fifo", max_wait_s: float = 1.0):
         import torch
 
         self.torch = torch
@@ -75,6 +76,10 @@ class Server:
         self.tile_bits = tile_bits
         self.batch_small_n = batch_small_n
         self.batch_max = batch_max
+        if order not in ("fifo", "sjf"):
+            raise ValueError("order must be 'fifo' or 'sjf'")
+        self.order = order            # sjf: least estimated work first, unless a request waited max_wait_s
+        self.max_wait_s = max_wait_s
         self.batched_requests = 0
         self.batches = 0
         self.waiting: deque = deque()
@@ -92,9 +97,28 @@ class Server:
             raise ValueError(f"request {rid} needs more device memory than the whole budget")
         self.waiting.append((rid, req, arrival_s))
 
+    @staticmethod
+    def work_estimate(req) -> float:
+        """Relative device work: gates x amplitudes, complex128 (double-float) ~8x complex64."""
+        return len(req.circuit) * float(1 << req.n) * (8.0 if req.dtype == "c128" else 1.0)
+
+    def _next(self, now_s: float) -> int:
+        """Index in `waiting` of the request to admit next."""
+        if self.order == "fifo" or len(self.waiting) == 1:
+            return 0
+        if now_s - self.waiting[0][2] >= self.max_wait_s:   # the oldest has waited long enough
+            return 0
+        return min(range(len(self.waiting)), key=lambda k: self.work_estimate(self.waiting[k][1]))
+
     def _admit(self, now_s: float) -> int:
         admitted = 0
         while self.waiting:
+            k = self._next(now_s)
+            if k:
+                self.waiting.rotate(-k)   # bring it to the front; the others keep their order after it
+                item = self.waiting.popleft()
+                self.waiting.rotate(k)
+                self.waiting.appendleft(item)
             rid, req, arr = self.waiting[0]
             need = self.state_bytes(req.n, req.dtype)
             free = [i for i, s in enumerate(self.slots) if not s.busy]

@@ -59,3 +59,12 @@ def test_oversized_request_rejected():
     r = wc.Request(0.0, 20, "c128", [])
     with pytest.raises(ValueError):
         srv.submit(0, r, 0.0)
+
+
+def test_sjf_order_same_results():
+    """Shortest-work-first admission changes when requests run, not what they compute."""
+    reqs = make_requests(16, seed=7)
+    a = serve.Server(slots=2, readout=1 << 15, order="fifo").run(reqs, realtime=False)
+    b = serve.Server(slots=2, readout=1 << 15, order="sjf").run(reqs, realtime=False)
+    for rid in range(len(reqs)):
+        assert a[rid].amplitudes.tobytes() == b[rid].amplitudes.tobytes()
