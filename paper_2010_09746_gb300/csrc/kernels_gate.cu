@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "arith.cuh"
 #include "qs_internal.h"
 
@@ -125,6 +127,71 @@ __global__ void __launch_bounds__(kThreads) k_exchange(S* __restrict__ psi, uint
   }
 }
 
+// complex64 with 16-byte accesses: every load and store moves two adjacent amplitudes (a
+// float4).  Work item t expands to an index i0 with bit 0 clear.  A 2x2 (or RX) on bit 0
+// finds its pair inside one word; on a bit p >= 1 the words at i0 and i0 + 2^p hold two
+// pairs.  Controls never include bit 0 here (the launcher falls back otherwise).
+template <bool kRX>
+__global__ void __launch_bounds__(kThreads) k_pair_c64x2(float2* __restrict__ psi, uint64_t nwork, Expand e, int p,
+                                                          const float2* __restrict__ m) {
+  using A = AF32;
+  const float2 u00 = m[0], u01 = kRX ? m[0] : m[1], u10 = kRX ? m[0] : m[2], u11 = kRX ? m[0] : m[3];
+  float4* psi4 = reinterpret_cast<float4*>(psi);
+  const uint64_t s = 1ull << p;
+  auto upd = [&](float2 a, float2 b, float2& ra, float2& rb) {
+    if (kRX) {
+      ra = A::rx(u00, a, b);
+      rb = A::rx(u00, b, a);
+    } else {
+      ra = A::mac2(u00, a, u01, b);
+      rb = A::mac2(u10, a, u11, b);
+    }
+  };
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nwork; t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i0 = expand(t, e);
+    float2 r0, r1;
+    if (p == 0) {
+      const float4 v = psi4[i0 >> 1];
+      upd(make_float2(v.x, v.y), make_float2(v.z, v.w), r0, r1);
+      psi4[i0 >> 1] = make_float4(r0.x, r0.y, r1.x, r1.y);
+    } else {
+      const float4 va = psi4[i0 >> 1], vb = psi4[(i0 | s) >> 1];
+      float2 r2, r3;
+      upd(make_float2(va.x, va.y), make_float2(vb.x, vb.y), r0, r1);
+      upd(make_float2(va.z, va.w), make_float2(vb.z, vb.w), r2, r3);
+      psi4[i0 >> 1] = make_float4(r0.x, r0.y, r2.x, r2.y);
+      psi4[(i0 | s) >> 1] = make_float4(r1.x, r1.y, r3.x, r3.y);
+    }
+  }
+}
+
+// complex64 diagonal factors on two adjacent amplitudes per 16-byte word (bit 0 not a
+// control): kind 0 = diag(d0, d1) on bit p, 1 = multiply by d0, 2 = exact sign flip
+template <int kKind>
+__global__ void __launch_bounds__(kThreads) k_diag_c64x2(float2* __restrict__ psi, uint64_t nwork, Expand e, int p,
+                                                          const float2* __restrict__ m) {
+  using A = AF32;
+  float4* psi4 = reinterpret_cast<float4*>(psi);
+  const float2 d0 = kKind == 2 ? make_float2(0.f, 0.f) : m[0];
+  const float2 d1 = kKind == 0 ? m[1] : d0;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nwork; t += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = expand(t, e);
+    float4 v = psi4[i >> 1];
+    if (kKind == 2) {
+      v = make_float4(-v.x, -v.y, -v.z, -v.w);
+    } else {
+      float2 f0 = d0, f1 = d0;
+      if (kKind == 0) {
+        if (p == 0) f1 = d1;
+        else f0 = f1 = ((i >> p) & 1) ? d1 : d0;
+      }
+      const float2 a = A::mul(f0, make_float2(v.x, v.y)), b = A::mul(f1, make_float2(v.z, v.w));
+      v = make_float4(a.x, a.y, b.x, b.y);
+    }
+    psi4[i >> 1] = v;
+  }
+}
+
 // dense 2^K x 2^K on bits kq[0..K-1]: a block stages kThreads / 2^K groups of 2^K
 // amplitudes in shared memory; thread (g, r) computes output row r of group g.
 template <class A, int K>
@@ -170,6 +237,35 @@ Expand make_expand(int n, uint64_t zero_bits, uint64_t ones, uint64_t* nwork) {
   return e;
 }
 
+// complex64 gates that the 16-byte kernels cover; false = use the general kernels
+bool launch_gate_c64x2(float2* psi, int n, const DevOp& op, const float2* mp, cudaStream_t st) {
+  if (n < 2 || (op.cmask & 1ull) || __builtin_popcountll(op.cmask) > 6) return false;
+  uint64_t nwork = 0;
+  switch (op.type) {
+    case OP_U1:
+    case OP_RX: {
+      const uint64_t zb = (op.k0 == 0) ? 1ull : ((1ull << op.k0) | 1ull);
+      Expand e = make_expand(n, zb, op.cmask, &nwork);
+      if (op.type == OP_U1) k_pair_c64x2<false><<<grid_for(nwork), kThreads, 0, st>>>(psi, nwork, e, op.k0, mp);
+      else k_pair_c64x2<true><<<grid_for(nwork), kThreads, 0, st>>>(psi, nwork, e, op.k0, mp);
+      return true;
+    }
+    case OP_DIAG: {
+      Expand e = make_expand(n, 1ull, op.cmask, &nwork);
+      k_diag_c64x2<0><<<grid_for(nwork), kThreads, 0, st>>>(psi, nwork, e, op.k0, mp);
+      return true;
+    }
+    case OP_PHASE: {
+      Expand e = make_expand(n, 1ull, op.cmask, &nwork);
+      if (op.mat < 0) k_diag_c64x2<2><<<grid_for(nwork), kThreads, 0, st>>>(psi, nwork, e, 0, mp);
+      else k_diag_c64x2<1><<<grid_for(nwork), kThreads, 0, st>>>(psi, nwork, e, 0, mp);
+      return true;
+    }
+    default:
+      return false;
+  }
+}
+
 template <class A>
 cudaError_t launch_gate_t(void* psi_v, int n, const DevOp& op, const void* pool, cudaStream_t st) {
   using S = typename A::store_t;
@@ -177,6 +273,9 @@ cudaError_t launch_gate_t(void* psi_v, int n, const DevOp& op, const void* pool,
   S* psi = (S*)psi_v;
   const M* mp = (const M*)pool + op.mat;
   uint64_t nwork = 0;
+  if constexpr (std::is_same<A, AF32>::value) {   // complex64: 16-byte accesses where possible
+    if (launch_gate_c64x2(psi, n, op, mp, st)) return cudaGetLastError();
+  }
   switch (op.type) {
     case OP_U1: {
       Expand e = make_expand(n, 1ull << op.k0, op.cmask, &nwork);
