@@ -266,7 +266,7 @@ qs_status qs_run(qs_handle h, const qs_op* ops, size_t nops, const double* mats,
  * persistent kernel launch over all those passes' tiles.  After the first (eager) run the
  * sequence init -> waves -> per-circuit norms is replayed from a captured CUDA graph when a
  * non-default stream is set.  A circuit's amplitudes are bitwise those of a solo qs_execute
- * with the same options. */
+ * with the same options.  opts->renorm_every must be 0 (QS_EINVAL otherwise). */
 typedef struct qs_batch* qs_batch_t;
 
 typedef struct {
@@ -362,6 +362,15 @@ qs_status qs_renormalize(qs_handle h, double* norm_out);
  * wrong results; calls on one stream are safe.  Asynchronous: synchronise the stream
  * before reading *out_dev. */
 qs_status qs_norm_noalloc(const void* psi, int n, qs_dtype dtype, double* out_dev, void* stream);
+
+/* ---- self-test of the bounded waits (no counterpart in the paper) ------------------ *
+ * Every kernel that waits on an mbarrier (bulk copies, tensor-core commits) gives up after
+ * a %globaltimer limit and reports QS_ETIMEOUT instead of hanging.  This call exercises that
+ * path on purpose: one CTA waits on an mbarrier nothing arrives on, with a limit of limit_us
+ * microseconds (1 .. 1000000), and writes its verdict to *device_status (HOST memory):
+ * QS_ETIMEOUT when the wait expired as designed.  Synchronous on the default stream;
+ * returns QS_OK unless a CUDA call failed (QS_ECUDA) or the arguments are invalid. */
+qs_status qs_selftest_bounded_wait(int limit_us, int* device_status);
 
 #ifdef __cplusplus
 }

@@ -394,3 +394,11 @@ def use_default_allocator():
     null_f = ctypes.cast(None, _lib.FREE_FN)
     _lib.check(_L().qs_set_allocator(null_a, null_f, None))
     _torch_cb = None
+
+
+def selftest_bounded_wait(limit_us: int = 20000) -> int:
+    """Run the bounded-wait self-test (qs_selftest_bounded_wait); returns the status the
+    device reported (QS_ETIMEOUT when the deliberately unsatisfiable wait expired)."""
+    out = ctypes.c_int(-1)
+    _lib.check(_L().qs_selftest_bounded_wait(int(limit_us), ctypes.byref(out)))
+    return out.value

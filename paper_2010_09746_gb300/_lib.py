@@ -101,6 +101,7 @@ SIGNATURES = {
     "qs_norm_noalloc": (_I, [_P, _I, _I, _P, _P]),
     "qs_inner": (_I, [_H, _H, _DP]),
     "qs_set_dense_path": (_I, [_H, _I]),
+    "qs_selftest_bounded_wait": (_I, [_I, _IP]),
     "qs_renormalize": (_I, [_H, _DP]),
     "qs_batch_create": (_I, [_I, _IP, ctypes.POINTER(qs_op), ctypes.POINTER(ctypes.c_int64), _DP, ctypes.c_size_t,
                              ctypes.POINTER(qs_compile_opts), ctypes.POINTER(_H)]),

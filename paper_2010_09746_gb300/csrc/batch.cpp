@@ -112,6 +112,7 @@ qs_status qs_batch_create(int count, const int* n, const qs_op* ops, const int64
   if (o.mode != QS_MODE_TILE) return bfail(QS_EINVAL, "batches run tile-mode plans only");
   if (o.dtype != QS_C64 && o.dtype != QS_C128) return bfail(QS_EINVAL, "unknown dtype");
   if ((o.flags & ~QS_FLAG_FULL_RX) || o.reg_bits < 0 || o.reg_bits > 5) return bfail(QS_EINVAL, "bad options");
+  if (o.renorm_every != 0) return bfail(QS_EINVAL, "periodic renormalisation is not available in batches");
   auto t0 = std::chrono::steady_clock::now();
   qs_batch* b = new qs_batch();
   b->count = count;

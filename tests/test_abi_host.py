@@ -228,3 +228,18 @@ def test_tangent_rx_lowers_the_count():
     ops, nops, mats = qs.marshal(circ[:3])
     assert _lib.load().qs_compile(n, ops, nops, mats.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), mats.size,
                                   None, ctypes.byref(o), ctypes.byref(h)) == _lib.QS_EINVAL
+
+
+def test_batch_rejects_periodic_renorm():
+    n = 6
+    circ = wc.rzrx_cz_circuit(n, 2, seed=0)
+    ops, nops, mats = qs.marshal(circ)
+    o = qs._opts(dtype="c64", renorm_every=2)
+    n_arr = np.array([n], dtype=np.int32)
+    offs = np.array([0, nops], dtype=np.int64)
+    h = ctypes.c_void_p()
+    st = _lib.load().qs_batch_create(1, n_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ops,
+                                     offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                     mats.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), mats.size,
+                                     ctypes.byref(o), ctypes.byref(h))
+    assert st == _lib.QS_EINVAL
