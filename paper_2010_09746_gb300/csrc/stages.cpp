@@ -147,25 +147,28 @@ void merge_diagonals(std::vector<RegOp>& rl, int K, Pool& pool) {
     std::vector<RegOp> fac, rest;
     for (size_t k = i; k < e; k++) (slot_only(rl[k]) ? fac : rest).push_back(rl[k]);
     if (!fac.empty()) {   // even a single slot factor: a table multiply avoids per-element selects
-      // entry j = product of the run's factors at register index j, divided by entry 0; the
-      // entries whose factors all equal their value at index 0 are exactly 1 and skipped
-      // (mask), and entry 0's value (a phase of the whole tile) is kept after the table for
-      // the pass-level fold
+      // entry j = product of the run's factors at register index j, divided by entry 0; an
+      // entry whose factors all equal their values at index 0 is exactly 1 and skipped (it is
+      // outside the mask), and entry 0's value (a phase of the whole tile) is kept after the
+      // table for the pass-level fold
       std::vector<cd> tab(D, cd(1, 0));
       uint32_t mask = 0;
       for (const RegOp& r : fac) {
-        for (int j = 0; j < D; j++) {
-          if (((uint32_t)j & r.csl) != r.csl) continue;
+        // this factor's value at register index j (1 where its slot controls are not all set)
+        auto fval = [&](int j) -> cd {
+          if (((uint32_t)j & r.csl) != r.csl) return cd(1, 0);
           if (r.type == OP_DIAG) {
             const int m = r.mat + (((j >> r.s0) & 1) ? 1 : 0);
-            tab[j] *= cd(pool.f64[2 * m], pool.f64[2 * m + 1]);
-            if (((j >> r.s0) & 1) && (pool.f64[2 * (r.mat + 1)] != pool.f64[2 * r.mat] ||
-                                      pool.f64[2 * (r.mat + 1) + 1] != pool.f64[2 * r.mat + 1]))
-              mask |= 1u << j;
-          } else {
-            tab[j] *= r.neg ? cd(-1, 0) : cd(pool.f64[2 * r.mat], pool.f64[2 * r.mat + 1]);
-            if (r.csl != 0) mask |= 1u << j;   // differs from index 0, where the control is 0
+            return cd(pool.f64[2 * m], pool.f64[2 * m + 1]);
           }
+          return r.neg ? cd(-1, 0) : cd(pool.f64[2 * r.mat], pool.f64[2 * r.mat + 1]);
+        };
+        const cd f0 = fval(0);
+        for (int j = 0; j < D; j++) {
+          if (((uint32_t)j & r.csl) != r.csl) continue;
+          const cd f = fval(j);
+          tab[j] *= f;
+          if (f != f0) mask |= 1u << j;
         }
       }
       // a phase without slot controls multiplies every entry alike: it only changes entry 0
@@ -319,7 +322,12 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
   const int N = (int)ops.size();
 
   std::vector<OpInfo> info(N);
-  for (int i = 0; i < N; i++) info[i] = classify_op(ops[i]);
+  for (int i = 0; i < N; i++) {
+    info[i] = classify_op(ops[i]);
+    // an op whose non-diagonal bits outnumber the register bits (a 4x4 block with K = 1)
+    // cannot run in registers
+    if (__builtin_popcount(info[i].need) > K) info[i].smem_only = true;
+  }
   // dependency DAG over tile bits (same grouping rule as the circuit DAG)
   std::vector<std::vector<int>> preds(N);
   struct BS {

@@ -240,3 +240,38 @@ def test_tangent_rx_matches_full_form(dtype):
     else:
         for v in out.values():
             assert sv.fidelity_loss(v, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+@pytest.mark.parametrize("K", [1, 2, 3, 4, 5])
+def test_tile_mode_every_register_width(dtype, arith, K):
+    """Every register-stage width the kernels instantiate (complex128 up to 4, complex64 up to
+    5), on mixed circuits with 1- to 4-qubit gates, controls and diagonals, plus the
+    RZ/RX/CZ construction (tangent-form RX runs, phase tables)."""
+    if dtype == "c128" and K > 4:
+        pytest.skip("complex128 holds at most 4 register bits")
+    n = 15
+    circ = wc.random_mixed_circuit(n, 200, seed=100 + K, kmax=3) + wc.rzrx_cz_circuit(n, 6, seed=K)
+    st = qs.State(n, dtype, arith=arith)
+    st.execute(qs.compile(n, circ, mode="tile", dtype=dtype, arith=arith, tile_bits=11, reg_bits=K))
+    check(st.amplitudes(), sv.simulate(n, circ), dtype)
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+def test_controlled_diagonals_in_phase_tables(dtype, arith):
+    """Controlled diagonal gates (controlled RZ-type 2x2) between rotations: inside a register
+    stage they become phase-table factors whose value at index 0 is 1 (control clear) while
+    other entries take d0 or d1, the case the table's multiply mask must cover."""
+    n = 14
+    rng = np.random.default_rng(5)
+    circ = []
+    for layer in range(8):
+        for q in range(n):
+            circ.append(wc.Gate("RX", (q,), param=float(rng.uniform(0, 2 * np.pi))))
+        for _ in range(n):
+            c, t = (int(x) for x in rng.choice(n, 2, replace=False))
+            a, b = rng.uniform(0, 2 * np.pi, 2)
+            circ.append(wc.Gate("CU", (c, t), matrix=np.diag([np.exp(1j * a), np.exp(1j * b)])))
+    st = qs.State(n, dtype, arith=arith)
+    st.execute(qs.compile(n, circ, mode="tile", dtype=dtype, arith=arith))
+    check(st.amplitudes(), sv.simulate(n, circ), dtype)
