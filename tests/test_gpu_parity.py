@@ -7,7 +7,6 @@ Tolerances (stated requirements of the hot path):
   ~6e-8 per operation over a few hundred gates on unit-norm states);
   permutations: bit-exact.
 """
-import math
 
 import numpy as np
 import pytest

@@ -4,7 +4,6 @@ units (weak scaling, no collective on the data path)."""
 import os
 import socket
 
-import pytest
 import torch.distributed as dist
 import torch.multiprocessing as mp
 

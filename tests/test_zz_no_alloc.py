@@ -8,7 +8,6 @@ read-out tests use, and checks that oversized and null arguments are rejected.
 """
 import ctypes
 
-import numpy as np
 import pytest
 
 from workloads import circuits as wc
