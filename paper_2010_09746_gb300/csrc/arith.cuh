@@ -13,10 +13,13 @@
 //       an unevaluated sum hi + lo of two floats (Dekker 1971 TwoProduct via FMA; Knuth
 //       TwoSum; Shewchuk 1997 renormalisation).  About 47-48 significant bits, relative
 //       error ~1e-14 per operation.  The FP64 <-> (hi, lo) conversions are done with
-//       integer bit manipulation so that no instruction touches the FP64 pipe.
+//       integer bit manipulation so that no instruction touches the FP64 pipe; the real
+//       and imaginary lanes run through packed f32x2 instructions.
 #pragma once
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace qs {
 
@@ -28,6 +31,8 @@ struct AF32 {
   using reg_t = float2;
   using mat_t = float2;
   static constexpr int kStoreBytes = 8;
+  static constexpr bool kFrame = false;
+  static __device__ __forceinline__ mat_t ld(const mat_t* p) { return *p; }
   static __device__ __forceinline__ reg_t from_store(store_t v) { return v; }
   static __device__ __forceinline__ store_t to_store(reg_t v) { return v; }
   static __device__ __forceinline__ reg_t zero() { return make_float2(0.f, 0.f); }
@@ -77,6 +82,8 @@ struct AF64 {
   using reg_t = double2;
   using mat_t = double2;
   static constexpr int kStoreBytes = 16;
+  static constexpr bool kFrame = false;
+  static __device__ __forceinline__ mat_t ld(const mat_t* p) { return *p; }
   static __device__ __forceinline__ reg_t from_store(store_t v) { return v; }
   static __device__ __forceinline__ store_t to_store(reg_t v) { return v; }
   static __device__ __forceinline__ reg_t zero() { return make_double2(0.0, 0.0); }
@@ -113,28 +120,167 @@ struct AF64 {
 };
 
 // ------------------------------------------------------------------------------------------
-// double-float building blocks (all explicitly rounded: no contraction changes them)
+// double-float building blocks (all explicitly rounded: no contraction changes them).
+// They are host-callable as well, so that the formulas can be checked on a CPU against
+// binary64; on the host the float operations are plain IEEE binary32 with
+// round-to-nearest (build with contraction off).
 // ------------------------------------------------------------------------------------------
+#define QS_HD __host__ __device__ __forceinline__
+
+QS_HD float f_add(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fadd_rn(a, b);
+#else
+  return a + b;
+#endif
+}
+QS_HD float f_sub(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fsub_rn(a, b);
+#else
+  return a - b;
+#endif
+}
+QS_HD float f_mul(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+QS_HD float f_fma(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+  return __fmaf_rn(a, b, c);
+#else
+  return fmaf(a, b, c);
+#endif
+}
+QS_HD unsigned int f_bits(float x) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(x);
+#else
+  unsigned int u;
+  memcpy(&u, &x, 4);
+  return u;
+#endif
+}
+QS_HD float f_from_bits(unsigned int u) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(u);
+#else
+  float x;
+  memcpy(&x, &u, 4);
+  return x;
+#endif
+}
+QS_HD unsigned long long d_bits(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long u;
+  memcpy(&u, &x, 8);
+  return u;
+#endif
+}
+QS_HD double d_from_bits(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)u);
+#else
+  double x;
+  memcpy(&x, &u, 8);
+  return x;
+#endif
+}
+QS_HD float u32_to_f_rn(unsigned int r) {
+#ifdef __CUDA_ARCH__
+  return __uint2float_rn(r);
+#else
+  return (float)r;
+#endif
+}
+QS_HD int f_to_i_rn(float x) {
+#ifdef __CUDA_ARCH__
+  return __float2int_rn(x);
+#else
+  return (int)lrintf(x);
+#endif
+}
+
+// Packed lane pairs: one f32x2 instruction (FADD2 / FMUL2 / FFMA2 on sm_100 and later)
+// does the same operation on both floats of a 64-bit register pair.
+QS_HD float2 add2(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+  return __fadd2_rn(a, b);
+#else
+  return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+QS_HD float2 sub2(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+#else
+  return make_float2(a.x - b.x, a.y - b.y);
+#endif
+}
+QS_HD float2 mul2(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+  return __fmul2_rn(a, b);
+#else
+  return make_float2(a.x * b.x, a.y * b.y);
+#endif
+}
+QS_HD float2 fma2(float2 a, float2 b, float2 c) {
+#ifdef __CUDA_ARCH__
+  return __ffma2_rn(a, b, c);
+#else
+  return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+#endif
+}
+
 struct dfl { float hi, lo; };
 
 // s + e == a + b exactly (Knuth TwoSum, 6 flops)
-static __device__ __forceinline__ dfl two_sum(float a, float b) {
-  float s = __fadd_rn(a, b);
-  float bb = __fsub_rn(s, a);
-  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-// s + e == a + b exactly when |a| >= |b| (Dekker FastTwoSum, 3 flops)
-static __device__ __forceinline__ dfl fast_two_sum(float a, float b) {
-  float s = __fadd_rn(a, b);
-  float e = __fsub_rn(b, __fsub_rn(s, a));
+QS_HD dfl two_sum(float a, float b) {
+  float s = f_add(a, b);
+  float bb = f_sub(s, a);
+  float e = f_add(f_sub(a, f_sub(s, bb)), f_sub(b, bb));
   return {s, e};
 }
 // p + e == a * b exactly (TwoProduct with FMA)
-static __device__ __forceinline__ dfl two_prod(float a, float b) {
-  float p = __fmul_rn(a, b);
-  float e = __fmaf_rn(a, b, -p);
+QS_HD dfl two_prod(float a, float b) {
+  float p = f_mul(a, b);
+  float e = f_fma(a, b, -p);
   return {p, e};
+}
+// lane-wise TwoSum: s + e == a + b exactly in each lane
+QS_HD void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = add2(a, b);
+  const float2 bb = sub2(s, a);
+  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+// lane-wise TwoSum of a and -b: s + e == a - b exactly
+QS_HD void two_diff2(float2 a, float2 b, float2& s, float2& e) {
+  s = sub2(a, b);
+  const float2 bb = sub2(s, a);
+  e = sub2(sub2(a, sub2(s, bb)), add2(b, bb));
+}
+// Lane-wise double-float product of U = Uh + Ul (given as Uh, -Uh, -Ul) and v = vh + vl:
+// p = Uh vh rounded, ne = -(TwoProduct error + Uh vl + Ul vh), so that U v ~= p - ne
+// (the product of the low parts, ~2^-48 relative, is dropped).  The negated operands keep
+// every step a plain packed FMA: FMA(-Uh, vh, p) is the exact negated TwoProduct error.
+QS_HD void prod2(float2 Uh, float2 nUh, float2 nUl, float2 vh, float2 vl, float2& p, float2& ne) {
+  p = mul2(Uh, vh);
+  ne = fma2(nUh, vh, p);
+  ne = fma2(nUh, vl, ne);
+  ne = fma2(nUl, vh, ne);
 }
 
 // Split a binary64 value into hi + lo floats without FP64 instructions.
@@ -142,21 +288,21 @@ static __device__ __forceinline__ dfl two_prod(float a, float b) {
 // to 24): |x - (hi + lo)| <= 2^-47 |x|.  |x| < 2^-126 flushes to 0 (absolute error
 // below 1.2e-38); the lo part flushes when it would leave the normal float range
 // (|x| below about 2^-98; absolute error below 2^-120).
-static __device__ __forceinline__ dfl split_double(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+QS_HD dfl split_double(double x) {
+  const unsigned long long b = d_bits(x);
   const unsigned int w1 = (unsigned int)(b >> 32);
   const unsigned int w0 = (unsigned int)b;
   const unsigned int sign = w1 & 0x80000000u;
   const int e = (int)((w1 >> 20) & 0x7FFu);
   const int ef = e - 896;                                   // float biased exponent
   const unsigned int m23 = ((w1 & 0xFFFFFu) << 3) | (w0 >> 29);
-  float hi = __uint_as_float(sign | ((unsigned int)ef << 23) | m23);
+  float hi = f_from_bits(sign | ((unsigned int)ef << 23) | m23);
   hi = (ef > 0) ? hi : 0.0f;
   const unsigned int r = w0 & 0x1FFFFFFFu;                   // low 29 mantissa bits
   // lo = r * 2^(e - 1075): convert r exactly-rounded, then move its exponent field
-  const unsigned int rb = __float_as_uint(__uint2float_rn(r));
+  const unsigned int rb = f_bits(u32_to_f_rn(r));
   const int el = (int)(rb >> 23) + (e - 1075);               // biased exponent of lo
-  float lo = __uint_as_float(sign | ((unsigned int)el << 23) | (rb & 0x7FFFFFu));
+  float lo = f_from_bits(sign | ((unsigned int)el << 23) | (rb & 0x7FFFFFu));
   lo = (r != 0u && el > 0 && ef > 0) ? lo : 0.0f;
   return {hi, lo};
 }
@@ -165,15 +311,15 @@ static __device__ __forceinline__ dfl split_double(double x) {
 // with integer operations only: the binary64 pattern of hi plus lo counted in binary64 ulps
 // (IEEE patterns are monotonic in magnitude for a fixed sign, so adding k to the pattern
 // moves the value by k ulps, across a binade boundary included).
-static __device__ __forceinline__ double join_double(float hi, float lo) {
-  const unsigned int hb = __float_as_uint(hi);
+QS_HD double join_double(float hi, float lo) {
+  const unsigned int hb = f_bits(hi);
   const unsigned int sign = hb & 0x80000000u;
   const int ef = (int)((hb >> 23) & 0xFFu);
   if (ef == 0) return 0.0;
   unsigned long long db = ((unsigned long long)(sign | ((unsigned int)(ef + 896) << 20) |
                                                 ((hb & 0x7FFFFFu) >> 3)) << 32) |
                           ((unsigned long long)(hb & 7u) << 29);
-  const unsigned int lb = __float_as_uint(lo);
+  const unsigned int lb = f_bits(lo);
   const int el = (int)((lb >> 23) & 0xFFu);
   // lo is counted in binary64 ulps of hi's binade, 2^(ef-179); when hi is a power of two and
   // lo points down, the result lies in the binade below, whose ulp is half as large
@@ -181,124 +327,174 @@ static __device__ __forceinline__ double join_double(float hi, float lo) {
   const int ne = el + (down ? 180 : 179) - ef;             // exponent of lo / ulp
   int k = 0;
   if (el != 0 && ne > 0) {
-    float ls = __uint_as_float((lb & 0x807FFFFFu) | ((unsigned int)ne << 23));
-    k = __float2int_rn(ls);
+    float ls = f_from_bits((lb & 0x807FFFFFu) | ((unsigned int)ne << 23));
+    k = f_to_i_rn(ls);
   }
   long long delta = sign ? -(long long)k : (long long)k;
   db = (unsigned long long)((long long)db + delta);
-  return __longlong_as_double((long long)db);
+  return d_from_bits(db);
 }
 
 // ------------------------------------------------------------------------------------------
-// complex128 storage, double-float arithmetic
-// reg_t = (re.hi, re.lo, im.hi, im.lo); mat_t the same format (prepared on the host).
+// complex128 storage, double-float arithmetic, two lanes per instruction
+//
+// reg_t = (re.hi, im.hi, re.lo, im.lo): the (re, im) lanes of the high parts and of the
+// low parts are each one 64-bit register pair, so each step of the complex arithmetic is
+// one packed f32x2 instruction instead of two scalar ones.  Register values are kept
+// unnormalised between operations (hi need not be the rounded value of hi + lo);
+// to_store normalises once with TwoSum before the exact integer join.
+//
+// mat_t (48 bytes, prepared on the host) holds a complex u = ur + i ui as lane patterns:
+//   a = ( ur.hi,  ur.hi, -ur.hi, -ur.hi)     ur on both lanes, and its negation
+//   b = (-ui.hi,  ui.hi,  ui.hi, -ui.hi)     (-ui, ui): i ui acting on a swapped (im, re)
+//   c = (-ur.lo, -ur.lo,  ui.lo, -ui.lo)     negated low parts of both patterns
+// so that u a = ur (.) a + (-ui, ui) (.) swap(a) lane-wise and no packed operand needs a
+// sign flip at run time.
+//
+// Tile passes run in a phase frame: amplitude i of a tile is held as (-i)^popcount(i)
+// times its value (S^dagger on every tile bit).  Diagonal gates are unchanged, RX becomes
+// the real rotation [[c, s], [-s, c]] (no lane swaps at all), X becomes [[0, i], [-i, 0]],
+// and the host transforms the matrices of general gates (entry (r, c) times
+// (-i)^(popcount r - popcount c)).  The per-gate kernels use the plain frame.
 // ------------------------------------------------------------------------------------------
+struct alignas(16) dfm {
+  float4 a, b, c;
+};
+// a real double-float factor t as the three lane pairs the products need: (t.hi, t.hi),
+// its negation, and the negated low part
+struct dfr {
+  float2 h, nh, nl;
+};
+
 struct ADF {
   using store_t = double2;
   using reg_t = float4;
-  using mat_t = float4;
+  using mat_t = dfm;
   static constexpr int kStoreBytes = 16;
-  static __device__ __forceinline__ reg_t from_store(store_t v) {
-    dfl r = split_double(v.x), i = split_double(v.y);
-    return make_float4(r.hi, r.lo, i.hi, i.lo);
+  static constexpr bool kFrame = true;
+
+  static QS_HD float2 hi(reg_t v) { return make_float2(v.x, v.y); }
+  static QS_HD float2 lo(reg_t v) { return make_float2(v.z, v.w); }
+  static QS_HD float2 swp(float2 v) { return make_float2(v.y, v.x); }
+  static QS_HD reg_t mk(float2 h, float2 l) { return make_float4(h.x, h.y, l.x, l.y); }
+
+  // A 48-byte entry loaded where it is used: the loads are volatile so that the compiler
+  // cannot hoist the entries of a whole matrix out of a loop (12 registers each).
+  static QS_HD mat_t ld(const mat_t* p) {
+#ifdef __CUDA_ARCH__
+    mat_t m;
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(m.a.x), "=f"(m.a.y), "=f"(m.a.z), "=f"(m.a.w) : "l"(p));
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4+16];"
+                 : "=f"(m.b.x), "=f"(m.b.y), "=f"(m.b.z), "=f"(m.b.w) : "l"(p));
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4+32];"
+                 : "=f"(m.c.x), "=f"(m.c.y), "=f"(m.c.z), "=f"(m.c.w) : "l"(p));
+    return m;
+#else
+    return *p;
+#endif
   }
-  // register values are kept unnormalised between operations (hi need not be the rounded
-  // value of hi + lo); normalise once with TwoSum before the exact integer join
-  static __device__ __forceinline__ store_t to_store(reg_t v) {
-    const dfl r = two_sum(v.x, v.y), i = two_sum(v.z, v.w);
+  // the real part of an entry (t, 0): two of its three 16-byte words
+  static QS_HD dfr ld_real(const mat_t* p) {
+#ifdef __CUDA_ARCH__
+    float4 a, c;
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w) : "l"(p));
+    asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4+32];" : "=f"(c.x), "=f"(c.y), "=f"(c.z), "=f"(c.w) : "l"(p));
+    return dfr{make_float2(a.x, a.y), make_float2(a.z, a.w), make_float2(c.x, c.y)};
+#else
+    return real_of(*p);
+#endif
+  }
+  static QS_HD dfr real_of(const mat_t& m) {
+    return dfr{make_float2(m.a.x, m.a.y), make_float2(m.a.z, m.a.w), make_float2(m.c.x, m.c.y)};
+  }
+  static QS_HD reg_t from_store(store_t v) {
+    const dfl r = split_double(v.x), i = split_double(v.y);
+    return make_float4(r.hi, i.hi, r.lo, i.lo);
+  }
+  static QS_HD store_t to_store(reg_t v) {
+    const dfl r = two_sum(v.x, v.z), i = two_sum(v.y, v.w);
     return make_double2(join_double(r.hi, r.lo), join_double(i.hi, i.lo));
   }
-  static __device__ __forceinline__ reg_t zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static QS_HD reg_t zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
-  // Sum of two products p0 + p1 where p_k = (a_k.hi + a_k.lo) * (b_k.hi + b_k.lo) (signs
-  // folded into the a's): TwoProduct of the high parts, first-order cross terms in FP32,
-  // TwoSum of the two leading terms.  The result is left unnormalised (lo collects the
-  // TwoSum error and the first-order terms, |lo| ~ 2^-22 |hi|); the next operation uses lo
-  // only in first-order terms, so accuracy stays near 2^-44 relative, and to_store
-  // normalises before converting back to binary64.
-  static __device__ __forceinline__ dfl dot2(float a0h, float a0l, float b0h, float b0l,
-                                             float a1h, float a1l, float b1h, float b1l) {
-    dfl p0 = two_prod(a0h, b0h);
-    dfl p1 = two_prod(a1h, b1h);
-    float err = __fmaf_rn(a0h, b0l, p0.lo);
-    err = __fmaf_rn(a0l, b0h, err);
-    err = __fadd_rn(err, p1.lo);
-    err = __fmaf_rn(a1h, b1l, err);
-    err = __fmaf_rn(a1l, b1h, err);
-    dfl s = two_sum(p0.hi, p1.hi);
-    return {s.hi, __fadd_rn(s.lo, err)};
+  // u a
+  static QS_HD reg_t mul(const mat_t& u, reg_t a) {
+    float2 p1, n1, p2, n2, s, e;
+    prod2(make_float2(u.a.x, u.a.y), make_float2(u.a.z, u.a.w), make_float2(u.c.x, u.c.y), hi(a), lo(a), p1, n1);
+    prod2(make_float2(u.b.x, u.b.y), make_float2(u.b.z, u.b.w), make_float2(u.c.z, u.c.w), swp(hi(a)), swp(lo(a)),
+          p2, n2);
+    two_sum2(p1, p2, s, e);
+    return mk(s, sub2(e, add2(n1, n2)));
   }
-  static __device__ __forceinline__ dfl dot4(float a0h, float a0l, float b0h, float b0l,
-                                             float a1h, float a1l, float b1h, float b1l,
-                                             float a2h, float a2l, float b2h, float b2l,
-                                             float a3h, float a3l, float b3h, float b3l) {
-    dfl p0 = two_prod(a0h, b0h);
-    dfl p1 = two_prod(a1h, b1h);
-    dfl p2 = two_prod(a2h, b2h);
-    dfl p3 = two_prod(a3h, b3h);
-    float err = __fmaf_rn(a0h, b0l, p0.lo);
-    err = __fmaf_rn(a0l, b0h, err);
-    err = __fadd_rn(err, p1.lo);
-    err = __fmaf_rn(a1h, b1l, err);
-    err = __fmaf_rn(a1l, b1h, err);
-    err = __fadd_rn(err, p2.lo);
-    err = __fmaf_rn(a2h, b2l, err);
-    err = __fmaf_rn(a2l, b2h, err);
-    err = __fadd_rn(err, p3.lo);
-    err = __fmaf_rn(a3h, b3l, err);
-    err = __fmaf_rn(a3l, b3h, err);
-    dfl s01 = two_sum(p0.hi, p1.hi);
-    dfl s23 = two_sum(p2.hi, p3.hi);
-    dfl s = two_sum(s01.hi, s23.hi);
-    err = __fadd_rn(err, __fadd_rn(s01.lo, __fadd_rn(s23.lo, s.lo)));
-    return {s.hi, err};
+  static QS_HD reg_t add(reg_t x, reg_t y) {
+    float2 s, e;
+    two_sum2(hi(x), hi(y), s, e);
+    return mk(s, add2(e, add2(lo(x), lo(y))));
   }
-  // acc + u*a (complex)
-  static __device__ __forceinline__ reg_t mac(reg_t acc, mat_t u, reg_t a) {
-    reg_t p = mul(u, a);
-    dfl re = two_sum(acc.x, p.x);
-    dfl im = two_sum(acc.z, p.z);
-    return make_float4(re.hi, __fadd_rn(re.lo, __fadd_rn(acc.y, p.y)), im.hi, __fadd_rn(im.lo, __fadd_rn(acc.w, p.w)));
+  // acc + u a
+  static QS_HD reg_t mac(reg_t acc, const mat_t& u, reg_t a) { return add(acc, mul(u, a)); }
+  // u a + v b
+  static QS_HD reg_t mac2(const mat_t& u, reg_t a, const mat_t& v, reg_t b) { return add(mul(u, a), mul(v, b)); }
+  // c a - i s b for cs = (c, s), plain frame: c (.) a + (s, -s) (.) swap(b), and (s, -s) is
+  // the negated (-ui, ui) pattern of the entry
+  static QS_HD reg_t rx(const mat_t& cs, reg_t a, reg_t b) {
+    float2 p1, n1, p2, n2, s, e;
+    prod2(make_float2(cs.a.x, cs.a.y), make_float2(cs.a.z, cs.a.w), make_float2(cs.c.x, cs.c.y), hi(a), lo(a), p1, n1);
+    prod2(make_float2(cs.b.x, cs.b.y), make_float2(cs.b.z, cs.b.w), make_float2(cs.c.z, cs.c.w), swp(hi(b)),
+          swp(lo(b)), p2, n2);
+    two_diff2(p1, p2, s, e);   // (p1 - n1) - (p2 - n2)
+    return mk(s, add2(e, sub2(n2, n1)));
   }
-  // u*a + v*b: re = u.re a.re - u.im a.im + v.re b.re - v.im b.im, im likewise
-  static __device__ __forceinline__ reg_t mac2(mat_t u, reg_t a, mat_t v, reg_t b) {
-    dfl re = dot4(u.x, u.y, a.x, a.y, -u.z, -u.w, a.z, a.w,
-                  v.x, v.y, b.x, b.y, -v.z, -v.w, b.z, b.w);
-    dfl im = dot4(u.x, u.y, a.z, a.w, u.z, u.w, a.x, a.y,
-                  v.x, v.y, b.z, b.w, v.z, v.w, b.x, b.y);
-    return make_float4(re.hi, re.lo, im.hi, im.lo);
+
+  // ---- phase-frame updates with a real double-float factor t
+  // u + t v
+  static QS_HD reg_t axpy_r(const dfr& t, reg_t v, reg_t u) {
+    float2 p, n, s, e;
+    prod2(t.h, t.nh, t.nl, hi(v), lo(v), p, n);
+    two_sum2(hi(u), p, s, e);
+    return mk(s, add2(e, sub2(lo(u), n)));
   }
-  static __device__ __forceinline__ reg_t mul(mat_t u, reg_t a) {
-    dfl re = dot2(u.x, u.y, a.x, a.y, -u.z, -u.w, a.z, a.w);
-    dfl im = dot2(u.x, u.y, a.z, a.w, u.z, u.w, a.x, a.y);
-    return make_float4(re.hi, re.lo, im.hi, im.lo);
+  // u - t v
+  static QS_HD reg_t axmy_r(const dfr& t, reg_t v, reg_t u) {
+    float2 p, n, s, e;
+    prod2(t.h, t.nh, t.nl, hi(v), lo(v), p, n);
+    two_diff2(hi(u), p, s, e);
+    return mk(s, add2(e, add2(lo(u), n)));
   }
-  // c*a - i*s*b with cs = (c.hi, c.lo, s.hi, s.lo): re = c a.re + s b.im, im = c a.im - s b.re
-  static __device__ __forceinline__ reg_t rx(mat_t cs, reg_t a, reg_t b) {
-    dfl re = dot2(cs.x, cs.y, a.x, a.y, cs.z, cs.w, b.z, b.w);
-    dfl im = dot2(cs.x, cs.y, a.z, a.w, -cs.z, -cs.w, b.x, b.y);
-    return make_float4(re.hi, re.lo, im.hi, im.lo);
+  // t v - u
+  static QS_HD reg_t ymx_r(const dfr& t, reg_t v, reg_t u) {
+    float2 p, n, s, e;
+    prod2(t.h, t.nh, t.nl, hi(v), lo(v), p, n);
+    two_diff2(p, hi(u), s, e);
+    return mk(s, sub2(e, add2(n, lo(u))));
   }
-  // u + t v for a real double-float t = (t.x, t.y): TwoProduct of the high parts, the two
-  // first-order cross terms, TwoSum with u's high part (12 instructions per component
-  // against 16 for a two-term dot product).  Used by the tangent-form RX, which applies
-  // (I - i t X) or (t I - i X) and leaves the factor cos or sin to one full-form RX of the
-  // pass.
-  static __device__ __forceinline__ reg_t axpy(mat_t t, reg_t v, reg_t u) {
-    const dfl pr = two_prod(t.x, v.x);
-    float er = __fmaf_rn(t.x, v.y, pr.lo);
-    er = __fmaf_rn(t.y, v.x, er);
-    const dfl sr = two_sum(u.x, pr.hi);
-    const dfl pi = two_prod(t.x, v.z);
-    float ei = __fmaf_rn(t.x, v.w, pi.lo);
-    ei = __fmaf_rn(t.y, v.z, ei);
-    const dfl si = two_sum(u.z, pi.hi);
-    return make_float4(sr.hi, __fadd_rn(sr.lo, __fadd_rn(u.y, er)), si.hi, __fadd_rn(si.lo, __fadd_rn(u.w, ei)));
+  // (a, b) -> (c a + s b, c b - s a) with real c and s
+  static QS_HD void rot_r(const dfr& c, const dfr& sn, reg_t a, reg_t b, reg_t& a2, reg_t& b2) {
+    const float2 ch = c.h, nch = c.nh, ncl = c.nl;
+    const float2 sh = sn.h, nsh = sn.nh, nsl = sn.nl;
+    float2 p1, n1, p2, n2, s, e;
+    prod2(ch, nch, ncl, hi(a), lo(a), p1, n1);
+    prod2(sh, nsh, nsl, hi(b), lo(b), p2, n2);
+    two_sum2(p1, p2, s, e);
+    const reg_t ra = mk(s, sub2(e, add2(n1, n2)));
+    prod2(ch, nch, ncl, hi(b), lo(b), p1, n1);
+    prod2(sh, nsh, nsl, hi(a), lo(a), p2, n2);
+    two_diff2(p1, p2, s, e);
+    b2 = mk(s, add2(e, sub2(n2, n1)));
+    a2 = ra;
   }
-  static __device__ __forceinline__ reg_t mul_mi(reg_t b) { return make_float4(b.z, b.w, -b.x, -b.y); }
-  static __device__ __forceinline__ reg_t neg(reg_t a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
-  static __device__ __forceinline__ double norm2(reg_t a) {
-    double r = (double)a.x + (double)a.y, i = (double)a.z + (double)a.w;
+  // v (-i)^q, exact (a lane swap and sign flips); q in 0..3
+  static QS_HD reg_t rot_q(reg_t v, unsigned int q) {
+    const bool sw = (q & 1u) != 0u;
+    const float r0 = sw ? v.y : v.x, r1 = sw ? v.x : v.y, l0 = sw ? v.w : v.z, l1 = sw ? v.z : v.w;
+    const unsigned int n0 = (q >> 1) << 31, n1 = ((q ^ (q >> 1)) & 1u) << 31;
+    return make_float4(f_from_bits(f_bits(r0) ^ n0), f_from_bits(f_bits(r1) ^ n1), f_from_bits(f_bits(l0) ^ n0),
+                       f_from_bits(f_bits(l1) ^ n1));
+  }
+  static QS_HD reg_t neg(reg_t a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
+  static QS_HD double norm2(reg_t a) {
+    double r = (double)a.x + (double)a.z, i = (double)a.y + (double)a.w;
     return r * r + i * i;
   }
 };

@@ -131,14 +131,18 @@ std::vector<unsigned char> Pool::serialise(Policy pol) const {
     out.resize(E * 16);
     memcpy(out.data(), f64.data(), E * 16);
   } else {
-    out.resize(E * 16);
+    // double-float lane patterns of u = ur + i ui (12 floats): (ur, ur) and its negation,
+    // (-ui, ui) and its negation, then the negated low parts of (ur, ur) and (-ui, ui)
+    out.resize(E * 48);
     float* f = (float*)out.data();
-    for (size_t k = 0; k < 2 * E; k++) {
-      const double x = f64[k];
-      const float hi = (float)x;
-      const float lo = (float)(x - (double)hi);
-      f[2 * k] = hi;
-      f[2 * k + 1] = lo;
+    for (size_t k = 0; k < E; k++) {
+      const double ur = f64[2 * k], ui = f64[2 * k + 1];
+      const float rh = (float)ur, rl = (float)(ur - (double)rh);
+      const float ih = (float)ui, il = (float)(ui - (double)ih);
+      float* e = f + 12 * k;
+      e[0] = rh; e[1] = rh; e[2] = -rh; e[3] = -rh;
+      e[4] = -ih; e[5] = ih; e[6] = ih; e[7] = -ih;
+      e[8] = -rl; e[9] = -rl; e[10] = il; e[11] = -il;
     }
   }
   return out;

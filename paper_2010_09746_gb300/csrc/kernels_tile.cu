@@ -137,7 +137,7 @@ __device__ __noinline__ void apply_dense_op(typename A::reg_t* Tm, int L, const 
     }
     for (int r = 0; r < D; r++) {
       R acc = A::zero();
-      for (int c = 0; c < D; c++) acc = A::mac(acc, m[r * D + c], x[c]);
+      for (int c = 0; c < D; c++) acc = A::mac(acc, A::ld(m + r * D + c), x[c]);
       Tm[off[r]] = acc;
     }
   }
@@ -164,12 +164,21 @@ __device__ __forceinline__ void apply_op(typename A::reg_t* Tm, int L, const Dev
       const uint32_t nw = 1u << (L - nz);
       const uint32_t s = 1u << op.k0;
       if (op.type == OP_U1) {
-        const M u00 = pool[op.mat], u01 = pool[op.mat + 1], u10 = pool[op.mat + 2], u11 = pool[op.mat + 3];
+        const M* u = pool + op.mat;
         for (uint32_t t = tid; t < nw; t += kTileThreads) {
           const uint32_t i = texpand(t, pos, nz, cm);
           const R a = T[i], b = T[i | s];
-          T[i] = A::mac2(u00, a, u01, b);
-          T[i | s] = A::mac2(u10, a, u11, b);
+          T[i] = A::mac2(A::ld(u), a, A::ld(u + 1), b);
+          T[i | s] = A::mac2(A::ld(u + 2), a, A::ld(u + 3), b);
+        }
+      } else if constexpr (A::kFrame) {
+        const auto c = A::ld_real(pool + op.mat), sn = A::ld_real(pool + op.mat + 1);   // (c, 0), (s, 0)
+        for (uint32_t t = tid; t < nw; t += kTileThreads) {
+          const uint32_t i = texpand(t, pos, nz, cm);
+          R a2, b2;
+          A::rot_r(c, sn, T[i], T[i | s], a2, b2);
+          T[i] = a2;
+          T[i | s] = b2;
         }
       } else {
         const M cs = pool[op.mat];
@@ -231,11 +240,18 @@ __device__ __forceinline__ void apply_op(typename A::reg_t* Tm, int L, const Dev
       }
       const int nz = bit_list(cm | zb, pos);
       const uint32_t nw = 1u << (L - nz);
+      // in the phase frame X is [[0, i], [-i, 0]]; SWAP exchanges equal popcounts
+      const bool framed_x = A::kFrame && op.type == OP_X;
       for (uint32_t t = tid; t < nw; t += kTileThreads) {
         const uint32_t i = texpand(t, pos, nz, cm);
-        const R a = T[i | s0];
-        T[i | s0] = T[i | s1];
-        T[i | s1] = a;
+        const R a = T[i | s0], b = T[i | s1];
+        if constexpr (A::kFrame) {
+          T[i | s0] = framed_x ? A::rot_q(b, 3u) : b;
+          T[i | s1] = framed_x ? A::rot_q(a, 1u) : a;
+        } else {
+          T[i | s0] = b;
+          T[i | s1] = a;
+        }
       }
       break;
     }
@@ -252,9 +268,9 @@ __device__ __forceinline__ void apply_op(typename A::reg_t* Tm, int L, const Dev
         for (int r = 0; r < 4; r++) x[r] = T[idx[r]];
 #pragma unroll
         for (int r = 0; r < 4; r++) {
-          R acc = A::mac2(m[4 * r + 0], x[0], m[4 * r + 1], x[1]);
-          acc = A::mac(acc, m[4 * r + 2], x[2]);
-          acc = A::mac(acc, m[4 * r + 3], x[3]);
+          R acc = A::mac2(A::ld(m + 4 * r + 0), x[0], A::ld(m + 4 * r + 1), x[1]);
+          acc = A::mac(acc, A::ld(m + 4 * r + 2), x[2]);
+          acc = A::mac(acc, A::ld(m + 4 * r + 3), x[3]);
           T[idx[r]] = acc;
         }
       }
@@ -284,53 +300,104 @@ __device__ __forceinline__ uint32_t pdep32(uint32_t g, uint32_t mask) {
 // update into a 4x4 block on the (target, control) slots); X keeps its predicate
 template <class A, int K, int S>
 __device__ __forceinline__ void r_u1(typename A::reg_t (&x)[1 << K], const typename A::mat_t* m, uint32_t csl) {
-  const typename A::mat_t u00 = m[0], u01 = m[1], u10 = m[2], u11 = m[3];
 #pragma unroll
   for (int j = 0; j < (1 << K); j++) {
     if (j & (1 << S)) continue;
     const typename A::reg_t a = x[j], b = x[j | (1 << S)];
-    x[j] = A::mac2(u00, a, u01, b);
-    x[j | (1 << S)] = A::mac2(u10, a, u11, b);
+    x[j] = A::mac2(A::ld(m + 0), a, A::ld(m + 1), b);
+    x[j | (1 << S)] = A::mac2(A::ld(m + 2), a, A::ld(m + 3), b);
   }
 }
 template <class A, int K, int S>
 __device__ __forceinline__ void r_rx(typename A::reg_t (&x)[1 << K], const typename A::mat_t* m, uint32_t csl) {
-  const typename A::mat_t cs = m[0];
+  if constexpr (A::kFrame) {   // real rotation, entries (c, 0) and (s, 0)
+    const auto c = A::ld_real(m), sn = A::ld_real(m + 1);
 #pragma unroll
-  for (int j = 0; j < (1 << K); j++) {
-    if (j & (1 << S)) continue;
-    const typename A::reg_t a = x[j], b = x[j | (1 << S)];
-    x[j] = A::rx(cs, a, b);
-    x[j | (1 << S)] = A::rx(cs, b, a);
+    for (int j = 0; j < (1 << K); j++) {
+      if (j & (1 << S)) continue;
+      A::rot_r(c, sn, x[j], x[j | (1 << S)], x[j], x[j | (1 << S)]);
+    }
+  } else {
+    const typename A::mat_t cs = m[0];
+#pragma unroll
+    for (int j = 0; j < (1 << K); j++) {
+      if (j & (1 << S)) continue;
+      const typename A::reg_t a = x[j], b = x[j | (1 << S)];
+      x[j] = A::rx(cs, a, b);
+      x[j | (1 << S)] = A::rx(cs, b, a);
+    }
   }
 }
-// tangent-form RX on slot S: mode 0 applies I - i t X, mode 1 applies t I - i X (the
-// compiler moves the dropped factor cos or sin into one full-form RX of the same pass)
-template <class A, int K, int S>
-__device__ __forceinline__ void r_rxt(typename A::reg_t (&x)[1 << K], const typename A::mat_t* m, uint32_t mode) {
-  const typename A::mat_t t = m[0];
+// phase frame (double-float policy): tangent-form RX mode 0 is [[1, t], [-t, 1]], mode 1 is
+// [[t, 1], [-1, t]], both real
+template <class A, int K, int S, class T>
+__device__ __forceinline__ void r_rxt_frame(typename A::reg_t (&x)[1 << K], const T& t, uint32_t mode) {
   if (mode == 0) {
 #pragma unroll
     for (int j = 0; j < (1 << K); j++) {
       if (j & (1 << S)) continue;
       const typename A::reg_t a = x[j], b = x[j | (1 << S)];
-      x[j] = A::axpy(t, A::mul_mi(b), a);
-      x[j | (1 << S)] = A::axpy(t, A::mul_mi(a), b);
+      x[j] = A::axpy_r(t, b, a);
+      x[j | (1 << S)] = A::axmy_r(t, a, b);
     }
   } else {
 #pragma unroll
     for (int j = 0; j < (1 << K); j++) {
       if (j & (1 << S)) continue;
       const typename A::reg_t a = x[j], b = x[j | (1 << S)];
-      x[j] = A::axpy(t, a, A::mul_mi(b));
-      x[j | (1 << S)] = A::axpy(t, b, A::mul_mi(a));
+      x[j] = A::axpy_r(t, a, b);
+      x[j | (1 << S)] = A::ymx_r(t, b, a);
+    }
+  }
+}
+// tangent-form RX on slot S: mode 0 applies I - i t X, mode 1 applies t I - i X (the
+// compiler moves the dropped factor cos or sin into one full-form RX of the same pass)
+template <class A, int K, int S>
+__device__ __forceinline__ void r_rxt(typename A::reg_t (&x)[1 << K], const typename A::mat_t* m, uint32_t mode) {
+  if constexpr (A::kFrame) {
+    r_rxt_frame<A, K, S>(x, A::ld_real(m), mode);
+  } else {
+    const typename A::mat_t t = m[0];
+    if (mode == 0) {
+#pragma unroll
+      for (int j = 0; j < (1 << K); j++) {
+        if (j & (1 << S)) continue;
+        const typename A::reg_t a = x[j], b = x[j | (1 << S)];
+        x[j] = A::axpy(t, A::mul_mi(b), a);
+        x[j | (1 << S)] = A::axpy(t, A::mul_mi(a), b);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < (1 << K); j++) {
+        if (j & (1 << S)) continue;
+        const typename A::reg_t a = x[j], b = x[j | (1 << S)];
+        x[j] = A::axpy(t, a, A::mul_mi(b));
+        x[j | (1 << S)] = A::axpy(t, b, A::mul_mi(a));
+      }
     }
   }
 }
 // several tangent-form RX on distinct slots (slot mask sm, form bits fm), one decode
+template <class A, int K, int S, class F>
+__device__ __forceinline__ void r_rxt_multi_frame(typename A::reg_t (&x)[1 << K], const typename A::mat_t* m,
+                                                  uint32_t sm, uint32_t fm, int idx, F cur) {
+  // the factor of the next rotation is loaded before this one computes
+  if constexpr (S < K) {
+    if (sm & (1u << S)) {
+      const bool more = (sm >> (S + 1)) != 0u;
+      F nxt = cur;
+      if (more) nxt = A::ld_real(m + idx + 1);
+      r_rxt_frame<A, K, S>(x, cur, (fm >> S) & 1u);
+      r_rxt_multi_frame<A, K, S + 1>(x, m, sm, fm, idx + 1, nxt);
+    } else {
+      r_rxt_multi_frame<A, K, S + 1>(x, m, sm, fm, idx, cur);
+    }
+  }
+}
 template <class A, int K>
 __device__ __forceinline__ void r_rxt_multi(typename A::reg_t (&x)[1 << K], const typename A::mat_t* m, uint32_t sm,
                                             uint32_t fm) {
+
   int idx = 0;
   if constexpr (K > 0) if (sm & 1u) { r_rxt<A, K, 0>(x, m + idx, fm & 1u); idx++; }
   if constexpr (K > 1) if (sm & 2u) { r_rxt<A, K, (K > 1 ? 1 : 0)>(x, m + idx, (fm >> 1) & 1u); idx++; }
@@ -346,8 +413,13 @@ __device__ __forceinline__ void r_x(typename A::reg_t (&x)[1 << K], const typena
     if (j & (1 << S)) continue;
     if ((j & csl) != csl) continue;
     const typename A::reg_t a = x[j];
-    x[j] = x[j | (1 << S)];
-    x[j | (1 << S)] = a;
+    if constexpr (A::kFrame) {   // [[0, i], [-i, 0]] in the phase frame
+      x[j] = A::rot_q(x[j | (1 << S)], 3u);
+      x[j | (1 << S)] = A::rot_q(a, 1u);
+    } else {
+      x[j] = x[j | (1 << S)];
+      x[j | (1 << S)] = a;
+    }
   }
 }
 
@@ -364,9 +436,9 @@ __device__ __forceinline__ void r_u2(typename A::reg_t (&x)[1 << K], const typen
     R y[4];
 #pragma unroll
     for (int r = 0; r < 4; r++) {
-      R acc = A::mac2(m[4 * r + 0], x0, m[4 * r + 1], x1);
-      acc = A::mac(acc, m[4 * r + 2], x2);
-      y[r] = A::mac(acc, m[4 * r + 3], x3);
+      R acc = A::mac2(A::ld(m + 4 * r + 0), x0, A::ld(m + 4 * r + 1), x1);
+      acc = A::mac(acc, A::ld(m + 4 * r + 2), x2);
+      y[r] = A::mac(acc, A::ld(m + 4 * r + 3), x3);
     }
     x[i0] = y[0];
     x[i1] = y[1];
@@ -413,7 +485,7 @@ __device__ __forceinline__ void r_dtab(typename A::reg_t (&x)[1 << K], const typ
   } else {
 #pragma unroll
     for (int j = 0; j < (1 << K); j++)
-      if ((csl >> j) & 1u) x[j] = A::mul(m[j], x[j]);
+      if ((csl >> j) & 1u) x[j] = A::mul(A::ld(m + j), x[j]);
   }
 }
 
@@ -492,6 +564,19 @@ __device__ __forceinline__ RegOp load_regop(const RegOp* p) {
   return r;
 }
 
+// Phase frame of the double-float policy: tile element i is held as (-i)^popcount(i) times
+// its value while the tile is in register format.
+template <class A>
+__device__ __forceinline__ typename A::reg_t to_frame(typename A::reg_t v, uint32_t i) {
+  if constexpr (A::kFrame) return A::rot_q(v, __popc(i) & 3u);
+  else return v;
+}
+template <class A>
+__device__ __forceinline__ typename A::reg_t from_frame(typename A::reg_t v, uint32_t i) {
+  if constexpr (A::kFrame) return A::rot_q(v, (0u - (uint32_t)__popc(i)) & 3u);
+  else return v;
+}
+
 // One register stage over the whole tile.  from_store / to_store: the shared-memory tile
 // holds storage-format elements before / after the stage (policies whose register format
 // differs from the storage format convert here instead of in a separate pass).
@@ -512,6 +597,7 @@ __device__ __forceinline__ void run_reg_stage(typename A::reg_t* T, const StageR
   for (uint32_t g = threadIdx.x; g < ngroups; g += kTileThreads) {
     const uint32_t gidx = pdep32(g, omask);
     const uint32_t gpos = px(gidx);
+    const uint32_t wg = __popc(gidx);   // phase frame: element j carries (-i)^(wg + popcount j)
     R x[1 << K];
 #pragma unroll
     for (int j = 0; j < (1 << K); j++) {
@@ -521,6 +607,8 @@ __device__ __forceinline__ void run_reg_stage(typename A::reg_t* T, const StageR
         if ((j >> b) & 1) p += pb[b];
       if constexpr (std::is_same<R, S>::value) {
         x[j] = T[p];
+      } else if constexpr (A::kFrame) {
+        x[j] = from_store ? A::rot_q(A::from_store(reinterpret_cast<const S*>(T)[p]), (wg + __popc(j)) & 3u) : T[p];
       } else {
         x[j] = from_store ? A::from_store(reinterpret_cast<const S*>(T)[p]) : T[p];
       }
@@ -550,6 +638,9 @@ __device__ __forceinline__ void run_reg_stage(typename A::reg_t* T, const StageR
         if ((j >> b) & 1) p += pb[b];
       if constexpr (std::is_same<R, S>::value) {
         T[p] = x[j];
+      } else if constexpr (A::kFrame) {
+        if (to_store) reinterpret_cast<S*>(T)[p] = A::to_store(A::rot_q(x[j], (0u - (wg + __popc(j))) & 3u));
+        else T[p] = x[j];
       } else {
         if (to_store) reinterpret_cast<S*>(T)[p] = A::to_store(x[j]);
         else T[p] = x[j];
@@ -613,7 +704,7 @@ __device__ __forceinline__ bool process_block(typename A::store_t* __restrict__ 
     } else {
       if (kConv && in_store) {
         S* Ts = reinterpret_cast<S*>(T);
-        for (uint32_t i = tid; i < nelem; i += kTileThreads) T[px(i)] = A::from_store(Ts[px(i)]);
+        for (uint32_t i = tid; i < nelem; i += kTileThreads) T[px(i)] = to_frame<A>(A::from_store(Ts[px(i)]), i);
         __syncthreads();
       }
       in_store = false;
@@ -630,7 +721,7 @@ __device__ __forceinline__ bool process_block(typename A::store_t* __restrict__ 
     S* Ts = reinterpret_cast<S*>(T);
     for (uint32_t i = tid; i < nelem; i += kTileThreads) {
       const R v = T[px(i)];
-      Ts[px(i)] = A::to_store(v);
+      Ts[px(i)] = A::to_store(from_frame<A>(v, i));
     }
   }
   // ---- store: bulk copies back; the tile is reused only after they have been read

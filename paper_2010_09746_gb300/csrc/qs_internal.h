@@ -174,7 +174,7 @@ struct Pool {
     return (int)(f64.size() / 2 - 1);
   }
   size_t entries() const { return f64.size() / 2; }
-  // serialised for a policy: F32 -> float2, F64 -> double2, DF -> float4 (hi, lo, hi, lo)
+  // serialised for a policy: F32 -> float2, F64 -> double2, DF -> 48-byte lane patterns
   std::vector<unsigned char> serialise(Policy pol) const;
 };
 

@@ -312,6 +312,69 @@ void merge_rxt_runs(CompileResult* out, int st0, int nst) {
   out->reg_ops.insert(out->reg_ops.end(), rebuilt.begin(), rebuilt.end());
 }
 
+// The double-float tile kernels hold tile element i as (-i)^popcount(i) times its value
+// (S^dagger on every tile bit; in that frame RX is a real rotation).  The general matrices
+// of a pass move into the frame here: entry (r, c) of a gate on k tile bits (r, c indices
+// over those bits) gets the factor (-i)^(popcount r - popcount c); controls cancel, rows
+// and columns share them.  Full-form RX keeps its own kernel form, the real rotation
+// [[c, s], [-s, c]], and gets c and s as two real entries; tangent-form RX, X (the kernel
+// applies [[0, i], [-i, 0]]), SWAP and diagonal ops are unchanged.
+namespace {
+
+void times_mi_pow(Pool& pool, int entry, int e) {
+  double& re = pool.f64[2 * (size_t)entry];
+  double& im = pool.f64[2 * (size_t)entry + 1];
+  const double a = re, b = im;
+  switch (((e % 4) + 4) % 4) {
+    case 1: re = b; im = -a; break;    // (-i)(a + ib) = b - ia
+    case 2: re = -a; im = -b; break;
+    case 3: re = -b; im = a; break;    // i(a + ib) = -b + ia
+    default: break;
+  }
+}
+
+void frame_block(Pool& pool, int mat, int k) {
+  const int D = 1 << k;
+  for (int r = 0; r < D; r++)
+    for (int c = 0; c < D; c++) times_mi_pow(pool, mat + r * D + c, __builtin_popcount(r) - __builtin_popcount(c));
+}
+
+int split_rx(Pool& pool, int mat) {
+  const double c = pool.f64[2 * (size_t)mat], sn = pool.f64[2 * (size_t)mat + 1];
+  const int m = pool.add(cd(c, 0));
+  pool.add(cd(sn, 0));
+  return m;
+}
+
+}  // namespace
+
+void apply_phase_frame(CompileResult* out, int st0, int nst) {
+  for (int k = st0; k < st0 + nst; k++) {
+    const StageRec& st = out->stages[k];
+    for (int i = st.op0; i < st.op0 + st.nops; i++) {
+      int32_t* mat;
+      int type, nk = 0;
+      if (st.kind == 1) {
+        DevOp& o = out->tile_ops[i];
+        mat = &o.mat;
+        type = o.type;
+        nk = o.nk;
+      } else {
+        RegOp& r = out->reg_ops[i];
+        mat = &r.mat;
+        type = r.type;
+      }
+      switch (type) {
+        case OP_U1: frame_block(out->pool, *mat, 1); break;
+        case OP_U2: frame_block(out->pool, *mat, 2); break;
+        case OP_DENSE: frame_block(out->pool, *mat, nk); break;
+        case OP_RX: *mat = split_rx(out->pool, *mat); break;
+        default: break;
+      }
+    }
+  }
+}
+
 int register_bits(int dtype, int L, int requested) {
   const int kmax = (dtype == QS_C128) ? 4 : 5;
   const int k = (requested > 0) ? std::min(requested, kmax) : kmax;
@@ -551,6 +614,7 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
   *nst = (int)out->stages.size() - *st0;
   fold_pass_factors(out, *st0, *nst, K);
   merge_rxt_runs(out, *st0, *nst);
+  if (out->pol == POL_DF) apply_phase_frame(out, *st0, *nst);
 }
 
 }  // namespace qs
