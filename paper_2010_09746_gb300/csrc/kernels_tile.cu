@@ -378,22 +378,6 @@ __device__ __forceinline__ void r_rxt(typename A::reg_t (&x)[1 << K], const type
   }
 }
 // several tangent-form RX on distinct slots (slot mask sm, form bits fm), one decode
-template <class A, int K, int S, class F>
-__device__ __forceinline__ void r_rxt_multi_frame(typename A::reg_t (&x)[1 << K], const typename A::mat_t* m,
-                                                  uint32_t sm, uint32_t fm, int idx, F cur) {
-  // the factor of the next rotation is loaded before this one computes
-  if constexpr (S < K) {
-    if (sm & (1u << S)) {
-      const bool more = (sm >> (S + 1)) != 0u;
-      F nxt = cur;
-      if (more) nxt = A::ld_real(m + idx + 1);
-      r_rxt_frame<A, K, S>(x, cur, (fm >> S) & 1u);
-      r_rxt_multi_frame<A, K, S + 1>(x, m, sm, fm, idx + 1, nxt);
-    } else {
-      r_rxt_multi_frame<A, K, S + 1>(x, m, sm, fm, idx, cur);
-    }
-  }
-}
 template <class A, int K>
 __device__ __forceinline__ void r_rxt_multi(typename A::reg_t (&x)[1 << K], const typename A::mat_t* m, uint32_t sm,
                                             uint32_t fm) {
