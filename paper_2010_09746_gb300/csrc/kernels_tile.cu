@@ -381,7 +381,6 @@ __device__ __forceinline__ void r_rxt(typename A::reg_t (&x)[1 << K], const type
 template <class A, int K>
 __device__ __forceinline__ void r_rxt_multi(typename A::reg_t (&x)[1 << K], const typename A::mat_t* m, uint32_t sm,
                                             uint32_t fm) {
-
   int idx = 0;
   if constexpr (K > 0) if (sm & 1u) { r_rxt<A, K, 0>(x, m + idx, fm & 1u); idx++; }
   if constexpr (K > 1) if (sm & 2u) { r_rxt<A, K, (K > 1 ? 1 : 0)>(x, m + idx, (fm >> 1) & 1u); idx++; }
