@@ -170,15 +170,16 @@ def roofline(kstats, steps, step_ms, peaks, peaks_kind, policy, clk_mhz):
            "ms_per_launch": round(per_launch_ms, 4), "share_of_step": round(dom["total_ms"] / steps / step_ms, 4),
            "hbm": {"achieved": round(hbm, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                    "frac": round(hbm / peaks["hbm_gbs"], 4), "peak_source": f"{peaks_kind} hbm_gbs"}}
-    # ALU roofline: instructions the arithmetic's formulas need / time, against the
-    # pipe's issue rate at the maximum SM clock
+    # ALU roofline: FP32 lane operations the arithmetic's formulas need / time (a packed
+    # f32x2 instruction counts as two), against the FMA pipe's 128 lanes per SM per clock at
+    # the maximum SM clock
     f = 2070.0
     if policy == "f64":
         peak_alu = N_SM * FP64_PER_CLK * f * 1e6 / 1e12
         unit = "T DFMA/s"
     else:
         peak_alu = N_SM * FP32_LANES * f * 1e6 / 1e12
-        unit = "T FP32-inst/s"
+        unit = "T FP32 lane-ops/s"
     alu = alu_pl / (per_launch_ms * 1e-3) / 1e12
     out["alu"] = {"achieved": round(alu, 3), "peak": round(peak_alu, 2), "unit": unit,
                   "frac": round(alu / peak_alu, 4),
