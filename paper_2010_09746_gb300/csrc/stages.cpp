@@ -255,7 +255,8 @@ void fold_pass_factors(CompileResult* out, int st0, int nst, int K) {
 }
 
 // Runs of tangent-form RX on distinct register slots (they commute) become one op: one
-// decode for up to K rotations.  Rebuilds the pass's register-op range in place.
+// decode for up to K rotations.  A single rotation becomes such an op too, since the merged
+// op has the kernels' fast path.  Rebuilds the pass's register-op range in place.
 void merge_rxt_runs(CompileResult* out, int st0, int nst) {
   int first = -1;
   for (int k = st0; k < st0 + nst; k++)
@@ -282,11 +283,6 @@ void merge_rxt_runs(CompileResult* out, int st0, int nst) {
       while (e < st.op0 + st.nops && out->reg_ops[e].type == OP_RXT && !((slots >> out->reg_ops[e].s0) & 1u)) {
         slots |= 1u << out->reg_ops[e].s0;
         e++;
-      }
-      if (e - i == 1) {
-        rebuilt.push_back(r);
-        i++;
-        continue;
       }
       RegOp m;
       memset(&m, 0, sizeof(m));
