@@ -1,0 +1,165 @@
+"""Compiled plans executed on the host, against the FP64 oracle (no GPU).
+
+`plan_emulator_host.cpp` compiles a circuit with the library's own host compiler (the
+same make_hgate / compile_circuit the C ABI calls). It then runs every step in
+complex<double> with the kernels' op semantics: tile passes with their register stages,
+phase tables, merged tangent-form RX and, for complex128 double-float plans, the S-dagger
+phase frame; per-gate steps; permutations; renormalisations. Any scheduling, lowering,
+table, folding or frame mistake gives an O(1) error. The emulation's own rounding is
+~1e-15, so the bound is 1e-10. The GPU parity tests run the same compiled plans on the
+kernels.
+"""
+import os
+import shutil
+import struct
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import sv
+from workloads import circuits as wc
+
+qs = pytest.importorskip("paper_2010_09746_gb300")
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_2010_09746_gb300", "csrc")
+TOL = 1e-10
+
+
+def _nvcc():
+    for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", shutil.which("nvcc")):
+        if cand and os.path.exists(cand):
+            return cand
+    return None
+
+
+@pytest.fixture(scope="module")
+def emulator(tmp_path_factory):
+    nvcc = _nvcc()
+    if nvcc is None:
+        pytest.skip("nvcc not available")
+    d = tmp_path_factory.mktemp("emu")
+    exe = str(d / "plan_emulator_host")
+    srcs = [os.path.join(HERE, "plan_emulator_host.cpp")] + \
+        [os.path.join(CSRC, f) for f in ("gates.cpp", "compiler.cpp", "stages.cpp")]
+    r = subprocess.run([nvcc, "-std=c++17", "-O2", "-o", exe] + srcs, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-3000:]
+
+    def run(n, circ, **opts):
+        ops, nops, mats = qs.marshal(circ)
+        o = qs._opts(**opts)
+        inp, out = str(d / "in.bin"), str(d / "out.bin")
+        with open(inp, "wb") as f:
+            f.write(struct.pack("<iiq", n, nops, mats.size if nops else 0))
+            f.write(bytes(o))
+            f.write(bytes(ops)[: nops * 48])
+            if nops:
+                f.write(np.ascontiguousarray(mats, dtype=np.float64).tobytes())
+        r = subprocess.run([exe, inp, out], capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-3000:]
+        with open(out, "rb") as f:
+            n2, nsteps = struct.unpack("<ii", f.read(8))
+            sigma = np.frombuffer(f.read(4 * n2), dtype=np.int32)
+            psi = np.frombuffer(f.read(), dtype=np.complex128)
+        assert n2 == n and psi.size == 1 << n
+        # logical index i sits at storage index sum_q bit_q(i) << sigma[q]
+        idx = np.zeros(1 << n, dtype=np.int64)
+        ar = np.arange(1 << n, dtype=np.int64)
+        for q in range(n):
+            idx |= ((ar >> q) & 1) << int(sigma[q])
+        return psi[idx], nsteps
+
+    return run
+
+
+def check(got, circ, n):
+    ref = sv.simulate(n, circ)
+    err = float(np.max(np.abs(got - ref)))
+    assert err <= TOL, f"max amplitude error {err:.3e}"
+
+
+MODES = [("c128", "df"), ("c128", "f64"), ("c64", "auto")]
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+@pytest.mark.parametrize("n,L,c", [(6, 4, 1), (9, 6, 2), (12, 8, 3), (12, 10, 3), (13, 12, 3)])
+def test_tile_mode_random_circuits(emulator, dtype, arith, n, L, c):
+    circ = wc.random_mixed_circuit(n, 150, seed=n * 31 + L, kmax=min(4, L - c))
+    got, _ = emulator(n, circ, mode="tile", dtype=dtype, arith=arith, tile_bits=L, low_bits=c)
+    check(got, circ, n)
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+@pytest.mark.parametrize("K", [1, 2, 3, 4, 5])
+def test_tile_mode_every_register_width(emulator, dtype, arith, K):
+    if dtype == "c128" and K > 4:
+        pytest.skip("complex128 holds at most 4 register bits")
+    n = 12
+    circ = wc.random_mixed_circuit(n, 160, seed=100 + K, kmax=3) + wc.rzrx_cz_circuit(n, 6, seed=K)
+    got, _ = emulator(n, circ, mode="tile", dtype=dtype, arith=arith, tile_bits=10, reg_bits=K)
+    check(got, circ, n)
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+@pytest.mark.parametrize("full_rx", [False, True])
+def test_rzrx_cz_construction(emulator, dtype, arith, full_rx):
+    """The 30-qubit workload's construction: tangent-form RX runs (both forms), phase tables
+    with masks, the pass-level factor folded into the first table, CZ sign flips."""
+    n = 14
+    circ = wc.rzrx_cz_circuit(n, 24, seed=3)
+    got, nsteps = emulator(n, circ, mode="tile", dtype=dtype, arith=arith, tile_bits=10, full_rx=full_rx)
+    assert nsteps > 1
+    check(got, circ, n)
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+@pytest.mark.parametrize("n,m", [(10, 6), (12, 8)])
+def test_paper_mode(emulator, dtype, arith, n, m):
+    circ = wc.paper_random_circuit(n, 0.3, seed=n) + wc.rzrx_cz_circuit(n, 3, seed=n)
+    got, _ = emulator(n, circ, mode="paper", dtype=dtype, arith=arith, tile_bits=m)
+    check(got, circ, n)
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+def test_pergate_mode(emulator, dtype, arith):
+    n = 9
+    circ = wc.random_mixed_circuit(n, 120, seed=9, kmax=4)
+    got, _ = emulator(n, circ, mode="pergate", dtype=dtype, arith=arith)
+    check(got, circ, n)
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+def test_controlled_diagonals_in_phase_tables(emulator, dtype, arith):
+    n = 12
+    rng = np.random.default_rng(5)
+    circ = []
+    for layer in range(6):
+        for q in range(n):
+            circ.append(wc.Gate("RX", (q,), param=float(rng.uniform(0, 2 * np.pi))))
+        for _ in range(n):
+            cq, t = (int(x) for x in rng.choice(n, 2, replace=False))
+            a, b = rng.uniform(0, 2 * np.pi, 2)
+            circ.append(wc.Gate("CU", (cq, t), matrix=np.diag([np.exp(1j * a), np.exp(1j * b)])))
+    got, _ = emulator(n, circ, mode="tile", dtype=dtype, arith=arith, tile_bits=10)
+    check(got, circ, n)
+
+
+def test_periodic_renormalisation(emulator):
+    n = 10
+    circ = wc.rzrx_cz_circuit(n, 8, seed=4)
+    got, _ = emulator(n, circ, mode="tile", dtype="c64", tile_bits=8, renorm_every=2)
+    check(got, circ, n)
+
+
+def test_emulator_sees_a_planted_mistake(emulator):
+    """The check has teeth: the same plan against a circuit with one angle changed fails."""
+    n = 10
+    circ = wc.rzrx_cz_circuit(n, 6, seed=8)
+    got, _ = emulator(n, circ, mode="tile", dtype="c128", tile_bits=8)
+    wrong = list(circ)
+    g = wrong[17]
+    wrong[17] = wc.Gate(g.kind, tuple(g.qubits), param=float(g.param) + 1e-3)
+    ref_wrong = sv.simulate(n, wrong)
+    assert float(np.max(np.abs(got - ref_wrong))) > 1e-6
