@@ -559,20 +559,8 @@ qs_status qs_compile(int n, const qs_op* ops, size_t nops, const double* mats, s
   o.mode = QS_MODE_TILE;
   o.dtype = QS_C128;
   if (opts) o = *opts;
-  if (o.dtype != QS_C64 && o.dtype != QS_C128) return fail(QS_EINVAL, "unknown dtype");
-  if (o.mode < QS_MODE_PERGATE || o.mode > QS_MODE_TILE) return fail(QS_EINVAL, "unknown mode");
-  if (o.flags & ~QS_FLAG_FULL_RX) return fail(QS_EINVAL, "unknown flags");
-  if (o.reg_bits < 0 || o.reg_bits > 5) return fail(QS_EINVAL, "reg_bits must be in [0, 5]");
-  if (o.renorm_every < 0) return fail(QS_EINVAL, "renorm_every must be >= 0");
-  if (o.tile_bits == 0) o.tile_bits = default_tile_bits(o.dtype);
-  if (o.low_bits == 0) o.low_bits = default_low_bits(o.dtype);
-  if (o.tile_bits < 1 || (o.mode != QS_MODE_PAPER && o.tile_bits > kMaxTileBits))
-    return fail(QS_EINVAL, "tile_bits must be in [1, 14] (QS_MODE_PAPER: [1, n])");
-  if (o.tile_bits > n) o.tile_bits = n;
-  if (o.low_bits > o.tile_bits) o.low_bits = o.tile_bits;
-  const int min_low = (o.dtype == QS_C64) ? 1 : 0;   // 16-byte bulk copies
-  if (o.low_bits < min_low) o.low_bits = min_low;
-  if (o.low_bits > o.tile_bits) return fail(QS_EINVAL, "state too small for a tile pass");
+  std::string err;
+  if (!normalize_compile_opts(n, &o, &err)) return fail(QS_EINVAL, err);
   std::vector<int> s0(n);
   if (sigma0) {
     if (!valid_perm(n, sigma0)) return fail(QS_EINVAL, "sigma0 is not a permutation");
@@ -581,7 +569,6 @@ qs_status qs_compile(int n, const qs_op* ops, size_t nops, const double* mats, s
     for (int q = 0; q < n; q++) s0[q] = q;
   }
   std::vector<HGate> gates(nops);
-  std::string err;
   for (size_t i = 0; i < nops; i++)
     if (!make_hgate(n, ops[i], mats, nmats, &gates[i], &err)) return fail(QS_EINVAL, "op " + std::to_string(i) + ": " + err);
   qs_plan* p = new qs_plan();

@@ -20,6 +20,28 @@ namespace qs {
 int default_tile_bits(int dtype) { return dtype == QS_C128 ? 12 : 13; }
 int default_low_bits(int dtype) { return dtype == QS_C128 ? 3 : 4; }
 
+bool normalize_compile_opts(int n, qs_compile_opts* o, std::string* err) {
+  auto bad = [&](const char* m) {
+    *err = m;
+    return false;
+  };
+  if (o->dtype != QS_C64 && o->dtype != QS_C128) return bad("unknown dtype");
+  if (o->mode < QS_MODE_PERGATE || o->mode > QS_MODE_TILE) return bad("unknown mode");
+  if (o->flags & ~QS_FLAG_FULL_RX) return bad("unknown flags");
+  if (o->reg_bits < 0 || o->reg_bits > 5) return bad("reg_bits must be in [0, 5]");
+  if (o->renorm_every < 0) return bad("renorm_every must be >= 0");
+  if (o->tile_bits == 0) o->tile_bits = default_tile_bits(o->dtype);
+  if (o->low_bits == 0) o->low_bits = default_low_bits(o->dtype);
+  if (o->tile_bits < 1 || (o->mode != QS_MODE_PAPER && o->tile_bits > kMaxTileBits))
+    return bad("tile_bits must be in [1, 14] (QS_MODE_PAPER: [1, n])");
+  if (o->tile_bits > n) o->tile_bits = n;
+  if (o->low_bits > o->tile_bits) o->low_bits = o->tile_bits;
+  const int min_low = (o->dtype == QS_C64) ? 1 : 0;   // 16-byte bulk copies
+  if (o->low_bits < min_low) o->low_bits = min_low;
+  if (o->low_bits > o->tile_bits) return bad("state too small for a tile pass");
+  return true;
+}
+
 // Gate j depends on an earlier gate i iff they share a qubit on which their action
 // classes differ (classes Z and X each commute with themselves, N with nothing).  Per
 // qubit, consecutive gates of one commuting class form a group; a gate's immediate

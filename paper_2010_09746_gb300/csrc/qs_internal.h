@@ -217,6 +217,9 @@ void set_last_error(const std::string& msg);
 
 int default_tile_bits(int dtype);
 int default_low_bits(int dtype);
+// Validate compile options and fill in the defaults (tile and low bits for the dtype,
+// clamped to the state); false with a message if they are invalid.
+bool normalize_compile_opts(int n, qs_compile_opts* o, std::string* err);
 int register_bits(int dtype, int L, int requested);
 
 // Split a pass's op list (tile-local DevOps, program order) into register / shared-memory

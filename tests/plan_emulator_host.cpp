@@ -318,8 +318,12 @@ int main(int argc, char** argv) {
     fprintf(stderr, "bad input\n");
     return 2;
   }
-  std::vector<HGate> gates(nops);
   std::string err;
+  if (!normalize_compile_opts(n, &o, &err)) {   // as qs_compile does
+    fprintf(stderr, "options: %s\n", err.c_str());
+    return 4;
+  }
+  std::vector<HGate> gates(nops);
   for (int i = 0; i < nops; i++)
     if (!make_hgate(n, ops[i], mats.data(), (size_t)nmats, &gates[i], &err)) {
       fprintf(stderr, "gate %d: %s\n", i, err.c_str());

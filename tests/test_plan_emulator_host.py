@@ -146,6 +146,15 @@ def test_controlled_diagonals_in_phase_tables(emulator, dtype, arith):
     check(got, circ, n)
 
 
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_default_options(emulator, dtype):
+    """Default tile / low / register bits, as qs_compile fills them in."""
+    n = 14
+    circ = wc.rzrx_cz_circuit(n, 10, seed=21) + wc.random_mixed_circuit(n, 60, seed=21, kmax=3)
+    got, _ = emulator(n, circ, dtype=dtype)
+    check(got, circ, n)
+
+
 def test_periodic_renormalisation(emulator):
     n = 10
     circ = wc.rzrx_cz_circuit(n, 8, seed=4)
