@@ -306,7 +306,7 @@ def run_ours(args):
         "config": {"workload": name, "seeds": list(range(args.seed, args.seed + len(circs))),
                    "passes_per_seed": [p.stats()["n_passes"] for p in plans],
                    "n_qubits": n, "gates": G, "mode": args.mode, "state_dtype": args.dtype,
-                   "arith": {"df": "double-float (pairs of f32), f64 storage", "f32": "f32", "f64": "f64"}[policy],
+                   "arith": {"df": "double-float (pairs of f32) on packed f32x2 lanes, f64 storage", "f32": "f32", "f64": "f64"}[policy],
                    "tile_bits": args.tile_bits or None, "low_bits": args.low_bits or None,
                    "reg_bits": args.reg_bits or None,
                    "passes": pstats["n_passes"], "permutes": pstats["n_permutes"], "pergate": pstats["n_pergate"],
