@@ -155,6 +155,17 @@ def test_default_options(emulator, dtype):
     check(got, circ, n)
 
 
+@pytest.mark.parametrize("mode", ["tile", "paper", "pergate"])
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_appendix_c_and_config1_circuits(emulator, mode, dtype):
+    """The QFT-like circuit of Appendix C (controlled phases, Hadamards) and 12-qubit
+    Haar + CNOT layers, in every mode."""
+    kw = {"tile_bits": 8} if mode == "paper" else {}
+    for n, circ in ((11, wc.qft_like_circuit(11)), (11, wc.qft_circuit(11)), (12, wc.haar_cnot_circuit(12, 8, 2))):
+        got, _ = emulator(n, circ, mode=mode, dtype=dtype, **kw)
+        check(got, circ, n)
+
+
 def test_periodic_renormalisation(emulator):
     n = 10
     circ = wc.rzrx_cz_circuit(n, 8, seed=4)
