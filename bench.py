@@ -35,9 +35,30 @@ sys.path.insert(0, ROOT)
 from workloads import circuits as wc  # noqa: E402
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-N_SM = 152
-FP32_LANES = 128        # FP32 FMA-pipe instructions per clock per SM
-FP64_PER_CLK = 1.7      # DFMA per clock per SM, measured (probe of this machine's GB300)
+FP32_LANES = 128        # FP32 FMA-pipe lanes per SM (4 partitions x 32)
+FP64_PER_CLK = 1.7      # DFMA per clock per SM on GB300, measured with a register-resident probe
+
+
+def device_info(dev, clk):
+    """SM count from the device properties; SM clock: the maximum nvidia-smi reported during
+    the timed region, else the measured one."""
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    peaks, _ = load_peaks()
+    mhz = clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    return {"sms": int(props.multi_processor_count), "sm_max_mhz": float(mhz), "name": props.name}
+
+
+# FP64 floating-point operations per amplitude that each gate needs as the method writes it
+# (complex 2x2 on an amplitude pair: 2 complex multiplies + 1 add = 14 per amplitude; a
+# diagonal phase: 1 complex multiply = 6; sign flips and swaps: 0; a control halves the
+# amplitudes touched; a general 4x4: 4 multiplies + 3 adds = 30 per amplitude).
+METHOD_FLOPS = {"U1": 14, "H": 14, "RX": 14, "RY": 14, "Y": 0, "X": 0, "Z": 0, "RZ": 6, "P": 6 / 2, "S": 6 / 2,
+                "T": 6 / 2, "CZ": 0, "CNOT": 0, "CP": 6 / 4, "CU": 14 / 2, "SWAP": 0, "U2": 30}
+
+
+def method_flops(circ, n):
+    return sum(METHOD_FLOPS[g.kind] for g in circ) * float(1 << n)
 
 
 def load_peaks():
@@ -158,36 +179,46 @@ def profiled_traffic(kernel_name, n):
     return float(m_b.group(1)) * 2.0 ** (n - int(m_b.group(2)))
 
 
-def roofline(kstats, steps, step_ms, peaks, peaks_kind, policy, clk_mhz):
+def roofline(kstats, steps, step_ms, peaks, peaks_kind, policy, dev, circ_flops):
+    """Roofline of the dominant kernel (the most device time per step).
+
+    bound / frac: the HBM fraction -- algorithmic bytes per launch (2 S for a tile pass: the
+    state read and written once) over the launch's CUDA-event time, against the measured copy
+    bandwidth.  `method_alu`: the FP64 flops the circuit's gates need (METHOD_FLOPS; all of the
+    circuit's arithmetic runs in this kernel, split evenly over its launches) per second,
+    against the native FP64 pipe.  `fma_pipe`: a diagnostic, not the method's work -- the
+    lane operations the arithmetic's own formulas issue (for complex128 that is the
+    double-float emulation), against the FP32 FMA lanes at the maximum clock."""
     if not kstats:
         return None
     dom = max(kstats, key=lambda k: k["total_ms"])
     per_launch_ms = dom["total_ms"] / dom["launches"]
+    launches_per_step = dom["launches"] / steps
     bytes_pl = dom["bytes"] / dom["launches"]
     alu_pl = dom["alu"] / dom["launches"]
     hbm = bytes_pl / (per_launch_ms * 1e-3) / 1e9
-    out = {"kernel": dom["name"], "launches_per_step": dom["launches"] / steps,
+    clk = dev["sm_max_mhz"] * 1e6
+    out = {"kernel": dom["name"], "launches_per_step": launches_per_step,
            "ms_per_launch": round(per_launch_ms, 4), "share_of_step": round(dom["total_ms"] / steps / step_ms, 4),
-           "hbm": {"achieved": round(hbm, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                   "frac": round(hbm / peaks["hbm_gbs"], 4), "peak_source": f"{peaks_kind} hbm_gbs"}}
-    # ALU roofline: FP32 lane operations the arithmetic's formulas need / time (a packed
-    # f32x2 instruction counts as two), against the FMA pipe's 128 lanes per SM per clock at
-    # the maximum SM clock
-    f = 2070.0
-    if policy == "f64":
-        peak_alu = N_SM * FP64_PER_CLK * f * 1e6 / 1e12
-        unit = "T DFMA/s"
-    else:
-        peak_alu = N_SM * FP32_LANES * f * 1e6 / 1e12
-        unit = "T FP32 lane-ops/s"
+           "bound": "hbm", "achieved": round(hbm, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": round(hbm / peaks["hbm_gbs"], 4), "peak_source": f"{peaks_kind} hbm_gbs (copy)",
+           "traffic": None, "algorithmic_bytes": bytes_pl}
+    if circ_flops and dom["name"].startswith("tile_pass"):
+        fl = circ_flops / launches_per_step
+        fp64_peak = dev["sms"] * FP64_PER_CLK * 2 * clk / 1e12
+        ach = fl / (per_launch_ms * 1e-3) / 1e12
+        out["method_alu"] = {"fp64_flops_per_launch": fl, "achieved_tflops": round(ach, 3),
+                             "fp64_pipe_peak_tflops": round(fp64_peak, 3), "frac_of_fp64_pipe": round(ach / fp64_peak, 3),
+                             "peak_source": f"{dev['sms']} SMs x {FP64_PER_CLK} DFMA/clk (measured) x 2 x "
+                                            f"{dev['sm_max_mhz']:.0f} MHz"}
+    lanes = FP64_PER_CLK if policy == "f64" else FP32_LANES
+    peak_alu = dev["sms"] * lanes * clk / 1e12
     alu = alu_pl / (per_launch_ms * 1e-3) / 1e12
-    out["alu"] = {"achieved": round(alu, 3), "peak": round(peak_alu, 2), "unit": unit,
-                  "frac": round(alu / peak_alu, 4),
-                  "peak_source": f"{N_SM} SMs x {FP32_LANES if policy != 'f64' else FP64_PER_CLK}/clk x 2070 MHz"}
-    bound = "alu" if out["alu"]["frac"] > out["hbm"]["frac"] else "hbm"
-    sel = out[bound]
-    out.update({"bound": bound, "achieved": sel["achieved"], "peak": sel["peak"], "unit": sel["unit"],
-                "frac": sel["frac"], "traffic": None, "algorithmic_bytes": bytes_pl, "algorithmic_alu": alu_pl})
+    out["fma_pipe"] = {"lane_ops_per_launch": alu_pl, "achieved": round(alu, 3), "peak": round(peak_alu, 2),
+                       "unit": "T DFMA/s" if policy == "f64" else "T FP32 lane-ops/s", "frac": round(alu / peak_alu, 4),
+                       "what": "instructions the arithmetic's formulas issue (double-float emulation for complex128): "
+                               "FMA-pipe occupancy, not the method's work",
+                       "peak_source": f"{dev['sms']} SMs x {lanes}/clk x {dev['sm_max_mhz']:.0f} MHz"}
     return out
 
 
@@ -293,7 +324,9 @@ def run_ours(args):
     value = job_rate(G, world, ms)
 
     peaks, peaks_kind = load_peaks()
-    roof = roofline(kstats, args.steps, ms, peaks, peaks_kind, policy, clk.get("sm_mhz"))
+    dev = device_info(local, clk)
+    roof = roofline(kstats, args.steps, ms, peaks, peaks_kind, policy, dev,
+                    method_flops(circ, n) if args.workload == "rzrx30" else None)
     if roof:
         roof["traffic"] = profiled_traffic(roof["kernel"], n)
     launches = int(round(sum(k["launches"] for k in kstats)))
@@ -326,7 +359,7 @@ def run_ours(args):
         readout = 1 << min(n, 16)
         d2h = readout * (16 if args.dtype == "c128" else 8) + 8
         torch.cuda.synchronize()
-        e2e_steps = max(1, min(args.steps, 3))
+        e2e_steps = max(1, args.steps if args.e2e_steps <= 0 else min(args.steps, args.e2e_steps))
         t0 = time.perf_counter()
         for k in range(e2e_steps):
             st.reset()
@@ -337,7 +370,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         t_e2e = reduce_max((time.perf_counter() - t0) / e2e_steps * 1e3, pg)
         out["e2e"] = {"value": round(job_rate(G, world, t_e2e), 2), "unit": "gates/s", "h2d_bytes_per_step": int(h2d),
-                      "d2h_bytes_per_step": int(d2h), "ms_per_step": round(t_e2e, 3)}
+                      "d2h_bytes_per_step": int(d2h), "ms_per_step": round(t_e2e, 3), "steps": e2e_steps,
+                      "what": "per step, host wall clock: the circuit's ops and matrices from host memory through "
+                              "qs_run (compile + execute), then the first %d amplitudes and the FP64 norm copied back "
+                              "to the host (not the whole %d-byte state)" % (readout, (1 << n) * (16 if args.dtype == "c128" else 8))}
 
     # ---- the same circuit without the reordering pass, and with the paper's Algorithm 1
     if args.modes and args.mode == "tile":
@@ -755,6 +791,7 @@ def main(argv=None):
     ap.add_argument("--low-bits", type=int, default=0)
     ap.add_argument("--reg-bits", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="end-to-end steps (0 = the same as --steps)")
     ap.add_argument("--modes", type=int, default=1, help="also time per-gate and Algorithm 1 modes")
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--qft", type=int, default=1, help="also time Appendix C's QFT-like circuit")

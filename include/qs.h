@@ -186,6 +186,12 @@ qs_status qs_reset_kernel_stats(qs_handle h);
 /* Re-initialise to |0...0> and sigma = identity (state preparation, Sec. 2). */
 qs_status qs_reset(qs_handle h);
 
+/* n, dtype, the device address of the amplitude vector and its size in bytes (any output
+ * may be NULL).  The address is valid until the next call that moves the vector: a
+ * permutation (qs_permute, a plan containing permutation steps, qs_apply_dense on the tensor
+ * path when it permutes first) writes into a second buffer of the same size and swaps the
+ * two.  That second buffer is allocated by the first such call and kept until qs_destroy,
+ * so a state that has permuted holds 2x `bytes` of device memory. */
 qs_status qs_get_info(qs_handle h, int* n, qs_dtype* dtype, void** device_ptr, size_t* bytes);
 qs_status qs_sync(qs_handle h);
 
@@ -239,6 +245,9 @@ qs_status qs_get_permutation(qs_handle h, int* perm_out);
  * complex128).  The plan holds copies of everything it needs, on host and device. */
 qs_status qs_compile(int n, const qs_op* ops, size_t nops, const double* mats, size_t nmats,
                      const int* sigma0, const qs_compile_opts* opts, qs_plan_t* out);
+/* Release a plan.  Never waits for the device: device buffers still needed by executions
+ * enqueued earlier are released later, once those executions have completed (checked
+ * without blocking whenever a plan is compiled or destroyed). */
 qs_status qs_plan_destroy(qs_plan_t p);
 qs_status qs_plan_get_stats(qs_plan_t p, qs_plan_stats* out);
 /* sigma after the plan has run (n ints). */
@@ -256,7 +265,7 @@ qs_status qs_plan_get_trace(qs_plan_t p, int32_t* kinds, int32_t* values, size_t
  * the permutation the plan was compiled for; afterwards sigma is the plan's final one. */
 qs_status qs_execute(qs_handle h, qs_plan_t p);
 
-/* qs_compile + qs_execute + qs_plan_destroy. */
+/* qs_compile + qs_execute + qs_plan_destroy; asynchronous like qs_execute. */
 qs_status qs_run(qs_handle h, const qs_op* ops, size_t nops, const double* mats, size_t nmats,
                  const qs_compile_opts* opts);
 
@@ -355,7 +364,8 @@ qs_status qs_renormalize(qs_handle h, double* norm_out);
  *   n        1..36; larger states are rejected with QS_EINVAL (the limit of the library)
  *   out_dev  device pointer to one double; written asynchronously on `stream`
  *   stream   cudaStream_t (NULL = the legacy default stream)
- * The first call on each device looks up the device address of the fixed array
+ * The first call on each device (and again the first after the device's context changed,
+ * e.g. after cudaDeviceReset) looks up the device address of the fixed array
  * (cudaGetSymbolAddress) with that device current; make that first call before any stream
  * capture begins.  All calls share the one array and each call overwrites all of it, so
  * calls whose kernels overlap on the GPU (different streams, no ordering) race and give

@@ -143,6 +143,17 @@ def inner(a: np.ndarray, b: np.ndarray, n: int) -> complex:
     return complex(out[0], out[1])
 
 
+def logical_index(j: np.ndarray, sigma: Sequence[int]) -> np.ndarray:
+    """Sec. 2's index map read backwards: the storage position j holds the amplitude of the
+    logical index i with i_q = bit sigma(q) of j, i.e. j = j(i, sigma) = sum_q i_q 2^sigma(q).
+    Vectorised over an array of positions (uint64)."""
+    j = np.asarray(j, dtype=np.uint64)
+    i = np.zeros_like(j)
+    for q, p in enumerate(sigma):
+        i |= ((j >> np.uint64(p)) & np.uint64(1)) << np.uint64(q)
+    return i
+
+
 def run_storage_program(n: int, program: Sequence, identity_start: bool = True) -> np.ndarray:
     """Execute a compiled instruction list in storage order and return the
     logical-order state.  Instructions: ("gate", Gate) or ("permute", sigma')."""

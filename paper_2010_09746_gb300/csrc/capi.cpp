@@ -111,6 +111,9 @@ struct qs_plan {
   void* pool_dev = nullptr;
   size_t pool_bytes = 0;
   bool uploaded = false;
+  // one event per stream the plan was executed on, recorded after its last launch there:
+  // the device buffers are released once all of them have completed
+  std::vector<std::pair<cudaStream_t, cudaEvent_t>> uses;
 };
 
 namespace {
@@ -335,6 +338,59 @@ qs_status renormalize(qs_state* h) {
   return QS_OK;
 }
 
+// Device buffers of destroyed plans whose last executions may still be running.  They are
+// released once every recorded event has completed, checked (without blocking) whenever a
+// plan is compiled or destroyed; a plan's destruction never waits for the device.
+struct DeferredFree {
+  std::vector<std::pair<void*, size_t>> bufs;
+  std::vector<cudaEvent_t> events;
+};
+std::mutex g_deferred_mu;
+std::vector<DeferredFree> g_deferred;
+
+bool events_done(const std::vector<cudaEvent_t>& evs) {
+  for (cudaEvent_t e : evs) {
+    const cudaError_t q = cudaEventQuery(e);
+    if (q == cudaErrorNotReady) return false;
+    if (q != cudaSuccess) cudaGetLastError();   // an event that failed is treated as finished
+  }
+  return true;
+}
+
+void release_deferred(DeferredFree& d) {
+  for (auto& b : d.bufs) dev_free(b.first, b.second, nullptr);
+  for (cudaEvent_t e : d.events) cudaEventDestroy(e);
+  d.bufs.clear();
+  d.events.clear();
+}
+
+void reap_deferred() {
+  std::vector<DeferredFree> ready;
+  {
+    std::lock_guard<std::mutex> lk(g_deferred_mu);
+    size_t w = 0;
+    for (size_t r = 0; r < g_deferred.size(); r++) {
+      if (events_done(g_deferred[r].events)) ready.push_back(std::move(g_deferred[r]));
+      else g_deferred[w++] = std::move(g_deferred[r]);
+    }
+    g_deferred.resize(w);
+  }
+  for (DeferredFree& d : ready) release_deferred(d);
+}
+
+// record that `p` has just been enqueued on `s`
+qs_status note_plan_use(qs_plan* p, cudaStream_t s) {
+  cudaEvent_t ev = nullptr;
+  for (auto& u : p->uses)
+    if (u.first == s) ev = u.second;
+  if (!ev) {
+    CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "plan event");
+    p->uses.push_back({s, ev});
+  }
+  CUDA_TRY(cudaEventRecord(ev, s), "plan event record");
+  return QS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -555,6 +611,7 @@ qs_status qs_compile(int n, const qs_op* ops, size_t nops, const double* mats, s
   *out = nullptr;
   if (n < 1 || n > kMaxQubits) return fail(QS_EINVAL, "n must be in [1, 36]");
   if (nops > 0 && !ops) return fail(QS_EINVAL, "null ops");
+  reap_deferred();
   qs_compile_opts o{};
   o.mode = QS_MODE_TILE;
   o.dtype = QS_C128;
@@ -587,13 +644,18 @@ qs_status qs_compile(int n, const qs_op* ops, size_t nops, const double* mats, s
 
 qs_status qs_plan_destroy(qs_plan_t p) {
   if (!p) return QS_OK;
+  reap_deferred();
+  DeferredFree d;
   if (p->uploaded) {
-    cudaDeviceSynchronize();
-    dev_free(p->ops_dev, p->ops_bytes, nullptr);
-    dev_free(p->rops_dev, p->rops_bytes, nullptr);
-    dev_free(p->stages_dev, p->stages_bytes, nullptr);
-    dev_free(p->pool_dev, p->pool_bytes, nullptr);
-    cudaDeviceSynchronize();
+    d.bufs = {{p->ops_dev, p->ops_bytes}, {p->rops_dev, p->rops_bytes}, {p->stages_dev, p->stages_bytes},
+              {p->pool_dev, p->pool_bytes}};
+  }
+  for (auto& u : p->uses) d.events.push_back(u.second);
+  if (events_done(d.events)) {
+    release_deferred(d);
+  } else {   // still in use on some stream: released by a later reap, without waiting here
+    std::lock_guard<std::mutex> lk(g_deferred_mu);
+    g_deferred.push_back(std::move(d));
   }
   delete p;
   return QS_OK;
@@ -647,15 +709,7 @@ static qs_status plan_upload(qs_plan* p) {
   return QS_OK;
 }
 
-qs_status qs_execute(qs_handle h, qs_plan_t p) {
-  if (!h || !p) return fail(QS_EINVAL, "null argument");
-  {
-    qs_status ust = plan_upload(p);
-    if (ust != QS_OK) return ust;
-  }
-  if (h->n != p->n) return fail(QS_EINVAL, "plan and state have different n");
-  if ((int)h->dtype != p->dtype) return fail(QS_EINVAL, "plan and state have different dtype");
-  if (h->sigma != p->sigma0) return fail(QS_EINVAL, "state permutation differs from the plan's start permutation");
+static qs_status execute_steps(qs_handle h, qs_plan_t p) {
   for (const Step& s : p->cr.steps) {
     const char* name = step_name(s, p->pol);
     if (s.kind == ST_PASS) {
@@ -681,6 +735,21 @@ qs_status qs_execute(qs_handle h, qs_plan_t p) {
   return QS_OK;
 }
 
+qs_status qs_execute(qs_handle h, qs_plan_t p) {
+  if (!h || !p) return fail(QS_EINVAL, "null argument");
+  {
+    qs_status ust = plan_upload(p);
+    if (ust != QS_OK) return ust;
+  }
+  if (h->n != p->n) return fail(QS_EINVAL, "plan and state have different n");
+  if ((int)h->dtype != p->dtype) return fail(QS_EINVAL, "plan and state have different dtype");
+  if (h->sigma != p->sigma0) return fail(QS_EINVAL, "state permutation differs from the plan's start permutation");
+  const qs_status st = execute_steps(h, p);
+  // whatever was enqueued keeps the plan's buffers alive until it has run
+  const qs_status su = note_plan_use(p, h->stream);
+  return st != QS_OK ? st : su;
+}
+
 qs_status qs_run(qs_handle h, const qs_op* ops, size_t nops, const double* mats, size_t nmats,
                  const qs_compile_opts* opts) {
   if (!h) return fail(QS_EINVAL, "null handle");
@@ -693,8 +762,7 @@ qs_status qs_run(qs_handle h, const qs_op* ops, size_t nops, const double* mats,
   qs_status st = qs_compile(h->n, ops, nops, mats, nmats, h->sigma.data(), &o, &p);
   if (st != QS_OK) return st;
   st = qs_execute(h, p);
-  // the plan's buffers are freed after the stream has consumed them
-  cudaStreamSynchronize(h->stream);
+  // the plan's device buffers are released once the stream has consumed them
   qs_plan_destroy(p);
   return st;
 }

@@ -42,8 +42,10 @@ __device__ __forceinline__ uint64_t expand(uint64_t t, const Expand& e) {
 int grid_for(uint64_t work) {
   int sms = 0, dev = 0;   // the current device's SM count (the runtime answers from a cache)
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      sms <= 0)
-    sms = 152;
+      sms <= 0) {
+    cudaGetLastError();
+    sms = 1;   // grid-stride loops stay correct with any grid
+  }
   uint64_t blocks = (work + kThreads - 1) / kThreads;
   uint64_t cap = (uint64_t)sms * 8;
   if (blocks > cap) blocks = cap;
@@ -355,7 +357,12 @@ __global__ void k_init_zero8(float2* psi, uint64_t N) {
 // Norm: every thread of a fixed grid accumulates a fixed strided subset in FP64, a fixed
 // shared-memory tree reduces the block, and a single block sums the per-block partials in
 // index order: the result does not depend on timing.
-constexpr int kNormBlocks = 1216;   // 152 SMs x 8
+// Determinism contract of every FP64 norm: the sum is always split into this many
+// partial sums (block b adds the grid-stride elements b, b + 1216 * threads, ...) and the
+// partials are added in index order, whatever GPU runs it, so a norm is the same bits on any
+// device and in every entry point that shares this reduction.  (1216 fills a 152-SM GB300
+// with 8 blocks per SM; on other SM counts it is still correct, only the balance differs.)
+constexpr int kNormBlocks = 1216;
 
 template <class S>
 __global__ void __launch_bounds__(kThreads) k_norm_partials(const S* __restrict__ psi, uint64_t N, double* partials) {

@@ -8,7 +8,9 @@ namespace qs {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kInnerBlocks = 1216;   // 152 SMs x 8, fixed so the summation order is fixed
+// Determinism contract of the inner product: always this many partial sums, added in
+// index order, so the result does not depend on the GPU's SM count.
+constexpr int kInnerBlocks = 1216;
 
 template <class S>
 __device__ __forceinline__ double2 load_d(const S* p, uint64_t i) {
@@ -95,7 +97,13 @@ __global__ void __launch_bounds__(kThreads) k_scale8(float4* psi2, uint64_t N2, 
 unsigned grid_stream(uint64_t items) {
   const uint64_t per = (uint64_t)kThreads * 4;
   uint64_t g = (items + per - 1) / per;
-  const uint64_t cap = 152ull * 8 * 4;
+  int sms = 0, dev = 0;   // the current device's SM count (the runtime answers from a cache)
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms <= 0) {
+    cudaGetLastError();
+    sms = 1;   // grid-stride loops stay correct with any grid
+  }
+  const uint64_t cap = (uint64_t)sms * 8 * 4;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (unsigned)g;

@@ -15,7 +15,8 @@
 //
 // Persistent grid: CTAs stride over the 2^(n-L) blocks; several CTAs per SM overlap one
 // tile's copies with another tile's arithmetic.  Every mbarrier wait is bounded by a
-// %globaltimer deadline; on expiry the CTA records QS_ETIMEOUT in *status and returns.
+// %globaltimer deadline; on expiry the whole CTA (a block-wide vote) records QS_ETIMEOUT in
+// *status and returns.  A pass that timed out leaves the state undefined.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -670,7 +671,11 @@ __device__ __forceinline__ bool process_block(typename A::store_t* __restrict__ 
       if ((s >> k) & 1u) off |= 1ull << tp.tpos[c + k];
     bulk_load(tile_s + s * seg_stride, psi + (base | off), seg_bytes, bar);
   }
-  if (!mbar_wait(bar, phase, globaltimer() + kWaitNs)) {
+  // every thread waits with its own bounded deadline; the CTA then decides as one whether
+  // to go on, so that no thread is left at a later barrier when another gave up.  After a
+  // timeout the tile's contents (and this pass's result) are undefined.
+  const bool loaded = mbar_wait(bar, phase, globaltimer() + kWaitNs);
+  if (__syncthreads_or(!loaded)) {
     if (tid == 0) atomicExch(status, (int)QS_ETIMEOUT);
     return false;
   }

@@ -3,8 +3,11 @@
 //
 // The array lives in this file at namespace scope, so every GPU that loads the library
 // holds it (kNoAllocParts doubles) until the process exits.  Host code cannot use the
-// array's name as a device address; the address is looked up once per device with
-// cudaGetSymbolAddress and cached.
+// array's name as a device address; the address is looked up with cudaGetSymbolAddress once
+// per device and context (the device current at the time) and cached under that context, so
+// that a new context on the device (after cudaDeviceReset, say), whose copy of the module
+// sits elsewhere, gets its own lookup instead of a stale address.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,8 +25,32 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_norm_scratch[kNoAllocParts];
 
+// cached address per device, valid for the context it was looked up in
+struct AddrCache {
+  void* ctx = nullptr;
+  void* addr = nullptr;
+};
 std::mutex g_addr_mu;
-void* g_addr[kMaxDevices] = {};
+AddrCache g_addr[kMaxDevices];
+
+// the calling thread's current driver context (entry point fetched through the runtime, so
+// the library needs no link against the driver library)
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+void* current_context() {
+  static CtxGetCurrentFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return (CtxGetCurrentFn)f;
+  }();
+  CUcontext c = nullptr;
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return (void*)c;
+}
 
 qs_status fail(qs_status st, const std::string& msg) {
   set_last_error(msg);
@@ -50,15 +77,21 @@ extern "C" qs_status qs_norm_noalloc(const void* psi, int n, qs_dtype dtype, dou
     return fail(QS_ECUDA, std::string("qs_norm_noalloc: no usable current device: ") + cudaGetErrorString(e));
   void* scratch = nullptr;
   {
+    // NULL before the runtime has made a context current on this thread (first use)
+    void* ctx = current_context();
     std::lock_guard<std::mutex> lk(g_addr_mu);
-    if (!g_addr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_norm_scratch);
-      if (e != cudaSuccess || !p)
+    AddrCache& c = g_addr[dev];
+    if (ctx && c.addr && c.ctx == ctx) {
+      scratch = c.addr;
+    } else {   // first call in this context (or no context handle: look up every call)
+      e = cudaGetSymbolAddress(&scratch, g_norm_scratch);
+      if (e != cudaSuccess || !scratch)
         return fail(QS_ECUDA, std::string("qs_norm_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
-      g_addr[dev] = p;
+      if (ctx) {
+        c.ctx = ctx;
+        c.addr = scratch;
+      }
     }
-    scratch = g_addr[dev];
   }
   cudaStream_t s = (cudaStream_t)stream;
   // every partial is overwritten by its block, so nothing needs clearing between calls

@@ -71,3 +71,26 @@ def test_gates_in_storage_order_match_logical():
     got = sv.run_storage_program(n, prog)
     ref = sv.simulate(n, circ)
     np.testing.assert_allclose(got, ref, atol=1e-14, rtol=0)
+
+
+@pytest.mark.parametrize("n", [1, 3, 6])
+def test_logical_index_against_brute_force(n):
+    """sv.logical_index (the storage -> logical map the full-size GPU permutation tests use)
+    agrees with the brute-force j(i, sigma) loop for every sigma at these sizes."""
+    ident = np.arange(1 << n, dtype=np.float64).astype(np.complex128)
+    j = np.arange(1 << n, dtype=np.uint64)
+    for s in itertools.permutations(range(n)):
+        stored = brute_store(ident, n, s)          # stored[j(i, s)] = i
+        np.testing.assert_array_equal(sv.logical_index(j, s), stored.real.astype(np.uint64))
+
+
+def test_logical_index_high_bits():
+    """Positions past 2^32 (a 36-qubit index space) map through every bit."""
+    n = 36
+    rng = np.random.default_rng(36)
+    s = wc.random_permutation(n, rng)
+    i = rng.integers(0, 1 << n, 1000, dtype=np.uint64)
+    j = np.zeros_like(i)
+    for q in range(n):
+        j |= ((i >> np.uint64(q)) & np.uint64(1)) << np.uint64(s[q])
+    np.testing.assert_array_equal(sv.logical_index(j, s), i)
