@@ -687,45 +687,41 @@ def measure_batched(qs, torch, args):
 
 
 def measure_serving(args):
-    """The serving workload: random circuits (n = floor(exp(U(ln 12, ln 29))), depth U{20..100},
-    Haar 2x2 + CNOT/CZ layers, complex64 or complex128 with probability 1/2), Poisson arrivals.
-    First all requests at once (saturation throughput), then Poisson arrivals at fixed
-    fractions of that throughput; latency = arrival -> result read back on the host."""
+    """The serving workload through the library's native server (qs_server_*): random circuits
+    (n = floor(exp(U(ln 12, ln 29))), depth U{20..100}, Haar 2x2 + CNOT/CZ layers, complex64 or
+    complex128 with probability 1/2), Poisson arrivals.  First all requests at once (the
+    saturation throughput), then Poisson arrivals at fixed fractions of that throughput;
+    latency = arrival -> result (FP64 norm and first amplitudes) in host memory."""
     from paper_2010_09746_gb300 import serve
     budget = int(args.serve_mem_gib * (1 << 30))
+
+    def one(reqs, realtime, order):
+        srv = serve.Server(slots=args.serve_slots, mem_budget=budget, order=order)
+        t0 = time.perf_counter()
+        res = srv.run(reqs, realtime=realtime)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        return dict(serve.latency_summary(res, wall), peak_in_flight=st["peak_in_flight"],
+                    batched_requests=st["batched_requests"], batches=st["batches"],
+                    peak_mem_gib=round(st["peak_mem_bytes"] / 2 ** 30, 2)), wall
+
     reqs = wc.serving_workload(args.serve_requests, rate_hz=1.0, seed=0)
-    srv = serve.Server(slots=args.serve_slots, mem_budget=budget, order=args.serve_order)
-    t0 = time.perf_counter()
-    res = srv.run(reqs, realtime=False)
-    wall = time.perf_counter() - t0
+    sat_entry, wall = one(reqs, False, args.serve_order)
     sat = len(reqs) / wall
     out = {"requests_per_load": len(reqs), "slots": args.serve_slots, "mem_budget_gib": args.serve_mem_gib,
-           "batch_small_n": srv.batch_small_n, "order": args.serve_order,
-           "saturation": dict(serve.latency_summary(res, wall), peak_in_flight=srv.peak_in_flight,
-                              batched_requests=srv.batched_requests, batches=srv.batches)}
+           "order": args.serve_order, "server": "native (qs_server_*: compile threads + admission thread)",
+           "saturation": sat_entry}
     for frac in args.serve_loads:
         rate = frac * sat
         reqs = wc.serving_workload(args.serve_requests, rate_hz=rate, seed=0)   # same circuits, Poisson times
-        srv = serve.Server(slots=args.serve_slots, mem_budget=budget, order=args.serve_order)
-        t0 = time.perf_counter()
-        res = srv.run(reqs, realtime=True)
-        wall = time.perf_counter() - t0
-        out[f"load_{frac:g}"] = dict(serve.latency_summary(res, wall), offered_rate_hz=round(rate, 3),
-                                      peak_in_flight=srv.peak_in_flight, batched_requests=srv.batched_requests,
-                                      batches=srv.batches)
+        entry, _ = one(reqs, True, args.serve_order)
+        out[f"load_{frac:g}"] = dict(entry, offered_rate_hz=round(rate, 3))
     # the other admission order at saturation and at 0.9 of it, same requests
     other = "sjf" if args.serve_order == "fifo" else "fifo"
     alt = {}
-    reqs = wc.serving_workload(args.serve_requests, rate_hz=1.0, seed=0)
-    srv = serve.Server(slots=args.serve_slots, mem_budget=budget, order=other)
-    t0 = time.perf_counter()
-    res = srv.run(reqs, realtime=False)
-    alt["saturation"] = serve.latency_summary(res, time.perf_counter() - t0)
-    reqs = wc.serving_workload(args.serve_requests, rate_hz=0.9 * sat, seed=0)
-    srv = serve.Server(slots=args.serve_slots, mem_budget=budget, order=other)
-    t0 = time.perf_counter()
-    res = srv.run(reqs, realtime=True)
-    alt["load_0.9"] = serve.latency_summary(res, time.perf_counter() - t0)
+    alt["saturation"], _ = one(wc.serving_workload(args.serve_requests, rate_hz=1.0, seed=0), False, other)
+    alt["load_0.9"], _ = one(wc.serving_workload(args.serve_requests, rate_hz=0.9 * sat, seed=0), True, other)
     out[f"order_{other}"] = alt
     return out
 
@@ -803,10 +799,10 @@ def main(argv=None):
     ap.add_argument("--batched", type=int, default=4096, help="circuits in the batched measurement (0 = skip)")
     ap.add_argument("--batch-tile-bits", type=int, nargs="+", default=[10, 12, 13],
                     help="tile widths the batched measurement's autotuner times")
-    ap.add_argument("--serve-requests", type=int, default=64, help="requests per serving load point (0 = skip)")
+    ap.add_argument("--serve-requests", type=int, default=500, help="requests per serving load point (0 = skip)")
     ap.add_argument("--serve-order", default="fifo", choices=["fifo", "sjf"],
                     help="admission order: first come, or least estimated work first (1 s maximum wait)")
-    ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.1, 0.5, 0.9, 1.2],
+    ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.5, 0.9],
                     help="Poisson arrival rates as fractions of the measured saturation throughput")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-mem-gib", type=float, default=96.0)

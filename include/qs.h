@@ -167,8 +167,12 @@ qs_status qs_set_allocator(void* (*alloc_fn)(size_t bytes, void* ctx, void* stre
 /* ---- states (Sec. 2: the 2^n-amplitude vector and its qubit permutation sigma) ------ */
 
 /* Allocate a state of n qubits (1 <= n <= 36) on the current device, set to |0...0>
- * with sigma = identity.  Work is enqueued on the default stream until qs_set_stream. */
+ * with sigma = identity (synchronises the legacy default stream).  Work is enqueued on the
+ * default stream until qs_set_stream. */
 qs_status qs_create(int n, qs_dtype dtype, qs_handle* out);
+/* The same, with the allocation and initialisation enqueued on `stream` (cudaStream_t),
+ * which becomes the state's stream; returns without waiting for the device. */
+qs_status qs_create_async(int n, qs_dtype dtype, void* stream, qs_handle* out);
 qs_status qs_destroy(qs_handle h);
 
 /* Stream (cudaStream_t) on which all later work of this state is enqueued. */
@@ -307,6 +311,70 @@ qs_status qs_batch_norms(qs_batch_t b, double* out);
 qs_status qs_batch_get_amplitudes(qs_batch_t b, int i, void* out, uint64_t first, uint64_t count);
 qs_status qs_batch_get_stats(qs_batch_t b, qs_batch_stats* out);
 qs_status qs_batch_destroy(qs_batch_t b);
+
+/* ---- serving: continuous batching (no counterpart in the paper) --------------------- *
+ * A server runs independent requests (an n-qubit circuit and a dtype, each simulated from
+ * |0...0>) as they arrive.  Host threads compile every request's plan (QS_MODE_TILE) as
+ * soon as it is submitted; one admission thread starts a compiled request as soon as one of
+ * the server's slots (each its own CUDA stream) and its state's bytes within the memory
+ * budget are free, without waiting for the requests already on the GPU, so work of
+ * different requests overlaps on the device.  Small requests (n <= batch_small_n) that are
+ * ready together share one slot as one batch (persistent tile-pass launches over all their
+ * states, as qs_batch_*).  Every request runs the same per-tile code on its own state
+ * whatever else is in flight, so its result is bitwise its result alone.  A finished
+ * request leaves the FP64 norm and its first amplitudes in host memory until taken.
+ * Device memory of the server's states comes from cudaMallocAsync on the slot streams, not
+ * from an allocator installed with qs_set_allocator. */
+typedef struct qs_server* qs_server_t;
+
+typedef struct {
+  int32_t slots;           /* requests (or batches) on the GPU at once, one stream each; 0 = 8 */
+  int32_t compile_threads; /* host threads compiling plans; 0 = 4 */
+  int64_t mem_budget;      /* device bytes for resident states; 0 = 3/4 of the free memory */
+  int32_t readout;         /* amplitudes kept per request: the first min(2^n, readout); 0 = 256 */
+  int32_t batch_small_n;   /* requests with n <= this that are ready together share a slot; 0 = 16,
+                              negative = never */
+  int32_t batch_max;       /* most requests sharing one slot; 0 = 64 */
+  int32_t order;           /* admission order: 0 = arrival, 1 = least estimated device work first */
+  int32_t max_wait_ms;     /* order 1: a request that has waited this long goes first; 0 = 1000 */
+  int32_t tile_bits;       /* compile option of every request (0 = the dtype's default) */
+  int32_t reserved;        /* must be 0 */
+} qs_server_opts;
+
+typedef struct {
+  int64_t id;
+  int32_t status;          /* qs_status of the request (compile or device failure) */
+  int32_t n;
+  int32_t dtype;
+  int32_t batched;         /* 1 if it shared a slot with other requests */
+  double norm;             /* FP64 norm of the final state */
+  double t_submit_s, t_admit_s, t_done_s;   /* server clock (seconds since qs_server_create) */
+  uint64_t amplitudes;     /* amplitudes kept for qs_server_take */
+  char error[128];         /* failure text, "" if none */
+} qs_server_result;
+
+typedef struct {
+  int64_t submitted, completed, in_flight, waiting, batches, batched_requests, peak_in_flight;
+  double peak_mem_bytes, mem_used_bytes;
+  double now_s;            /* server clock */
+} qs_server_stats;
+
+/* Start a server on the current device (opts NULL = defaults). */
+qs_status qs_server_create(const qs_server_opts* opts, qs_server_t* out);
+/* Queue one request (1 <= n <= 30; ops / mats as qs_compile, copied); *id identifies it.
+ * Returns at once; QS_EINVAL if the state alone exceeds the memory budget. */
+qs_status qs_server_submit(qs_server_t s, int n, qs_dtype dtype, const qs_op* ops, size_t nops, const double* mats,
+                           size_t nmats, int64_t* id);
+/* Up to `max` finished requests not reported before (each reported once), waiting up to
+ * timeout_ms for the first one when none is ready (0 = do not wait). */
+qs_status qs_server_poll(qs_server_t s, qs_server_result* out, int max, int* count, int timeout_ms);
+/* Copy the first `count` kept amplitudes of finished request `id` (interleaved (re, im) in
+ * its dtype) into HOST memory and release the result. */
+qs_status qs_server_take(qs_server_t s, int64_t id, void* amps, uint64_t count);
+qs_status qs_server_get_stats(qs_server_t s, qs_server_stats* out);
+/* Finish every submitted request, then stop the threads and release everything (results
+ * not taken are dropped). */
+qs_status qs_server_destroy(qs_server_t s);
 
 /* ---- read-outs (Sec. 2: measurement) ------------------------------------------------ */
 

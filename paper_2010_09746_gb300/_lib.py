@@ -52,6 +52,27 @@ class qs_batch_stats(ctypes.Structure):
                 ("alu_instr", ctypes.c_double), ("compile_ms", ctypes.c_double)]
 
 
+class qs_server_opts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int32), ("compile_threads", ctypes.c_int32), ("mem_budget", ctypes.c_int64),
+                ("readout", ctypes.c_int32), ("batch_small_n", ctypes.c_int32), ("batch_max", ctypes.c_int32),
+                ("order", ctypes.c_int32), ("max_wait_ms", ctypes.c_int32), ("tile_bits", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class qs_server_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int64), ("status", ctypes.c_int32), ("n", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("batched", ctypes.c_int32), ("norm", ctypes.c_double), ("t_submit_s", ctypes.c_double),
+                ("t_admit_s", ctypes.c_double), ("t_done_s", ctypes.c_double), ("amplitudes", ctypes.c_uint64),
+                ("error", ctypes.c_char * 128)]
+
+
+class qs_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("in_flight", ctypes.c_int64),
+                ("waiting", ctypes.c_int64), ("batches", ctypes.c_int64), ("batched_requests", ctypes.c_int64),
+                ("peak_in_flight", ctypes.c_int64), ("peak_mem_bytes", ctypes.c_double),
+                ("mem_used_bytes", ctypes.c_double), ("now_s", ctypes.c_double)]
+
+
 assert ctypes.sizeof(qs_op) == 48
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -70,6 +91,7 @@ SIGNATURES = {
     "qs_version": (ctypes.c_char_p, []),
     "qs_set_allocator": (_I, [ALLOC_FN, FREE_FN, _P]),
     "qs_create": (_I, [_I, _I, ctypes.POINTER(_H)]),
+    "qs_create_async": (_I, [_I, _I, _P, ctypes.POINTER(_H)]),
     "qs_destroy": (_I, [_H]),
     "qs_set_stream": (_I, [_H, _P]),
     "qs_set_arith": (_I, [_H, _I]),
@@ -113,6 +135,13 @@ SIGNATURES = {
     "qs_batch_get_amplitudes": (_I, [_H, _I, _P, ctypes.c_uint64, ctypes.c_uint64]),
     "qs_batch_get_stats": (_I, [_H, ctypes.POINTER(qs_batch_stats)]),
     "qs_batch_destroy": (_I, [_H]),
+    "qs_server_create": (_I, [ctypes.POINTER(qs_server_opts), ctypes.POINTER(_H)]),
+    "qs_server_submit": (_I, [_H, _I, _I, ctypes.POINTER(qs_op), ctypes.c_size_t, _DP, ctypes.c_size_t,
+                              ctypes.POINTER(ctypes.c_int64)]),
+    "qs_server_poll": (_I, [_H, ctypes.POINTER(qs_server_result), _I, _IP, _I]),
+    "qs_server_take": (_I, [_H, ctypes.c_int64, _P, ctypes.c_uint64]),
+    "qs_server_get_stats": (_I, [_H, ctypes.POINTER(qs_server_stats)]),
+    "qs_server_destroy": (_I, [_H]),
 }
 
 _lib = None

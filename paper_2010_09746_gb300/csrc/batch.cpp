@@ -13,7 +13,7 @@
 #include <thread>
 #include <vector>
 
-#include "qs_internal.h"
+#include "runtime.h"
 
 using namespace qs;
 
@@ -24,57 +24,20 @@ cudaError_t launch_batch_norms(const void* psi, int is_c128, const uint64_t* off
                                double* out, cudaStream_t s);
 }  // namespace qs
 
-struct qs_batch {
-  int count = 0;
-  qs_dtype dtype = QS_C64;
-  Policy pol = POL_F32;
-  int K = 0;
-  int store_bytes = 8;
-  std::vector<int> n;
-  std::vector<uint64_t> off;       // element offset of each state
-  size_t total_elems = 0;
-  // concatenated plan data
-  std::vector<StageRec> stages;
-  std::vector<RegOp> rops;
-  std::vector<DevOp> dops;
-  Pool pool;
-  struct Wave {
-    std::vector<BatchPass> passes;
-    std::vector<uint64_t> prefix;
-    int maxL = 0, minc = 64;
-    size_t pass_off = 0, prefix_off = 0;   // into the device arrays
-  };
-  std::vector<Wave> waves;
-  qs_batch_stats stats{};
-  // device
-  void* psi = nullptr;
-  StageRec* stages_d = nullptr;
-  RegOp* rops_d = nullptr;
-  DevOp* dops_d = nullptr;
-  void* pool_d = nullptr;
-  BatchPass* passes_d = nullptr;
-  uint64_t* prefix_d = nullptr;
-  uint64_t* off_d = nullptr;
-  int* n_d = nullptr;
-  double* norms_d = nullptr;
-  int* status_d = nullptr;
-  std::vector<void*> allocs;
-  cudaStream_t stream = nullptr;
-  bool use_graph = true;
-  int runs = 0;
-  cudaGraphExec_t graph = nullptr;
-};
-
 namespace {
 
 template <class T>
 T* upload(qs_batch* b, const std::vector<T>& v, cudaError_t* e) {
   if (v.empty() || *e != cudaSuccess) return nullptr;
-  void* p = nullptr;
-  *e = cudaMalloc(&p, v.size() * sizeof(T));
-  if (*e != cudaSuccess) return nullptr;
-  b->allocs.push_back(p);
-  *e = cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  const size_t bytes = v.size() * sizeof(T);
+  void* p = dev_alloc_as(bytes, b->stream, b->native_alloc);
+  if (!p) {
+    *e = cudaErrorMemoryAllocation;
+    return nullptr;
+  }
+  b->allocs.push_back({p, bytes});
+  // pageable source: read by the time the call returns; the vector lives in the batch anyway
+  *e = cudaMemcpyAsync(p, v.data(), bytes, cudaMemcpyHostToDevice, b->stream);
   return (T*)p;
 }
 
@@ -98,86 +61,35 @@ cudaError_t enqueue(qs_batch* b) {
 
 }  // namespace
 
-extern "C" {
+namespace qs {
 
-qs_status qs_batch_create(int count, const int* n, const qs_op* ops, const int64_t* op_offsets, const double* mats,
-                          size_t nmats, const qs_compile_opts* opts, qs_batch_t* out) {
-  if (!out) return bfail(QS_EINVAL, "null output batch");
+qs_status batch_from_plans(const std::vector<const qs_plan*>& plans, qs_dtype dtype, cudaStream_t stream,
+                           qs_batch** out) {
   *out = nullptr;
-  if (count < 1 || !n || !op_offsets) return bfail(QS_EINVAL, "empty batch");
-  qs_compile_opts o{};
-  o.mode = QS_MODE_TILE;
-  o.dtype = QS_C64;
-  if (opts) o = *opts;
-  if (o.mode != QS_MODE_TILE) return bfail(QS_EINVAL, "batches run tile-mode plans only");
-  if (o.dtype != QS_C64 && o.dtype != QS_C128) return bfail(QS_EINVAL, "unknown dtype");
-  if ((o.flags & ~QS_FLAG_FULL_RX) || o.reg_bits < 0 || o.reg_bits > 5) return bfail(QS_EINVAL, "bad options");
-  if (o.renorm_every != 0) return bfail(QS_EINVAL, "periodic renormalisation is not available in batches");
-  auto t0 = std::chrono::steady_clock::now();
+  const int count = (int)plans.size();
+  if (count < 1) return bfail(QS_EINVAL, "empty batch");
   qs_batch* b = new qs_batch();
+  b->stream = stream;
+  b->native_alloc = dev_alloc_native();
   b->count = count;
-  b->dtype = (qs_dtype)o.dtype;
-  b->store_bytes = o.dtype == QS_C128 ? 16 : 8;
-  b->n.assign(n, n + count);
+  b->dtype = dtype;
+  b->store_bytes = dtype == QS_C128 ? 16 : 8;
   b->off.resize(count);
-  const int Lreq = o.tile_bits ? o.tile_bits : default_tile_bits(o.dtype);
-  const int creq = o.low_bits ? o.low_bits : default_low_bits(o.dtype);
   size_t elems = 0;
   std::vector<std::vector<BatchPass>> per_circuit(count);
   for (int i = 0; i < count; i++) {
-    if (n[i] < 1 || n[i] > 30) {
+    const qs_plan* p = plans[i];
+    if (p->dtype != (int)dtype || p->n < 1 || p->n > 30) {
       delete b;
-      return bfail(QS_EINVAL, "circuit " + std::to_string(i) + ": n must be in [1, 30] in a batch");
+      return bfail(QS_EINVAL, "batch plan " + std::to_string(i) + " has another dtype or n outside [1, 30]");
     }
-    if (op_offsets[i + 1] < op_offsets[i]) {
-      delete b;
-      return bfail(QS_EINVAL, "op_offsets must be non-decreasing");
-    }
+    b->n.push_back(p->n);
     b->off[i] = elems;
-    elems += ((size_t)1 << n[i]);
+    elems += ((size_t)1 << p->n);
     elems = (elems + 31) & ~(size_t)31;   // 256-byte aligned starts
   }
-  // the circuits compile independently: spread them over the host's cores, then
-  // concatenate the programs in circuit order (the result does not depend on the split)
-  std::vector<CompileResult> results(count);
-  std::vector<std::string> errs(count);
-  {
-    std::atomic<int> next(0);
-    auto worker = [&] {
-      for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) {
-        std::vector<HGate> gates(op_offsets[i + 1] - op_offsets[i]);
-        std::string err;
-        bool ok = true;
-        for (size_t g = 0; g < gates.size() && ok; g++)
-          if (!make_hgate(n[i], ops[op_offsets[i] + g], mats, nmats, &gates[g], &err)) {
-            errs[i] = "circuit " + std::to_string(i) + " op " + std::to_string(g) + ": " + err;
-            ok = false;
-          }
-        if (!ok) continue;
-        qs_compile_opts oi = o;
-        oi.tile_bits = std::min(Lreq, n[i]);
-        oi.low_bits = std::min(std::max(creq, o.dtype == QS_C64 ? 1 : 0), oi.tile_bits);
-        std::vector<int> s0(n[i]);
-        for (int q = 0; q < n[i]; q++) s0[q] = q;
-        if (!compile_circuit(n[i], gates, s0, oi, &results[i], &err))
-          errs[i] = "circuit " + std::to_string(i) + ": " + err;
-      }
-    };
-    unsigned nt = std::thread::hardware_concurrency();
-    nt = std::max(1u, std::min(nt, 64u));
-    if ((int)nt > count) nt = (unsigned)count;
-    std::vector<std::thread> pool;
-    for (unsigned t = 1; t < nt; t++) pool.emplace_back(worker);
-    worker();
-    for (auto& t : pool) t.join();
-  }
-  for (int i = 0; i < count; i++)
-    if (!errs[i].empty()) {
-      delete b;
-      return bfail(QS_EINVAL, errs[i]);
-    }
   for (int i = 0; i < count; i++) {
-    CompileResult& cr = results[i];
+    const CompileResult& cr = plans[i]->cr;
     b->pol = cr.pol;
     const int sbase = (int)b->stages.size(), rbase = (int)b->rops.size(), dbase = (int)b->dops.size();
     const int pbase = (int)b->pool.entries();
@@ -215,7 +127,6 @@ qs_status qs_batch_create(int count, const int* n, const qs_op* ops, const int64
     }
     b->stats.n_gates += cr.stats.n_gates;
     b->stats.n_passes += cr.stats.n_passes;
-    cr = CompileResult();   // release the per-circuit copy
   }
   if (b->pool.entries() == 0) b->pool.add(cd(0, 0));
   b->total_elems = elems;
@@ -246,8 +157,10 @@ qs_status qs_batch_create(int count, const int* n, const qs_op* ops, const int64
     all_passes.insert(all_passes.end(), w.passes.begin(), w.passes.end());
     all_prefix.insert(all_prefix.end(), w.prefix.begin(), w.prefix.end());
   }
-  cudaError_t e = cudaMalloc(&b->psi, elems * b->store_bytes);
-  if (e == cudaSuccess) b->allocs.push_back(b->psi);
+  cudaError_t e = cudaSuccess;
+  b->psi = dev_alloc_as(elems * b->store_bytes, stream, b->native_alloc);
+  if (b->psi) b->allocs.push_back({b->psi, elems * b->store_bytes});
+  else e = cudaErrorMemoryAllocation;
   std::vector<unsigned char> ser = b->pool.serialise(b->pol);
   b->stages_d = upload(b, b->stages, &e);
   b->rops_d = upload(b, b->rops, &e);
@@ -265,6 +178,74 @@ qs_status qs_batch_create(int count, const int* n, const qs_op* ops, const int64
     qs_batch_destroy(b);
     set_last_error(std::string("batch upload: ") + cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? QS_ENOMEM : QS_ECUDA;
+  }
+  *out = b;
+  return QS_OK;
+}
+
+}  // namespace qs
+
+
+extern "C" {
+
+qs_status qs_batch_create(int count, const int* n, const qs_op* ops, const int64_t* op_offsets, const double* mats,
+                          size_t nmats, const qs_compile_opts* opts, qs_batch_t* out) {
+  if (!out) return bfail(QS_EINVAL, "null output batch");
+  *out = nullptr;
+  if (count < 1 || !n || !op_offsets) return bfail(QS_EINVAL, "empty batch");
+  qs_compile_opts o{};
+  o.mode = QS_MODE_TILE;
+  o.dtype = QS_C64;
+  if (opts) o = *opts;
+  if (o.mode != QS_MODE_TILE) return bfail(QS_EINVAL, "batches run tile-mode plans only");
+  if (o.dtype != QS_C64 && o.dtype != QS_C128) return bfail(QS_EINVAL, "unknown dtype");
+  if ((o.flags & ~QS_FLAG_FULL_RX) || o.reg_bits < 0 || o.reg_bits > 5) return bfail(QS_EINVAL, "bad options");
+  if (o.renorm_every != 0) return bfail(QS_EINVAL, "periodic renormalisation is not available in batches");
+  auto t0 = std::chrono::steady_clock::now();
+  for (int i = 0; i < count; i++) {
+    if (n[i] < 1 || n[i] > 30) return bfail(QS_EINVAL, "circuit " + std::to_string(i) + ": n must be in [1, 30] in a batch");
+    if (op_offsets[i + 1] < op_offsets[i]) return bfail(QS_EINVAL, "op_offsets must be non-decreasing");
+  }
+  // the circuits compile independently (each exactly as qs_compile compiles it): spread them
+  // over the host's cores, then concatenate the programs in circuit order
+  std::vector<qs_plan_t> plans(count, nullptr);
+  std::vector<std::string> errs(count);
+  std::vector<qs_status> sts(count, QS_OK);
+  {
+    std::atomic<int> next(0);
+    auto worker = [&] {
+      for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) {
+        sts[i] = qs_compile(n[i], ops + op_offsets[i], (size_t)(op_offsets[i + 1] - op_offsets[i]), mats, nmats, nullptr,
+                            &o, &plans[i]);
+        if (sts[i] != QS_OK) errs[i] = "circuit " + std::to_string(i) + ": " + qs_last_error();
+      }
+    };
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = std::max(1u, std::min(nt, 64u));
+    if ((int)nt > count) nt = (unsigned)count;
+    std::vector<std::thread> pool;
+    for (unsigned t = 1; t < nt; t++) pool.emplace_back(worker);
+    worker();
+    for (auto& t : pool) t.join();
+  }
+  qs_status st = QS_OK;
+  std::string err;
+  for (int i = 0; i < count && st == QS_OK; i++)
+    if (sts[i] != QS_OK) {
+      st = sts[i];
+      err = errs[i];
+    }
+  qs_batch* b = nullptr;
+  if (st == QS_OK) {
+    std::vector<const qs_plan*> cp(plans.begin(), plans.end());
+    st = batch_from_plans(cp, (qs_dtype)o.dtype, nullptr, &b);
+    if (st != QS_OK) err = qs_last_error();
+  }
+  for (qs_plan_t p : plans) qs_plan_destroy(p);   // never uploaded: nothing on the device
+  if (st != QS_OK) return bfail(st, err);
+  if (cudaStreamSynchronize(nullptr) != cudaSuccess) {   // uploads done before the stream may change
+    qs_batch_destroy(b);
+    return bfail(QS_ECUDA, "batch upload");
   }
   b->stats.compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = b;
@@ -319,9 +300,11 @@ qs_status qs_batch_sync(qs_batch_t b) {
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bfail(QS_ECUDA, std::string("batch sync: ") + cudaGetErrorString(e));
   int st = 0;
-  cudaMemcpy(&st, b->status_d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpyAsync(&st, b->status_d, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+  cudaStreamSynchronize(b->stream);
   if (st != 0) {
-    cudaMemset(b->status_d, 0, sizeof(int));
+    cudaMemsetAsync(b->status_d, 0, sizeof(int), b->stream);
+    cudaStreamSynchronize(b->stream);
     return bfail(QS_ETIMEOUT, "a device-side wait timed out");
   }
   return QS_OK;
@@ -331,7 +314,8 @@ qs_status qs_batch_norms(qs_batch_t b, double* out) {
   if (!b || !out) return bfail(QS_EINVAL, "null argument");
   qs_status s = qs_batch_sync(b);
   if (s != QS_OK) return s;
-  cudaError_t e = cudaMemcpy(out, b->norms_d, sizeof(double) * b->count, cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpyAsync(out, b->norms_d, sizeof(double) * b->count, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bfail(QS_ECUDA, std::string("batch norms: ") + cudaGetErrorString(e));
   return QS_OK;
 }
@@ -343,8 +327,9 @@ qs_status qs_batch_get_amplitudes(qs_batch_t b, int i, void* out, uint64_t first
   if (first > N || count > N - first) return bfail(QS_EINVAL, "amplitude range out of bounds");
   qs_status s = qs_batch_sync(b);
   if (s != QS_OK) return s;
-  cudaError_t e = cudaMemcpy(out, (char*)b->psi + (b->off[i] + first) * b->store_bytes, count * b->store_bytes,
-                             cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpyAsync(out, (char*)b->psi + (b->off[i] + first) * b->store_bytes, count * b->store_bytes,
+                                  cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bfail(QS_ECUDA, std::string("batch amplitudes: ") + cudaGetErrorString(e));
   return QS_OK;
 }
@@ -357,9 +342,11 @@ qs_status qs_batch_get_stats(qs_batch_t b, qs_batch_stats* out) {
 
 qs_status qs_batch_destroy(qs_batch_t b) {
   if (!b) return QS_OK;
+  // the batch's own stream finishes first (the caller may read results right up to here);
+  // the buffers then go back in stream order, without waiting for the whole device
   cudaStreamSynchronize(b->stream);
   if (b->graph) cudaGraphExecDestroy(b->graph);
-  for (void* p : b->allocs) cudaFree(p);
+  for (auto& a : b->allocs) dev_free_as(a.first, a.second, b->stream, b->native_alloc);
   delete b;
   return QS_OK;
 }

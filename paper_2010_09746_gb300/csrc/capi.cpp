@@ -7,7 +7,7 @@
 #include <string>
 #include <vector>
 
-#include "qs_internal.h"
+#include "runtime.h"
 
 using namespace qs;
 
@@ -29,14 +29,29 @@ qs_status cuda_fail(cudaError_t e, const char* where) {
     if (_e != cudaSuccess) return cuda_fail(_e, where); \
   } while (0)
 
+}  // namespace
+
+namespace qs {
+
 // ---- allocator -----------------------------------------------------------------------------
+namespace {
 void* (*g_alloc)(size_t, void*, void*) = nullptr;
 void (*g_free)(void*, size_t, void*, void*) = nullptr;
 void* g_alloc_ctx = nullptr;
+}  // namespace
 
-void* dev_alloc(size_t bytes, cudaStream_t s) {
+namespace {
+thread_local bool t_native_alloc = false;
+}  // namespace
+
+void set_thread_native_alloc(bool on) { t_native_alloc = on; }
+bool dev_alloc_native() { return t_native_alloc || g_alloc == nullptr; }
+
+void* dev_alloc(size_t bytes, cudaStream_t s) { return dev_alloc_as(bytes, s, dev_alloc_native()); }
+
+void* dev_alloc_as(size_t bytes, cudaStream_t s, bool native) {
   if (bytes == 0) bytes = 256;
-  if (g_alloc) return g_alloc(bytes, g_alloc_ctx, (void*)s);
+  if (!native && g_alloc) return g_alloc(bytes, g_alloc_ctx, (void*)s);
   void* p = nullptr;
   if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
     cudaGetLastError();
@@ -44,77 +59,28 @@ void* dev_alloc(size_t bytes, cudaStream_t s) {
   }
   return p;
 }
-void dev_free(void* p, size_t bytes, cudaStream_t s) {
+
+void dev_free_as(void* p, size_t bytes, cudaStream_t s, bool native) {
   if (!p) return;
-  if (g_free) {
+  if (!native && g_free) {
     g_free(p, bytes == 0 ? 256 : bytes, g_alloc_ctx, (void*)s);
     return;
   }
   cudaFreeAsync(p, s);
 }
 
+void dev_free(void* p, size_t bytes, cudaStream_t s) { dev_free_as(p, bytes, s, dev_alloc_native()); }
+
 Policy policy_for(qs_dtype dt, qs_arith a) {
   if (dt == QS_C64) return POL_F32;
   return a == QS_ARITH_F64 ? POL_F64 : POL_DF;
 }
 
-}  // namespace
+}  // namespace qs
 
 namespace qs {
 void set_last_error(const std::string& msg) { g_err = msg; }
 }  // namespace qs
-
-struct KernelRecord {
-  std::string name;
-  cudaEvent_t e0, e1;
-  double bytes;
-  double alu;
-};
-
-constexpr size_t kDenseWBytes = 2 * 128 * 128 * sizeof(float);
-
-struct qs_state {
-  int n = 0;
-  qs_dtype dtype = QS_C128;
-  qs_arith arith = QS_ARITH_AUTO;
-  int store_bytes = 16;
-  size_t bytes = 0;
-  void* psi = nullptr;
-  void* scratch = nullptr;        // permutation target, allocated on first use
-  std::vector<int> sigma;
-  cudaStream_t stream = nullptr;
-  int* status_dev = nullptr;      // device status word (bounded waits)
-  double* norm_buf = nullptr;     // norm partials + result
-  void* gate_pool = nullptr;      // matrix entries of qs_apply_* calls
-  size_t gate_pool_bytes = 0;
-  int dense_path = QS_DENSE_AUTO; // qs_apply_dense engine (qs_set_dense_path)
-  float* dense_w = nullptr;       // 2 x 128 x 128 floats: W^T split for the tensor-core kernel
-  int num_sms = 0;
-  bool profiling = false;
-  std::vector<KernelRecord> pending;
-  std::vector<cudaEvent_t> free_events;
-  std::vector<qs_kernel_stat> stats;
-};
-
-struct qs_plan {
-  int n = 0;
-  int dtype = QS_C128;
-  Policy pol = POL_DF;
-  std::vector<int> sigma0;
-  CompileResult cr;
-  DevOp* ops_dev = nullptr;
-  size_t ops_bytes = 0;
-  RegOp* rops_dev = nullptr;
-  size_t rops_bytes = 0;
-  StageRec* stages_dev = nullptr;
-  size_t stages_bytes = 0;
-  void* pool_dev = nullptr;
-  size_t pool_bytes = 0;
-  bool uploaded = false;
-  // one event per stream the plan was executed on, recorded after its last launch there:
-  // the device buffers are released once all of them have completed
-  std::vector<std::pair<cudaStream_t, cudaEvent_t>> uses;
-};
 
 namespace {
 
@@ -210,9 +176,9 @@ qs_status apply_hgate(qs_state* h, const HGate& g) {
   const Policy pol = policy_for(h->dtype, h->arith);
   std::vector<unsigned char> ser = pool.serialise(pol);
   if (ser.size() > h->gate_pool_bytes) {
-    dev_free(h->gate_pool, h->gate_pool_bytes, h->stream);
+    dev_free_as(h->gate_pool, h->gate_pool_bytes, h->stream, h->native_alloc);
     h->gate_pool_bytes = std::max<size_t>(ser.size(), 64 * 1024);
-    h->gate_pool = dev_alloc(h->gate_pool_bytes, h->stream);
+    h->gate_pool = dev_alloc_as(h->gate_pool_bytes, h->stream, h->native_alloc);
     if (!h->gate_pool) return fail(QS_ENOMEM, "gate matrix buffer allocation failed");
   }
   if (!ser.empty())
@@ -228,7 +194,7 @@ qs_status apply_hgate(qs_state* h, const HGate& g) {
 
 qs_status ensure_scratch(qs_state* h) {
   if (h->scratch) return QS_OK;
-  h->scratch = dev_alloc(h->bytes, h->stream);
+  h->scratch = dev_alloc_as(h->bytes, h->stream, h->native_alloc);
   if (!h->scratch) return fail(QS_ENOMEM, "permutation scratch allocation failed");
   return QS_OK;
 }
@@ -310,7 +276,7 @@ qs_status apply_dense_tensor(qs_state* h, const double* U, int k, const int* qub
   std::vector<float> w(2 * 128 * 128);
   dense_mma_weights(U, k, bits, w.data());
   if (!h->dense_w) {
-    h->dense_w = (float*)dev_alloc(kDenseWBytes, h->stream);
+    h->dense_w = (float*)dev_alloc_as(kDenseWBytes, h->stream, h->native_alloc);
     if (!h->dense_w) return fail(QS_ENOMEM, "dense weight buffer allocation failed");
   }
   if (!h->num_sms) {
@@ -344,6 +310,7 @@ qs_status renormalize(qs_state* h) {
 struct DeferredFree {
   std::vector<std::pair<void*, size_t>> bufs;
   std::vector<cudaEvent_t> events;
+  bool native = true;   // allocated by cudaMallocAsync (else by the installed allocator)
 };
 std::mutex g_deferred_mu;
 std::vector<DeferredFree> g_deferred;
@@ -358,7 +325,7 @@ bool events_done(const std::vector<cudaEvent_t>& evs) {
 }
 
 void release_deferred(DeferredFree& d) {
-  for (auto& b : d.bufs) dev_free(b.first, b.second, nullptr);
+  for (auto& b : d.bufs) dev_free_as(b.first, b.second, nullptr, d.native);
   for (cudaEvent_t e : d.events) cudaEventDestroy(e);
   d.bufs.clear();
   d.events.clear();
@@ -378,7 +345,10 @@ void reap_deferred() {
   for (DeferredFree& d : ready) release_deferred(d);
 }
 
-// record that `p` has just been enqueued on `s`
+}  // namespace
+
+namespace qs {
+
 qs_status note_plan_use(qs_plan* p, cudaStream_t s) {
   cudaEvent_t ev = nullptr;
   for (auto& u : p->uses)
@@ -391,7 +361,39 @@ qs_status note_plan_use(qs_plan* p, cudaStream_t s) {
   return QS_OK;
 }
 
-}  // namespace
+
+qs_status state_create_on(int n, qs_dtype dtype, cudaStream_t stream, qs_state** out) {
+  *out = nullptr;
+  if (n < 1 || n > kMaxQubits) return fail(QS_EINVAL, "n must be in [1, 36]");
+  if (dtype != QS_C64 && dtype != QS_C128) return fail(QS_EINVAL, "unknown dtype");
+  qs_state* h = new qs_state();
+  h->n = n;
+  h->dtype = dtype;
+  h->stream = stream;
+  h->native_alloc = dev_alloc_native();
+  h->store_bytes = dtype == QS_C128 ? 16 : 8;
+  h->bytes = (size_t)h->store_bytes << n;
+  h->sigma.resize(n);
+  for (int q = 0; q < n; q++) h->sigma[q] = q;
+  h->psi = dev_alloc(h->bytes, stream);
+  h->status_dev = (int*)dev_alloc(256, stream);
+  h->norm_buf = (double*)dev_alloc(sizeof(double) * (norm_num_partials() + 1), stream);
+  if (!h->psi || !h->status_dev || !h->norm_buf) {
+    const size_t b = h->bytes;
+    qs_destroy(h);
+    return fail(QS_ENOMEM, "state allocation failed (" + std::to_string(b) + " bytes)");
+  }
+  cudaError_t e = cudaMemsetAsync(h->status_dev, 0, 256, stream);
+  if (e == cudaSuccess) e = launch_init_zero(h->psi, n, h->store_bytes, stream);
+  if (e != cudaSuccess) {
+    qs_destroy(h);
+    return cuda_fail(e, "init");
+  }
+  *out = h;
+  return QS_OK;
+}
+
+}  // namespace qs
 
 extern "C" {
 
@@ -409,49 +411,33 @@ qs_status qs_set_allocator(void* (*alloc_fn)(size_t, void*, void*), void (*free_
 
 qs_status qs_create(int n, qs_dtype dtype, qs_handle* out) {
   if (!out) return fail(QS_EINVAL, "null output handle");
-  *out = nullptr;
-  if (n < 1 || n > kMaxQubits) return fail(QS_EINVAL, "n must be in [1, 36]");
-  if (dtype != QS_C64 && dtype != QS_C128) return fail(QS_EINVAL, "unknown dtype");
-  qs_state* h = new qs_state();
-  h->n = n;
-  h->dtype = dtype;
-  h->store_bytes = dtype == QS_C128 ? 16 : 8;
-  h->bytes = (size_t)h->store_bytes << n;
-  h->sigma.resize(n);
-  for (int q = 0; q < n; q++) h->sigma[q] = q;
-  h->psi = dev_alloc(h->bytes, h->stream);
-  h->status_dev = (int*)dev_alloc(256, h->stream);
-  h->norm_buf = (double*)dev_alloc(sizeof(double) * (norm_num_partials() + 1), h->stream);
-  if (!h->psi || !h->status_dev || !h->norm_buf) {
-    qs_destroy(h);
-    return fail(QS_ENOMEM, "state allocation failed (" + std::to_string(h->bytes) + " bytes)");
-  }
-  cudaMemsetAsync(h->status_dev, 0, 256, h->stream);
-  cudaError_t e = launch_init_zero(h->psi, n, h->store_bytes, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  if (e != cudaSuccess) {
-    qs_destroy(h);
-    return cuda_fail(e, "init");
-  }
-  *out = h;
+  qs_status st = state_create_on(n, dtype, nullptr, out);
+  if (st != QS_OK) return st;
+  CUDA_TRY(cudaStreamSynchronize(nullptr), "init");
   return QS_OK;
+}
+
+qs_status qs_create_async(int n, qs_dtype dtype, void* stream, qs_handle* out) {
+  if (!out) return fail(QS_EINVAL, "null output handle");
+  return state_create_on(n, dtype, (cudaStream_t)stream, out);
 }
 
 qs_status qs_destroy(qs_handle h) {
   if (!h) return QS_OK;
-  cudaStreamSynchronize(h->stream);
-  for (auto& r : h->pending) {
-    cudaEventDestroy(r.e0);
-    cudaEventDestroy(r.e1);
-  }
+  // buffers go back in stream order: nothing here waits for the device, except that the
+  // profiling events still pending are read first
+  if (!h->pending.empty()) collect_stats(h);
   for (auto e : h->free_events) cudaEventDestroy(e);
-  dev_free(h->psi, h->bytes, h->stream);
-  dev_free(h->scratch, h->bytes, h->stream);
-  dev_free(h->status_dev, 256, h->stream);
-  dev_free(h->norm_buf, sizeof(double) * (norm_num_partials() + 1), h->stream);
-  dev_free(h->gate_pool, h->gate_pool_bytes, h->stream);
-  dev_free(h->dense_w, kDenseWBytes, h->stream);
-  cudaStreamSynchronize(h->stream);
+  // an installed allocator may hand the memory to other streams at once: let this
+  // state's work finish first (the default pool orders the frees itself)
+  if (!h->native_alloc) cudaStreamSynchronize(h->stream);
+  const bool nat = h->native_alloc;
+  dev_free_as(h->psi, h->bytes, h->stream, nat);
+  dev_free_as(h->scratch, h->bytes, h->stream, nat);
+  dev_free_as(h->status_dev, 256, h->stream, nat);
+  dev_free_as(h->norm_buf, sizeof(double) * (norm_num_partials() + 1), h->stream, nat);
+  dev_free_as(h->gate_pool, h->gate_pool_bytes, h->stream, nat);
+  dev_free_as(h->dense_w, kDenseWBytes, h->stream, nat);
   delete h;
   return QS_OK;
 }
@@ -646,11 +632,13 @@ qs_status qs_plan_destroy(qs_plan_t p) {
   if (!p) return QS_OK;
   reap_deferred();
   DeferredFree d;
+  d.native = p->native_alloc;
   if (p->uploaded) {
     d.bufs = {{p->ops_dev, p->ops_bytes}, {p->rops_dev, p->rops_bytes}, {p->stages_dev, p->stages_bytes},
               {p->pool_dev, p->pool_bytes}};
   }
   for (auto& u : p->uses) d.events.push_back(u.second);
+  if (p->upload_event) d.events.push_back(p->upload_event);
   if (events_done(d.events)) {
     release_deferred(d);
   } else {   // still in use on some stream: released by a later reap, without waiting here
@@ -684,28 +672,39 @@ qs_status qs_plan_get_trace(qs_plan_t p, int32_t* kinds, int32_t* values, size_t
   return QS_OK;
 }
 
-static qs_status plan_upload(qs_plan* p) {
-  if (p->uploaded) return QS_OK;
+// Device copies of a plan, made on first execution on the executing stream (stream-ordered
+// allocation and copies); an execution on another stream waits for them through an event.
+static qs_status plan_upload(qs_plan* p, cudaStream_t s) {
+  if (p->uploaded) {
+    if (s != p->upload_stream) CUDA_TRY(cudaStreamWaitEvent(s, p->upload_event, 0), "plan upload wait");
+    return QS_OK;
+  }
   p->ops_bytes = p->cr.tile_ops.size() * sizeof(DevOp);
   p->rops_bytes = p->cr.reg_ops.size() * sizeof(RegOp);
   p->stages_bytes = p->cr.stages.size() * sizeof(StageRec);
   std::vector<unsigned char> ser = p->cr.pool.serialise(p->pol);
   p->pool_bytes = ser.size();
-  if (p->ops_bytes) p->ops_dev = (DevOp*)dev_alloc(p->ops_bytes, nullptr);
-  if (p->rops_bytes) p->rops_dev = (RegOp*)dev_alloc(p->rops_bytes, nullptr);
-  if (p->stages_bytes) p->stages_dev = (StageRec*)dev_alloc(p->stages_bytes, nullptr);
-  if (p->pool_bytes) p->pool_dev = dev_alloc(p->pool_bytes, nullptr);
+  if (p->ops_bytes) p->ops_dev = (DevOp*)dev_alloc(p->ops_bytes, s);
+  if (p->rops_bytes) p->rops_dev = (RegOp*)dev_alloc(p->rops_bytes, s);
+  if (p->stages_bytes) p->stages_dev = (StageRec*)dev_alloc(p->stages_bytes, s);
+  if (p->pool_bytes) p->pool_dev = dev_alloc(p->pool_bytes, s);
+  p->uploaded = true;   // whatever was allocated is released with the plan
+  p->native_alloc = dev_alloc_native();
+  p->upload_stream = s;
   if ((p->ops_bytes && !p->ops_dev) || (p->pool_bytes && !p->pool_dev) || (p->rops_bytes && !p->rops_dev) ||
       (p->stages_bytes && !p->stages_dev))
     return fail(QS_ENOMEM, "plan upload allocation failed");
+  // pageable sources: each copy has read its source when the call returns
   cudaError_t e = cudaSuccess;
-  if (p->ops_bytes) e = cudaMemcpy(p->ops_dev, p->cr.tile_ops.data(), p->ops_bytes, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && p->rops_bytes) e = cudaMemcpy(p->rops_dev, p->cr.reg_ops.data(), p->rops_bytes, cudaMemcpyHostToDevice);
+  if (p->ops_bytes) e = cudaMemcpyAsync(p->ops_dev, p->cr.tile_ops.data(), p->ops_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && p->rops_bytes)
+    e = cudaMemcpyAsync(p->rops_dev, p->cr.reg_ops.data(), p->rops_bytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && p->stages_bytes)
-    e = cudaMemcpy(p->stages_dev, p->cr.stages.data(), p->stages_bytes, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && p->pool_bytes) e = cudaMemcpy(p->pool_dev, ser.data(), p->pool_bytes, cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(p->stages_dev, p->cr.stages.data(), p->stages_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && p->pool_bytes) e = cudaMemcpyAsync(p->pool_dev, ser.data(), p->pool_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->upload_event, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(p->upload_event, s);
   if (e != cudaSuccess) return cuda_fail(e, "plan upload");
-  p->uploaded = true;
   return QS_OK;
 }
 
@@ -737,13 +736,16 @@ static qs_status execute_steps(qs_handle h, qs_plan_t p) {
 
 qs_status qs_execute(qs_handle h, qs_plan_t p) {
   if (!h || !p) return fail(QS_EINVAL, "null argument");
-  {
-    qs_status ust = plan_upload(p);
-    if (ust != QS_OK) return ust;
-  }
   if (h->n != p->n) return fail(QS_EINVAL, "plan and state have different n");
   if ((int)h->dtype != p->dtype) return fail(QS_EINVAL, "plan and state have different dtype");
   if (h->sigma != p->sigma0) return fail(QS_EINVAL, "state permutation differs from the plan's start permutation");
+  {
+    qs_status ust = plan_upload(p, h->stream);
+    if (ust != QS_OK) {
+      note_plan_use(p, h->stream);   // copies may have been enqueued
+      return ust;
+    }
+  }
   const qs_status st = execute_steps(h, p);
   // whatever was enqueued keeps the plan's buffers alive until it has run
   const qs_status su = note_plan_use(p, h->stream);

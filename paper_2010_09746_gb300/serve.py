@@ -1,29 +1,28 @@
-"""Continuous-batching request loop over the C ABI.
+"""Continuous-batching request loop: a thin binding of the library's server (qs_server_*).
 
-Requests (a circuit, its qubit count and dtype) arrive over time.  The server admits a
-waiting request as soon as a slot and enough device memory are free -- it does not wait
-for the requests already on the GPU -- compiles its plan on the host, and enqueues
-state preparation and the plan on the slot's own CUDA stream, so
-work of different requests overlaps on the device.  Small requests (n <= batch_small_n)
-waiting together with others of the same dtype share one slot: they are compiled into one
-batch (qs_batch_*), whose tile passes run as persistent launches over all of their states.
-Admission order is first-come or shortest-estimated-work first (with a maximum wait that
-lets long-waiting requests go first).  Completion is detected with CUDA events; the result (the FP64 norm and the first
-amplitudes) is read out, the state is released and the next request takes the slot.  Every
-request runs the same per-tile code on its own state whatever else is in flight (a batched
-circuit's amplitudes are bitwise those of its solo run), so its result does not depend on
-the mix.
+The server itself is native code (csrc/server.cpp): host threads compile each request's plan
+as it arrives, and one admission thread starts a compiled request as soon as a slot (its own
+CUDA stream) and enough device memory are free -- it does not wait for the requests already
+on the GPU -- so work of different requests overlaps on the device.  Small requests that are
+ready together share a slot as one batch (persistent tile-pass launches over all their
+states).  Admission order is first-come or least-estimated-work first (with a maximum wait).
+Every request runs the same per-tile code on its own state whatever else is in flight, so
+its result does not depend on the mix.  This module only submits requests (at their arrival
+times, or all at once), polls for results and copies them out.
 """
 from __future__ import annotations
 
+import ctypes
 import time
-from collections import deque
 from dataclasses import dataclass
-from typing import Dict, List, Optional
+from typing import Dict, Optional
 
 import numpy as np
 
-from . import Batch, Plan, State
+from . import _lib, marshal
+from ._lib import QS_C64, QS_C128
+
+_DT = {"c64": QS_C64, "c128": QS_C128}
 
 
 @dataclass
@@ -36,180 +35,131 @@ class Result:
     arrival_s: float
     admit_s: float
     done_s: float
+    batched: bool = False
 
     @property
     def latency_s(self) -> float:
         return self.done_s - self.arrival_s
 
 
-@dataclass
-class _Slot:
-    stream: object
-    busy: bool = False
-
-
-@dataclass
-class _Flight:
-    members: List[tuple]          # (rid, req, arrival_s) of every request in this flight
-    slot: int
-    state: Optional[State]        # one request
-    plan: Optional[Plan]
-    batch: Optional[Batch]        # several small requests
-    event: object
-    admit_s: float
-    bytes: int
-
-
 class Server:
-    """slots: requests in flight at once; mem_budget: device bytes for resident states;
-    readout: amplitudes copied back per request (first min(2^n, readout))."""
+    """slots: requests (or batches of small ones) on the GPU at once; mem_budget: device bytes
+    for resident states; readout: amplitudes copied back per request (the first
+    min(2^n, readout)); order: "fifo" or "sjf" (least estimated work first unless a request
+    has waited max_wait_s)."""
 
     def __init__(self, slots: int = 8, mem_budget: int = 64 << 30, readout: int = 256, tile_bits: int = 0,
-                 batch_small_n: int = 16, batch_max: int = 64, order: str = "fifo", max_wait_s: float = 1.0):
-        import torch
-
-        self.torch = torch
-        self.slots = [_Slot(torch.cuda.Stream()) for _ in range(slots)]
-        self.mem_budget = int(mem_budget)
-        self.mem_used = 0
-        self.readout = readout
-        self.tile_bits = tile_bits
-        self.batch_small_n = batch_small_n
-        self.batch_max = batch_max
+                 batch_small_n: int = 16, batch_max: int = 64, order: str = "fifo", max_wait_s: float = 1.0,
+                 compile_threads: int = 4):
         if order not in ("fifo", "sjf"):
             raise ValueError("order must be 'fifo' or 'sjf'")
-        self.order = order            # sjf: least estimated work first, unless a request waited max_wait_s
-        self.max_wait_s = max_wait_s
-        self.batched_requests = 0
-        self.batches = 0
-        self.waiting: deque = deque()
-        self.flights: List[_Flight] = []
+        o = _lib.qs_server_opts()
+        o.slots = slots
+        o.compile_threads = compile_threads
+        o.mem_budget = int(mem_budget)
+        o.readout = readout
+        o.batch_small_n = batch_small_n if batch_small_n > 0 else -1
+        o.batch_max = batch_max
+        o.order = 0 if order == "fifo" else 1
+        o.max_wait_ms = max(1, int(round(max_wait_s * 1e3)))
+        o.tile_bits = tile_bits
+        self.mem_budget = int(mem_budget)
+        self.readout = readout
+        self._L = _lib.load()
+        h = ctypes.c_void_p()
+        _lib.check(self._L.qs_server_create(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._rid_of: Dict[int, int] = {}
+        self._arrival: Dict[int, float] = {}
         self.results: Dict[int, Result] = {}
-        self.peak_in_flight = 0
-        self.peak_mem = 0
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._L.qs_server_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
 
     @staticmethod
     def state_bytes(n: int, dtype: str) -> int:
         return (1 << n) * (16 if dtype == "c128" else 8)
 
-    def submit(self, rid: int, req, arrival_s: float):
+    # -- statistics of the native server ---------------------------------------------------
+    def stats(self) -> dict:
+        st = _lib.qs_server_stats()
+        _lib.check(self._L.qs_server_get_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    @property
+    def peak_in_flight(self) -> int:
+        return int(self.stats()["peak_in_flight"])
+
+    @property
+    def batched_requests(self) -> int:
+        return int(self.stats()["batched_requests"])
+
+    @property
+    def batches(self) -> int:
+        return int(self.stats()["batches"])
+
+    @property
+    def peak_mem(self) -> float:
+        return self.stats()["peak_mem_bytes"]
+
+    # -- requests ----------------------------------------------------------------------------
+    def submit(self, rid: int, req) -> int:
         if self.state_bytes(req.n, req.dtype) > self.mem_budget:
             raise ValueError(f"request {rid} needs more device memory than the whole budget")
-        self.waiting.append((rid, req, arrival_s))
+        ops, nops, mats = marshal(req.circuit)
+        sid = ctypes.c_int64()
+        _lib.check(self._L.qs_server_submit(self._h, int(req.n), _DT[req.dtype], ops, nops,
+                                            mats.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), mats.size,
+                                            ctypes.byref(sid)))
+        self._rid_of[sid.value] = rid
+        return sid.value
 
-    @staticmethod
-    def work_estimate(req) -> float:
-        """Relative device work: gates x amplitudes, complex128 (double-float) ~8x complex64."""
-        return len(req.circuit) * float(1 << req.n) * (8.0 if req.dtype == "c128" else 1.0)
-
-    def _next(self, now_s: float) -> int:
-        """Index in `waiting` of the request to admit next."""
-        if self.order == "fifo" or len(self.waiting) == 1:
-            return 0
-        if now_s - self.waiting[0][2] >= self.max_wait_s:   # the oldest has waited long enough
-            return 0
-        return min(range(len(self.waiting)), key=lambda k: self.work_estimate(self.waiting[k][1]))
-
-    def _admit(self, now_s: float) -> int:
-        admitted = 0
-        while self.waiting:
-            k = self._next(now_s)
-            if k:
-                self.waiting.rotate(-k)   # bring it to the front; the others keep their order after it
-                item = self.waiting.popleft()
-                self.waiting.rotate(k)
-                self.waiting.appendleft(item)
-            rid, req, arr = self.waiting[0]
-            need = self.state_bytes(req.n, req.dtype)
-            free = [i for i, s in enumerate(self.slots) if not s.busy]
-            if not free or self.mem_used + need > self.mem_budget:
-                break
-            si = free[0]
-            slot = self.slots[si]
-            group = []
-            if req.n <= self.batch_small_n and self.batch_max > 1:
-                # the small requests of this dtype now waiting, in arrival order, that fit
-                mem = 0
-                for item in self.waiting:
-                    r2 = item[1]
-                    b2 = self.state_bytes(r2.n, r2.dtype)
-                    if (r2.n <= self.batch_small_n and r2.dtype == req.dtype and len(group) < self.batch_max
-                            and self.mem_used + mem + b2 <= self.mem_budget):
-                        group.append(item)
-                        mem += b2
-            if len(group) > 1:
-                ids = {id(item) for item in group}
-                self.waiting = deque(item for item in self.waiting if id(item) not in ids)
-                b = Batch([(r.n, r.circuit) for _, r, _ in group], dtype=req.dtype, stream=slot.stream, graph=False,
-                          tile_bits=self.tile_bits)
-                b.run()
-                ev = self.torch.cuda.Event()
-                ev.record(slot.stream)
-                self.flights.append(_Flight(group, si, None, None, b, ev, now_s, mem))
-                self.mem_used += mem
-                self.batched_requests += len(group)
-                self.batches += 1
-                admitted += len(group)
-            else:
-                self.waiting.popleft()
-                plan = Plan(req.n, req.circuit, mode="tile", dtype=req.dtype, tile_bits=self.tile_bits)
-                st = State(req.n, req.dtype, stream=slot.stream)
-                st.execute(plan)
-                ev = self.torch.cuda.Event()
-                ev.record(slot.stream)
-                self.flights.append(_Flight([(rid, req, arr)], si, st, plan, None, ev, now_s, need))
-                self.mem_used += need
-                admitted += 1
-            slot.busy = True
-        self.peak_in_flight = max(self.peak_in_flight, sum(len(f.members) for f in self.flights))
-        self.peak_mem = max(self.peak_mem, self.mem_used)
-        return admitted
-
-    def _poll(self, clock) -> int:
-        done = 0
-        keep = []
-        for f in self.flights:
-            if not f.event.query():
-                keep.append(f)
-                continue
-            if f.batch is not None:
-                norms = f.batch.norms()
-                t = clock()
-                for i, (rid, req, arr) in enumerate(f.members):
-                    amps = f.batch.amplitudes(i, 0, min(1 << req.n, self.readout))
-                    self.results[rid] = Result(rid, req.n, req.dtype, float(norms[i]), amps, arr, f.admit_s, t)
-                del f.batch
-            else:
-                rid, req, arr = f.members[0]
-                amps = f.state.amplitudes(0, min(1 << req.n, self.readout))
-                norm = f.state.norm()
-                t = clock()
-                self.results[rid] = Result(rid, req.n, req.dtype, norm, amps, arr, f.admit_s, t)
-                f.state.close()
-            self.slots[f.slot].busy = False
-            self.mem_used -= f.bytes
-            done += len(f.members)
-        self.flights = keep
-        return done
+    def poll(self, timeout_s: float = 0.0) -> int:
+        """Collect finished requests (waiting up to timeout_s for the first); returns how many."""
+        buf = (_lib.qs_server_result * 256)()
+        cnt = ctypes.c_int()
+        _lib.check(self._L.qs_server_poll(self._h, buf, 256, ctypes.byref(cnt), int(timeout_s * 1e3)))
+        for i in range(cnt.value):
+            r = buf[i]
+            if r.status != _lib.QS_OK:
+                raise _lib.QSError(r.status, f"request {self._rid_of.get(r.id)}: {r.error.decode(errors='replace')}")
+            dt = "c128" if r.dtype == QS_C128 else "c64"
+            amps = np.empty(r.amplitudes, dtype=np.complex128 if dt == "c128" else np.complex64)
+            _lib.check(self._L.qs_server_take(self._h, r.id, amps.ctypes.data_as(ctypes.c_void_p), r.amplitudes))
+            rid = self._rid_of.pop(r.id)
+            arr = self._arrival.pop(r.id, r.t_submit_s)
+            self.results[rid] = Result(rid, r.n, dt, r.norm, amps, arr, r.t_admit_s, r.t_done_s, bool(r.batched))
+        return cnt.value
 
     def run(self, requests, realtime: bool = True, timeout_s: float = 600.0) -> Dict[int, Result]:
-        """Serve `requests` (objects with arrival_s, n, dtype, circuit).  realtime: requests
-        become visible at their arrival times on the wall clock; otherwise all at once."""
+        """Serve `requests` (objects with arrival_s, n, dtype, circuit).  realtime: each request
+        is submitted at its arrival time (server clock); otherwise all at once.  Latency runs
+        from submission to the result being in host memory."""
+        self.results = {}
         reqs = sorted(enumerate(requests), key=lambda t: t[1].arrival_s)
-        t0 = time.perf_counter()
-        clock = lambda: time.perf_counter() - t0  # noqa: E731
+        st0 = self.stats()["now_s"]
+        w0 = time.perf_counter()
         nxt = 0
         while len(self.results) < len(reqs):
-            now = clock()
+            now = time.perf_counter() - w0
             if now > timeout_s:
                 raise TimeoutError("serving did not finish in time")
             while nxt < len(reqs) and (not realtime or reqs[nxt][1].arrival_s <= now):
                 rid, r = reqs[nxt]
-                self.submit(rid, r, r.arrival_s if realtime else 0.0)
+                sid = self.submit(rid, r)
+                if realtime:   # the arrival instant on the server's clock
+                    self._arrival[sid] = st0 + r.arrival_s
                 nxt += 1
-            self._admit(clock())
-            if self._poll(clock) == 0:
-                time.sleep(0.0002)
+            wait = 0.05
+            if realtime and nxt < len(reqs):
+                wait = max(0.0, min(wait, reqs[nxt][1].arrival_s - (time.perf_counter() - w0)))
+            self.poll(wait)
         return self.results
 
 

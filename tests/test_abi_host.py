@@ -77,6 +77,28 @@ def test_state_calls_validate_null():
     assert L.qs_create(37, 1, ctypes.byref(h)) == _lib.QS_EINVAL
 
 
+def test_server_rejects_bad_options():
+    """Options are checked before any device is touched."""
+    L = _lib.load()
+    h = ctypes.c_void_p()
+    for field, value in (("slots", -1), ("slots", 1000), ("compile_threads", -2), ("order", 2), ("readout", -1),
+                         ("tile_bits", 15), ("mem_budget", -5), ("reserved", 1), ("batch_max", -1)):
+        o = _lib.qs_server_opts()
+        setattr(o, field, value)
+        assert L.qs_server_create(ctypes.byref(o), ctypes.byref(h)) == _lib.QS_EINVAL, field
+        assert not h.value
+    assert L.qs_server_create(None, None) == _lib.QS_EINVAL
+    assert L.qs_server_destroy(None) == _lib.QS_OK
+    cnt = ctypes.c_int()
+    assert L.qs_server_poll(None, None, 0, ctypes.byref(cnt), 0) == _lib.QS_EINVAL
+
+
+def test_server_struct_layout():
+    assert ctypes.sizeof(_lib.qs_server_opts) == 48
+    assert ctypes.sizeof(_lib.qs_server_result) == 64 + 128
+    assert ctypes.sizeof(_lib.qs_server_stats) == 7 * 8 + 3 * 8
+
+
 def oracle_trace(n, m, circ, scoring="closure"):
     prog, st = cr.alg1(n, m, circ, scoring=scoring)
     out = []

@@ -58,7 +58,7 @@ def test_oversized_request_rejected():
     srv = serve.Server(slots=2, mem_budget=1 << 20)
     r = wc.Request(0.0, 20, "c128", [])
     with pytest.raises(ValueError):
-        srv.submit(0, r, 0.0)
+        srv.submit(0, r)
 
 
 def test_sjf_order_same_results():
