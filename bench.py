@@ -263,27 +263,55 @@ def per_gate_bound(qs, n, circ, args, peaks, gates_per_s):
     return {"bytes_per_circuit": b, "ideal_gates_per_s": round(ideal, 2), "ratio": round(gates_per_s / ideal, 3)}
 
 
-def fit_cost_model(dtype, runs):
+def fit_cost_model(qs, torch, st, stream, args, runs):
     """Per kernel class, least squares t = c_launch*launches + c_byte*bytes + c_alu*instructions
-    over the CUDA-event totals of these runs (one sample per class and run); then each
-    plan's step time predicted from its compile-time statistics (plus the state
-    initialisation and the norm) against the measured one."""
+    over the CUDA-event totals of the training runs (one sample per class and run).  The
+    fitted model then goes into the compiler (qs_compile_opts.cost), which predicts each
+    plan's time (predicted_ms); the check is out of sample: circuits the fit never saw (another
+    seed of the same construction, 28 qubits, Appendix C's QFT-like circuit under the tile
+    passes and under Algorithm 1), each measured once after a warm-up."""
     from paper_2010_09746_gb300 import tuning
     m = tuning.CostModel()
     for _, (_, _, ks, steps) in runs.items():
         m.add_kernel_stats([dict(k, launches=k["launches"] / steps, total_ms=k["total_ms"] / steps,
                                  bytes=k["bytes"] / steps, alu=k["alu"] / steps) for k in ks])
     coef = m.fit()
-    pred = {}
+    native = m.native(args.dtype, args.arith)
+    init_norm = sum(m.predict(c, 1, (1 << args.n) * (16 if args.dtype == "c128" else 8), 0)
+                    for c in ("init", "norm") if c in coef)
+
+    def predicted(n, circ, **kw):
+        p = qs.compile(n, circ, dtype=args.dtype, arith=args.arith, cost=native, **kw)
+        return p, p.stats()["predicted_ms"]
+
+    train = {}
     for name, (p, ms, _, _) in runs.items():
-        t = m.predict_plan(p, dtype)
-        sb = (1 << p.n) * (16 if dtype == "c128" else 8)
-        for cls in ("init", "norm"):
-            if t is not None and cls in coef:
-                t += m.predict(cls, 1, sb, 0)
-        pred[name] = {"predicted_ms": None if t is None else round(t, 3), "measured_ms": round(ms, 3)}
+        _, pr = predicted(p.n, runs_circuits[name], **runs_opts[name])
+        train[name] = {"predicted_ms": round(pr + init_norm, 3), "measured_ms": round(ms, 3)}
+    held = {}
+    cases = [("rzrx_30q_seed1_tile", args.n, wc.rzrx_cz_circuit(args.n, args.layers, seed=args.seed + 1), {"mode": "tile"}),
+             ("qft_like_30q_tile", args.n, wc.qft_like_circuit(args.n), {"mode": "tile"}),
+             ("qft_like_30q_alg1_m12", args.n, wc.qft_like_circuit(args.n), {"mode": "paper", "tile_bits": 12})]
+    for name, n, circ, kw in cases:
+        p, pr = predicted(n, circ, **kw)
+        ms, _, _ = measure(qs, st, p, 1, 1, torch, stream)
+        held[name] = {"predicted_ms": round(pr + init_norm, 3), "measured_ms": round(ms, 3),
+                      "rel_err": round((pr + init_norm - ms) / ms, 4)}
+    n2 = args.n - 2
+    st2 = qs.State(n2, args.dtype, arith=args.arith, stream=stream)
+    p, pr = predicted(n2, wc.rzrx_cz_circuit(n2, args.layers, seed=args.seed), mode="tile")
+    ms, _, _ = measure(qs, st2, p, 1, 1, torch, stream)
+    st2.close()
+    init_norm2 = init_norm / 4.0   # the state is a quarter of the size
+    held[f"rzrx_{n2}q_tile"] = {"predicted_ms": round(pr + init_norm2, 3), "measured_ms": round(ms, 3),
+                                "rel_err": round((pr + init_norm2 - ms) / ms, 4)}
     return {"coef_ms_per_launch_byte_instr": {k: [float(f"{x:.4g}") for x in v] for k, v in coef.items()},
-            "plans": pred}
+            "train": train, "held_out": held,
+            "held_out_max_abs_rel_err": max(abs(v["rel_err"]) for v in held.values())}
+
+
+runs_circuits = {}
+runs_opts = {}
 
 
 def run_ours(args):
@@ -390,9 +418,14 @@ def run_ours(args):
         modes["paper_alg1_m12"] = {"gates_per_s": round(G / (ms_pa / 1e3), 2), "passes": s_pa["n_passes"],
                                    "permutes": s_pa["n_permutes"], "nonlocal_gates": s_pa["n_comm_gates"]}
         out["modes"] = modes
-        out["cost_model"] = fit_cost_model(args.dtype, {"tile": (plan, ms, kstats, args.steps),
-                                                        "pergate": (p_pg, ms_pg, ks_pg, 1),
-                                                        "paper_alg1_m12": (p_pa, ms_pa, ks_pa, 1)})
+        runs_circuits.update({"tile": circ, "pergate": sub, "paper_alg1_m12": circ})
+        runs_opts.update({"tile": dict(mode=args.mode, tile_bits=args.tile_bits, low_bits=args.low_bits,
+                                       reg_bits=args.reg_bits),
+                          "pergate": {"mode": "pergate"}, "paper_alg1_m12": {"mode": "paper", "tile_bits": 12}})
+        if args.workload == "rzrx30":
+            out["cost_model"] = fit_cost_model(qs, torch, st, stream, args, {
+                "tile": (plan, ms, kstats, args.steps), "pergate": (p_pg, ms_pg, ks_pg, 1),
+                "paper_alg1_m12": (p_pa, ms_pa, ks_pa, 1)})
     if args.modes and args.workload == "rzrx30":
         out["permute"] = measure_permute(qs, torch, st, stream, n, (1 << n) * (16 if args.dtype == "c128" else 8))
     if args.small and args.workload == "rzrx30":
@@ -561,6 +594,22 @@ def measure_dense(qs, torch, args):
         row[path] = {"ms": round(e0.elapsed_time(e1) / 4, 3)}
     row["tensor_speedup"] = round(row["cuda_cores"]["ms"] / row["tensor"]["ms"], 2)
     res["k6_high_with_permute"] = row
+    # the compiler's own choice: the 30-qubit circuit as complex64, with the dense blocks the
+    # default cost model picks (gates ready on storage bits 0..5 fused into one tensor-core
+    # launch when that is predicted cheaper than their tile-pass arithmetic) and without
+    circ = wc.rzrx_cz_circuit(n, 40, seed=0)
+    plans = {}
+    for key, dense in (("with_dense_blocks", True), ("tile_passes_only", False)):
+        p = qs.compile(n, circ, mode="tile", dtype="c64", dense=dense)
+        ms, _, ks = measure(qs, st, p, 3, 2, torch, stream, profile=True)
+        s_ = p.stats()
+        plans[key] = {"gates_per_s": round(len(circ) / (ms / 1e3), 1), "ms": round(ms, 2),
+                      "passes": s_["n_passes"], "dense_blocks": s_["n_dense"],
+                      "predicted_ms": round(s_["predicted_ms"], 2),
+                      "dense_ms_per_launch": next((round(k["total_ms"] / k["launches"], 3) for k in ks
+                                                   if k["name"] == "dense_mma_c64"), None)}
+    plans["speedup"] = round(plans["tile_passes_only"]["ms"] / plans["with_dense_blocks"]["ms"], 3)
+    res["rzrx_30q_c64_compiled"] = plans
     st.close()
     torch.cuda.empty_cache()
     return res

@@ -98,11 +98,32 @@ typedef enum {
                            the pass's addressing, so no separate permutation pass is needed */
 } qs_mode;
 
-/* qs_compile_opts.flags.  By default an uncontrolled RX held in registers is applied in the
- * cheaper tangent form, (I - i tan X) or (cot I - i X), with the dropped cos / sin factors
- * of a tile pass multiplied into one full-form RX of that pass (same result up to
- * rounding); this flag keeps every RX in full form. */
-enum { QS_FLAG_FULL_RX = 1 };
+/* qs_compile_opts.flags.  QS_FLAG_FULL_RX: by default an uncontrolled RX held in registers
+ * is applied in the cheaper tangent form, (I - i tan X) or (cot I - i X), with the dropped
+ * cos / sin factors of a tile pass multiplied into one full-form RX of that pass (same result
+ * up to rounding); this flag keeps every RX in full form.  QS_FLAG_NO_DENSE: never emit dense
+ * tensor-core blocks (see qs_cost_model). */
+enum { QS_FLAG_FULL_RX = 1, QS_FLAG_NO_DENSE = 2 };
+
+/* Cost of one launch of each kernel class for the plan's dtype,
+ *   t [ms] = c[0] + c[1] * (algorithmic HBM bytes) + c[2] * (counted arithmetic instructions),
+ * the least-squares model that tuning.py fits to CUDA-event kernel times (Sec. 3 of the paper
+ * suggests compiler passes that use the simulator's measured benchmarks).  The compiler uses
+ * it in QS_MODE_TILE to decide, before each tile pass, whether the gates that are ready on
+ * storage bits 0..5 alone should instead run as one dense 64 x 64 block on the tensor cores
+ * (complex64, n >= 12): it does so when the block's predicted time is below the tile-pass
+ * time those gates are predicted to cost.  Every plan reports the model's prediction of its
+ * own execution time (qs_plan_stats.predicted_ms). */
+typedef struct {
+  double tile[3];      /* tile pass */
+  double gate[3];      /* per-gate kernel */
+  double permute[3];   /* permutation kernel */
+  double dense[3];     /* dense 6-qubit block on the tensor cores */
+} qs_cost_model;
+
+/* The model the compiler uses when qs_compile_opts.cost is NULL, for plans of this dtype and
+ * arithmetic (coefficients measured on GB300). */
+qs_status qs_default_cost_model(qs_dtype dtype, qs_arith arith, qs_cost_model* out);
 
 typedef struct {
   int32_t mode;       /* qs_mode */
@@ -124,6 +145,7 @@ typedef struct {
                            permutations) the state is divided by the square root of its FP64
                            norm, as by qs_renormalize; 0 = never.  Each costs one read for the
                            norm and one read + write for the scaling. */
+  const qs_cost_model* cost; /* kernel cost model; NULL = the library's defaults (GB300, measured) */
 } qs_compile_opts;
 
 typedef struct {
@@ -137,6 +159,8 @@ typedef struct {
                              formulas count them (FP32 FMA-pipe instructions for complex64 and
                              double-float, DFMA for native FP64), all amplitudes */
   double compile_ms;      /* host time spent compiling */
+  int64_t n_dense;        /* dense 6-qubit blocks on the tensor cores (QS_MODE_TILE, complex64) */
+  double predicted_ms;    /* the cost model's prediction of one execution */
 } qs_plan_stats;
 
 /* Per-kernel-class timing collected while profiling is on (qs_set_profiling). */
@@ -261,8 +285,9 @@ qs_status qs_plan_final_permutation(qs_plan_t p, int* perm_out);
  * kind 0 = gate run locally / inside a tile pass (value = gate index), 1 = gate run by the
  * per-gate kernel as a non-local gate (QS_MODE_PAPER), 2 = permutation exchanging logical
  * qubits l and g (value = 64 l + g, QS_MODE_PAPER), 3 and 4 = start of a tile pass whose
- * storage-bit set is (value of 3) | (value of 4) << 31 (QS_MODE_TILE).  Up to `max` entries
- * are written; *count gets the total.  Empty for QS_MODE_PERGATE. */
+ * storage-bit set is (value of 3) | (value of 4) << 31 (QS_MODE_TILE), 5 = start of a dense
+ * tensor-core block on storage bits 0..5 fusing the next `value` gates (QS_MODE_TILE).  Up to
+ * `max` entries are written; *count gets the total.  Empty for QS_MODE_PERGATE. */
 qs_status qs_plan_get_trace(qs_plan_t p, int32_t* kinds, int32_t* values, size_t max, size_t* count);
 
 /* Enqueue the plan on the state's stream.  The state must have the plan's n and dtype and

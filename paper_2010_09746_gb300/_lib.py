@@ -16,7 +16,7 @@ QS_ARITH_AUTO, QS_ARITH_DF, QS_ARITH_F64 = 0, 1, 2
 QS_MODE_PERGATE, QS_MODE_PAPER, QS_MODE_TILE = 0, 1, 2
 QS_ORDER_LOGICAL, QS_ORDER_STORAGE = 0, 1
 QS_DENSE_AUTO, QS_DENSE_CUDA_CORES, QS_DENSE_TENSOR = 0, 1, 2
-QS_FLAG_FULL_RX = 1
+QS_FLAG_FULL_RX, QS_FLAG_NO_DENSE = 1, 2
 OP_CODES = {"U1": 0, "H": 1, "X": 2, "Y": 3, "Z": 4, "S": 5, "T": 6, "RZ": 7, "RX": 8, "RY": 9, "P": 10,
             "CNOT": 11, "CZ": 12, "CP": 13, "CU": 14, "SWAP": 15, "U2": 16, "UK": 17, "RELABEL": 18}
 STATUS_NAMES = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ECUDA", 4: "QS_ETIMEOUT", 5: "QS_EBUSY",
@@ -28,17 +28,23 @@ class qs_op(ctypes.Structure):
                 ("param", ctypes.c_double), ("mat", ctypes.c_int64)]
 
 
+class qs_cost_model(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_double * 3), ("gate", ctypes.c_double * 3), ("permute", ctypes.c_double * 3),
+                ("dense", ctypes.c_double * 3)]
+
+
 class qs_compile_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("dtype", ctypes.c_int32), ("arith", ctypes.c_int32),
                 ("tile_bits", ctypes.c_int32), ("low_bits", ctypes.c_int32), ("max_ops", ctypes.c_int32),
                 ("scoring", ctypes.c_int32), ("flags", ctypes.c_int32), ("reg_bits", ctypes.c_int32),
-                ("renorm_every", ctypes.c_int32)]
+                ("renorm_every", ctypes.c_int32), ("cost", ctypes.POINTER(qs_cost_model))]
 
 
 class qs_plan_stats(ctypes.Structure):
     _fields_ = [("n_gates", ctypes.c_int64), ("n_passes", ctypes.c_int64), ("n_pergate", ctypes.c_int64),
                 ("n_permutes", ctypes.c_int64), ("n_comm_gates", ctypes.c_int64), ("hbm_bytes", ctypes.c_double),
-                ("alu_instr", ctypes.c_double), ("compile_ms", ctypes.c_double)]
+                ("alu_instr", ctypes.c_double), ("compile_ms", ctypes.c_double), ("n_dense", ctypes.c_int64),
+                ("predicted_ms", ctypes.c_double)]
 
 
 class qs_kernel_stat(ctypes.Structure):
@@ -110,6 +116,7 @@ SIGNATURES = {
     "qs_compile": (_I, [_I, ctypes.POINTER(qs_op), ctypes.c_size_t, _DP, ctypes.c_size_t, _IP,
                         ctypes.POINTER(qs_compile_opts), ctypes.POINTER(_H)]),
     "qs_plan_destroy": (_I, [_H]),
+    "qs_default_cost_model": (_I, [_I, _I, ctypes.POINTER(qs_cost_model)]),
     "qs_plan_get_stats": (_I, [_H, ctypes.POINTER(qs_plan_stats)]),
     "qs_plan_final_permutation": (_I, [_H, _IP]),
     "qs_plan_get_trace": (_I, [_H, _I32P, _I32P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),

@@ -162,6 +162,7 @@ bool valid_perm(int n, const int* p) {
 const char* step_name(const Step& s, Policy pol) {
   if (s.kind == ST_PASS) return pol == POL_F32 ? "tile_pass_c64" : (pol == POL_DF ? "tile_pass_c128_df" : "tile_pass_c128_f64");
   if (s.kind == ST_PERMUTE) return "permute";
+  if (s.kind == ST_DENSE) return "dense_mma_c64";
   return pol == POL_F32 ? "gate_c64" : (pol == POL_DF ? "gate_c128_df" : "gate_c128_f64");
 }
 
@@ -208,45 +209,6 @@ qs_status do_permute(qs_state* h, const std::vector<int>& src_of, const std::vec
   std::swap(h->psi, h->scratch);
   h->sigma = new_sigma;
   return QS_OK;
-}
-
-// The real 128 x 128 matrix of a dense k-qubit block on storage bits bits[0..k-1] (a
-// permutation of 0..k-1), replicated over storage bits k..5, transposed (row j = output
-// float j of a 64-amplitude row) and split into its nearest TF32 values and the TF32-rounded
-// remainders.
-void dense_mma_weights(const double* U, int k, const int* bits, float* out) {
-  const int kdim = 1 << k;
-  const int mask = kdim - 1;
-  auto mat_index = [&](int x) {
-    int r = 0;
-    for (int t = 0; t < k; t++) r |= ((x >> bits[t]) & 1) << t;
-    return r;
-  };
-  std::vector<double> wt(128 * 128, 0.0);
-  for (int xr = 0; xr < 64; xr++)
-    for (int xc = 0; xc < 64; xc++) {
-      if ((xr & ~mask) != (xc & ~mask)) continue;
-      const int r = mat_index(xr & mask), c = mat_index(xc & mask);
-      const double a = U[2 * (r * kdim + c)], b = U[2 * (r * kdim + c) + 1];
-      wt[(2 * xr) * 128 + 2 * xc] = a;
-      wt[(2 * xr) * 128 + 2 * xc + 1] = -b;
-      wt[(2 * xr + 1) * 128 + 2 * xc] = b;
-      wt[(2 * xr + 1) * 128 + 2 * xc + 1] = a;
-    }
-  auto tf32_rna = [](double v) {   // nearest TF32 value (ties away from zero), as a float
-    const float f = (float)v;
-    uint32_t u;
-    memcpy(&u, &f, 4);
-    u = (u + 0x1000u) & 0xFFFFE000u;
-    float r;
-    memcpy(&r, &u, 4);
-    return r;
-  };
-  for (int i = 0; i < 128 * 128; i++) {
-    const float big = tf32_rna(wt[i]);
-    out[i] = big;
-    out[128 * 128 + i] = tf32_rna(wt[i] - (double)big);
-  }
 }
 
 // Which engine QS_DENSE_AUTO picks for a complex64 block of k qubits (the CUDA-core
@@ -628,6 +590,14 @@ qs_status qs_compile(int n, const qs_op* ops, size_t nops, const double* mats, s
   return QS_OK;
 }
 
+qs_status qs_default_cost_model(qs_dtype dtype, qs_arith arith, qs_cost_model* out) {
+  if (!out) return fail(QS_EINVAL, "null output");
+  if (dtype != QS_C64 && dtype != QS_C128) return fail(QS_EINVAL, "unknown dtype");
+  if (arith != QS_ARITH_AUTO && arith != QS_ARITH_DF && arith != QS_ARITH_F64) return fail(QS_EINVAL, "unknown arith");
+  *out = default_cost_model(policy_for(dtype, arith));
+  return QS_OK;
+}
+
 qs_status qs_plan_destroy(qs_plan_t p) {
   if (!p) return QS_OK;
   reap_deferred();
@@ -635,7 +605,7 @@ qs_status qs_plan_destroy(qs_plan_t p) {
   d.native = p->native_alloc;
   if (p->uploaded) {
     d.bufs = {{p->ops_dev, p->ops_bytes}, {p->rops_dev, p->rops_bytes}, {p->stages_dev, p->stages_bytes},
-              {p->pool_dev, p->pool_bytes}};
+              {p->pool_dev, p->pool_bytes}, {p->dense_w_dev, p->dense_w_bytes}};
   }
   for (auto& u : p->uses) d.events.push_back(u.second);
   if (p->upload_event) d.events.push_back(p->upload_event);
@@ -684,6 +654,8 @@ static qs_status plan_upload(qs_plan* p, cudaStream_t s) {
   p->stages_bytes = p->cr.stages.size() * sizeof(StageRec);
   std::vector<unsigned char> ser = p->cr.pool.serialise(p->pol);
   p->pool_bytes = ser.size();
+  p->dense_w_bytes = p->cr.dense_w.size() * sizeof(float);
+  if (p->dense_w_bytes) p->dense_w_dev = (float*)dev_alloc(p->dense_w_bytes, s);
   if (p->ops_bytes) p->ops_dev = (DevOp*)dev_alloc(p->ops_bytes, s);
   if (p->rops_bytes) p->rops_dev = (RegOp*)dev_alloc(p->rops_bytes, s);
   if (p->stages_bytes) p->stages_dev = (StageRec*)dev_alloc(p->stages_bytes, s);
@@ -692,7 +664,7 @@ static qs_status plan_upload(qs_plan* p, cudaStream_t s) {
   p->native_alloc = dev_alloc_native();
   p->upload_stream = s;
   if ((p->ops_bytes && !p->ops_dev) || (p->pool_bytes && !p->pool_dev) || (p->rops_bytes && !p->rops_dev) ||
-      (p->stages_bytes && !p->stages_dev))
+      (p->stages_bytes && !p->stages_dev) || (p->dense_w_bytes && !p->dense_w_dev))
     return fail(QS_ENOMEM, "plan upload allocation failed");
   // pageable sources: each copy has read its source when the call returns
   cudaError_t e = cudaSuccess;
@@ -702,6 +674,8 @@ static qs_status plan_upload(qs_plan* p, cudaStream_t s) {
   if (e == cudaSuccess && p->stages_bytes)
     e = cudaMemcpyAsync(p->stages_dev, p->cr.stages.data(), p->stages_bytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && p->pool_bytes) e = cudaMemcpyAsync(p->pool_dev, ser.data(), p->pool_bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && p->dense_w_bytes)
+    e = cudaMemcpyAsync(p->dense_w_dev, p->cr.dense_w.data(), p->dense_w_bytes, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->upload_event, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(p->upload_event, s);
   if (e != cudaSuccess) return cuda_fail(e, "plan upload");
@@ -725,6 +699,15 @@ static qs_status execute_steps(qs_handle h, qs_plan_t p) {
     } else if (s.kind == ST_RENORM) {
       qs_status st = renormalize(h);
       if (st != QS_OK) return st;
+    } else if (s.kind == ST_DENSE) {
+      if (!h->num_sms) {
+        int dev = 0;
+        CUDA_TRY(cudaGetDevice(&dev), "device query");
+        CUDA_TRY(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+      }
+      const float* w = p->dense_w_dev + (size_t)s.dense_idx * kDenseWFloats;
+      CUDA_TRY(timed(h, name, s.bytes, [&] { return launch_dense_mma(h->psi, h->n, w, h->status_dev, h->num_sms, h->stream); }),
+               "dense block launch");
     } else {
       qs_status st = do_permute(h, s.src_of, s.perm, s.bytes);
       if (st != QS_OK) return st;

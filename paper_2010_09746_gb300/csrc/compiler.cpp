@@ -18,6 +18,40 @@
 namespace qs {
 
 int default_tile_bits(int dtype) { return dtype == QS_C128 ? 12 : 13; }
+
+// Per-launch cost coefficients measured on GB300 (ms, ms per byte, ms per counted
+// instruction): HBM-bound kernels at the bandwidth they reach (tile-pass floor ~6.5 TB/s,
+// per-gate ~6.4, permutation ~5.7, dense tensor-core block 3.6 ms per 17.2 GB); the tile
+// passes' arithmetic from the 30-qubit circuits (complex64 ~395 ms, double-float ~2030 ms per
+// circuit, less their HBM floor, over the counted instructions); native FP64 at 1.7 DFMA
+// per clock per SM.
+qs_cost_model default_cost_model(Policy pol) {
+  qs_cost_model m{};
+  const double tile_alu = pol == POL_F32 ? 7.2e-11 : (pol == POL_DF ? 4.12e-11 : 1.87e-9);
+  const double c_tile[3] = {0.005, 1.0 / 6.5e9, tile_alu};
+  const double c_gate[3] = {0.005, 1.0 / 6.4e9, pol == POL_F64 ? 1.87e-9 : 0.0};
+  const double c_perm[3] = {0.005, 1.0 / 5.7e9, 0.0};
+  const double c_dense[3] = {0.005, 3.6 / 17.18e9, 0.0};
+  for (int i = 0; i < 3; i++) {
+    m.tile[i] = c_tile[i];
+    m.gate[i] = c_gate[i];
+    m.permute[i] = c_perm[i];
+    m.dense[i] = c_dense[i];
+  }
+  return m;
+}
+
+double step_cost_ms(const qs_cost_model& m, const Step& s) {
+  const double* c = nullptr;
+  switch (s.kind) {
+    case ST_PASS: c = m.tile; break;
+    case ST_GATE: c = m.gate; break;
+    case ST_PERMUTE: c = m.permute; break;
+    case ST_DENSE: c = m.dense; break;
+    case ST_RENORM: return s.bytes * m.gate[1] + 2 * m.gate[0];
+  }
+  return c[0] + c[1] * s.bytes + c[2] * s.alu;
+}
 int default_low_bits(int dtype) { return dtype == QS_C128 ? 3 : 4; }
 
 bool normalize_compile_opts(int n, qs_compile_opts* o, std::string* err) {
@@ -27,7 +61,7 @@ bool normalize_compile_opts(int n, qs_compile_opts* o, std::string* err) {
   };
   if (o->dtype != QS_C64 && o->dtype != QS_C128) return bad("unknown dtype");
   if (o->mode < QS_MODE_PERGATE || o->mode > QS_MODE_TILE) return bad("unknown mode");
-  if (o->flags & ~QS_FLAG_FULL_RX) return bad("unknown flags");
+  if (o->flags & ~(QS_FLAG_FULL_RX | QS_FLAG_NO_DENSE)) return bad("unknown flags");
   if (o->reg_bits < 0 || o->reg_bits > 5) return bad("reg_bits must be in [0, 5]");
   if (o->renorm_every < 0) return bad("renorm_every must be >= 0");
   if (o->tile_bits == 0) o->tile_bits = default_tile_bits(o->dtype);
@@ -146,6 +180,23 @@ struct Sched {
   int closure(uint64_t local, const std::vector<uint64_t>& ndm, std::vector<char>& tmp) const {
     return closure(local, ndm, tmp, 1 << 30, [](int) { return false; });
   }
+  // the gates that sweep would schedule, in program order (nothing is marked)
+  std::vector<int> collect(uint64_t local, const std::vector<uint64_t>& mask, std::vector<char>& tmp) const {
+    std::vector<int> ids;
+    for (int v : rem) {
+      bool ok = (mask[v] & ~local) == 0;
+      if (ok)
+        for (int p : preds[v])
+          if (!done[p] && !tmp[p]) {
+            ok = false;
+            break;
+          }
+      tmp[v] = ok;
+      if (ok) ids.push_back(v);
+    }
+    for (int v : rem) tmp[v] = 0;
+    return ids;
+  }
 };
 
 double gate_bytes(const HGate& g, int n, int store_bytes) {
@@ -196,6 +247,16 @@ bool emit_pass(int n, int L, int c, const std::vector<int>& tbits_sorted, const 
   if (ops.empty()) return true;   // identity gates only
   st.pass.K = register_bits(out->store_bytes == 16 ? QS_C128 : QS_C64, L, out->reg_bits);
   build_stages(ops, L, st.pass.K, out, &st.pass.st0, &st.pass.nst);
+  bool lite = true;
+  for (int k = st.pass.st0; k < st.pass.st0 + st.pass.nst && lite; k++) {
+    const StageRec& sr = out->stages[k];
+    if (sr.kind != 0) continue;
+    for (int i = sr.op0; i < sr.op0 + sr.nops; i++) {
+      const int t = out->reg_ops[i].type;
+      if (t != OP_RXTM && t != OP_DTAB && t != OP_PHASE && t != OP_RX) lite = false;
+    }
+  }
+  if (lite) st.pass.flags |= kPassLite;
   const int store_bytes = out->store_bytes;
   st.bytes = 2.0 * (double)store_bytes * (double)(1ull << n);
   st.alu = stage_alu_per_amp(*out, st.pass.st0, st.pass.nst) * (double)(1ull << n);
@@ -235,6 +296,63 @@ bool emit_permute(int n, const std::vector<int>& sigma, const std::vector<int>& 
   st.bytes = 2.0 * (double)store_bytes * (double)(1ull << n);
   out->steps.push_back(std::move(st));
   return true;
+}
+
+// Fuse gates that act only on storage bits 0..5 into one 64 x 64 unitary (row / column index =
+// those bits) and emit it as a dense tensor-core step.
+void emit_dense(int n, const std::vector<int>& ids, const std::vector<HGate>& gates, const std::vector<int>& sigma,
+                int store_bytes, CompileResult* out) {
+  constexpr int D = 64;
+  std::vector<cd> M(D * D, cd(0, 0));
+  for (int i = 0; i < D; i++) M[i * D + i] = 1.0;
+  std::vector<cd> x(D), y(D);
+  for (int v : ids) {   // M <- G M, one column at a time
+    const HGate& g = gates[v];
+    const int k = g.nq, dk = 1 << k;
+    int pos[6];
+    uint32_t mask = 0;
+    for (int t = 0; t < k; t++) {
+      pos[t] = sigma[g.q[t]];
+      mask |= 1u << pos[t];
+    }
+    for (int col = 0; col < D; col++) {
+      for (int i = 0; i < D; i++) x[i] = M[i * D + col];
+      y = x;
+      for (int base = 0; base < D; base++) {
+        if (base & mask) continue;
+        for (int r = 0; r < dk; r++) {
+          int ir = base;
+          for (int t = 0; t < k; t++)
+            if ((r >> t) & 1) ir |= 1 << pos[t];
+          cd acc(0, 0);
+          for (int c = 0; c < dk; c++) {
+            int ic = base;
+            for (int t = 0; t < k; t++)
+              if ((c >> t) & 1) ic |= 1 << pos[t];
+            acc += g.U[r * dk + c] * x[ic];
+          }
+          y[ir] = acc;
+        }
+      }
+      for (int i = 0; i < D; i++) M[i * D + col] = y[i];
+    }
+  }
+  Step st;
+  st.kind = ST_DENSE;
+  st.dense_idx = (int32_t)(out->dense_u.size() / (D * D));
+  st.bytes = 2.0 * (double)store_bytes * (double)(1ull << n);
+  out->dense_u.insert(out->dense_u.end(), M.begin(), M.end());
+  std::vector<double> flat(2 * D * D);
+  for (int i = 0; i < D * D; i++) {
+    flat[2 * i] = M[i].real();
+    flat[2 * i + 1] = M[i].imag();
+  }
+  const int bits[6] = {0, 1, 2, 3, 4, 5};
+  const size_t w0 = out->dense_w.size();
+  out->dense_w.resize(w0 + kDenseWFloats);
+  dense_mma_weights(flat.data(), 6, bits, out->dense_w.data() + w0);
+  out->steps.push_back(std::move(st));
+  out->stats.n_dense++;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -391,7 +509,41 @@ bool compile_tile(int n, const std::vector<HGate>& gates, const std::vector<int>
       *err = "gate " + std::to_string(v) + " needs more qubits than a tile holds";
       return false;
     }
+  // dense blocks on the tensor cores (complex64): every gate's full storage-bit set
+  const bool dense_ok = out->pol == POL_F32 && !(o.flags & QS_FLAG_NO_DENSE) && n >= dense_mma_min_qubits();
+  std::vector<uint64_t> allq(G, 0);
+  std::vector<double> wsave(G, 0.0);
+  double t_dense = 0;
+  if (dense_ok) {
+    const double S2 = 2.0 * (double)store_bytes * (double)(1ull << n);
+    t_dense = out->cost.dense[0] + out->cost.dense[1] * S2;
+    for (int v = 0; v < G; v++) {
+      for (int t = 0; t < gates[v].nq; t++) allq[v] |= 1ull << sigma[gates[v].q[t]];
+      // tile-pass time the gate would cost: its arithmetic at the tile class's rate
+      wsave[v] = out->cost.tile[2] * gate_tile_alu_per_amp(out->pol, gates[v]) * (double)(1ull << n);
+    }
+  }
   while (S.remaining) {
+    if (dense_ok) {
+      // the gates ready on storage bits 0..5 alone: one dense block if the model says it
+      // is cheaper than leaving them to the tile passes
+      std::vector<int> ids = S.collect(63ull, allq, tmp);
+      double save = 0;
+      for (int v : ids) save += wsave[v];
+      if (!ids.empty() && save > t_dense) {
+        for (int v : ids) {
+          S.mark(v);
+          bool z = true;
+          for (int t = 0; t < gates[v].nq; t++) z &= gates[v].cls[t] == CLS_Z;
+          if (!z) nondiag_left--;
+        }
+        S.compact();
+        out->trace.push_back({5, (int)ids.size()});
+        for (int v : ids) out->trace.push_back({0, v});
+        emit_dense(n, ids, gates, sigma, store_bytes, out);
+        continue;
+      }
+    }
     uint64_t T = low;
     int nt = c;
     // demand: how many frontier gates need each bit
@@ -452,6 +604,7 @@ bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<i
   out->reg_bits = o.reg_bits;
   out->full_rx = (o.flags & QS_FLAG_FULL_RX) != 0;
   out->pol = (o.dtype == QS_C64) ? POL_F32 : (o.arith == QS_ARITH_F64 ? POL_F64 : POL_DF);
+  out->cost = o.cost ? *o.cost : default_cost_model(out->pol);
   out->stats = qs_plan_stats{};
   out->stats.n_gates = (int64_t)gates.size();
   bool ok = true;
@@ -503,6 +656,9 @@ bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<i
   }
   out->stats.hbm_bytes = bytes;
   out->stats.alu_instr = alu;
+  double pred = 0;
+  for (const Step& s : out->steps) pred += step_cost_ms(out->cost, s);
+  out->stats.predicted_ms = pred;
   if (getenv("QS_DEBUG_OPMIX")) {
     long cnt[16] = {0}, slot_only = 0, tb = 0, gb = 0;
     for (const RegOp& r : out->reg_ops) {

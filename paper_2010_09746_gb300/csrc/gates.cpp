@@ -289,4 +289,44 @@ bool lower_gate(const HGate& g, const LowerCtx& ctx, Pool& pool, std::vector<Dev
   return true;
 }
 
+// The real 128 x 128 matrix of a dense k-qubit block on storage bits bits[0..k-1] (a
+// permutation of 0..k-1), replicated over storage bits k..5, transposed (row j = output
+// float j of a 64-amplitude row) and split into its nearest TF32 values and the TF32-rounded
+// remainders.
+void dense_mma_weights(const double* U, int k, const int* bits, float* out) {
+  const int kdim = 1 << k;
+  const int mask = kdim - 1;
+  auto mat_index = [&](int x) {
+    int r = 0;
+    for (int t = 0; t < k; t++) r |= ((x >> bits[t]) & 1) << t;
+    return r;
+  };
+  std::vector<double> wt(128 * 128, 0.0);
+  for (int xr = 0; xr < 64; xr++)
+    for (int xc = 0; xc < 64; xc++) {
+      if ((xr & ~mask) != (xc & ~mask)) continue;
+      const int r = mat_index(xr & mask), c = mat_index(xc & mask);
+      const double a = U[2 * (r * kdim + c)], b = U[2 * (r * kdim + c) + 1];
+      wt[(2 * xr) * 128 + 2 * xc] = a;
+      wt[(2 * xr) * 128 + 2 * xc + 1] = -b;
+      wt[(2 * xr + 1) * 128 + 2 * xc] = b;
+      wt[(2 * xr + 1) * 128 + 2 * xc + 1] = a;
+    }
+  auto tf32_rna = [](double v) {   // nearest TF32 value (ties away from zero), as a float
+    const float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+  };
+  for (int i = 0; i < 128 * 128; i++) {
+    const float big = tf32_rna(wt[i]);
+    out[i] = big;
+    out[128 * 128 + i] = tf32_rna(wt[i] - (double)big);
+  }
+}
+
+
 }  // namespace qs

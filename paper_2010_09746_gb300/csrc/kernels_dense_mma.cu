@@ -392,7 +392,6 @@ __global__ void __launch_bounds__(kBlockThreads, 1)
 
 }  // namespace
 
-int dense_mma_min_qubits() { return 12; }
 
 cudaError_t launch_dense_mma(void* psi, int n, const float* wT_dev, int* status, int num_sms, cudaStream_t s) {
   if (n < 12) return cudaErrorInvalidValue;

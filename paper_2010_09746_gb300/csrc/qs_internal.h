@@ -81,6 +81,9 @@ struct StageRec {
 };
 static_assert(sizeof(StageRec) == 48, "StageRec layout");
 
+// TilePass.flags: every register op of the pass is OP_RXTM, OP_DTAB, OP_PHASE or OP_RX
+constexpr int32_t kPassLite = 1;
+
 // Tile pass launch description.
 struct TilePass {
   int32_t L;          // tile bits
@@ -88,6 +91,7 @@ struct TilePass {
   int32_t n;
   int32_t K;          // register bits per thread in register stages
   int32_t st0, nst;   // stage range in the plan's stage array
+  int32_t flags;      // kPass* bits
   int32_t tpos[kMaxTileBits];        // storage positions of tile bits, ascending
   int32_t npos[kMaxQubits];          // storage positions of the other bits, ascending
 };
@@ -100,13 +104,14 @@ struct BatchPass {
 };
 
 // One plan step.
-enum StepKind : int32_t { ST_PASS = 0, ST_GATE = 1, ST_PERMUTE = 2, ST_RENORM = 3 };
+enum StepKind : int32_t { ST_PASS = 0, ST_GATE = 1, ST_PERMUTE = 2, ST_RENORM = 3, ST_DENSE = 4 };
 struct Step {
   StepKind kind;
   TilePass pass{};           // ST_PASS
   DevOp op{};                // ST_GATE (storage bits)
   std::vector<int> perm;     // ST_PERMUTE: new sigma (logical -> storage)
   std::vector<int> src_of;   // ST_PERMUTE: storage bit p of the output takes input bit src_of[p]
+  int32_t dense_idx = -1;    // ST_DENSE: block index into CompileResult::dense_w / dense_u
   double bytes = 0;          // algorithmic HBM bytes
   double alu = 0;            // arithmetic instructions the policy's formulas need (all amplitudes)
 };
@@ -144,7 +149,8 @@ int inner_num_partials();
 // 64 amplitudes times the 128 x 128 real matrix whose transpose's TF32 split (big, small;
 // 2 x 128 x 128 floats) is at wT_dev.  n >= dense_mma_min_qubits().
 cudaError_t launch_dense_mma(void* psi, int n, const float* wT_dev, int* status, int num_sms, cudaStream_t s);
-int dense_mma_min_qubits();
+constexpr int kDenseMinQubits = 12;   // the tensor-core kernel needs rows of 64 amplitudes x 64
+inline int dense_mma_min_qubits() { return kDenseMinQubits; }
 // psi *= 1 / sqrt(*norm_dev), skipped on the device if *norm_dev is not positive and finite.
 cudaError_t launch_scale(void* psi, int n, int is_c128, const double* norm_dev, cudaStream_t s);
 
@@ -203,11 +209,29 @@ struct CompileResult {
   std::vector<RegOp> reg_ops;    // register-stage ops of all passes
   std::vector<StageRec> stages;  // stages of all passes
   Pool pool;
+  // ST_DENSE blocks: the fused 64 x 64 unitary on storage bits 0..5 (row / column index =
+  // those bits), and the tensor-core kernel's operand made from it (kDenseWFloats each)
+  std::vector<cd> dense_u;
+  std::vector<float> dense_w;
+  qs_cost_model cost{};          // the model the compiler used (also for predicted_ms)
   std::vector<int> sigma_final;
   qs_plan_stats stats{};
 };
 bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<int>& sigma0,
                      const qs_compile_opts& o, CompileResult* out, std::string* err);
+
+// Cost model the compiler uses when the caller gives none: per-launch coefficients measured
+// on GB300 for the policy's kernels.
+qs_cost_model default_cost_model(Policy pol);
+// predicted time of one step under a model
+double step_cost_ms(const qs_cost_model& m, const Step& s);
+
+// Floats of one dense block operand: W^T of the real 128 x 128 matrix, split into its nearest
+// TF32 values and the TF32-rounded remainders.
+constexpr size_t kDenseWFloats = 2 * 128 * 128;
+// That operand for the 2^k x 2^k complex block U (row / column r = sum_t b(q_t) 2^t) whose qubit
+// t sits on storage bit bits[t] (a permutation of 0..k-1), replicated over storage bits k..5.
+void dense_mma_weights(const double* U, int k, const int* bits, float* out);
 
 // Dependency DAG with commutation-pruned edges: immediate predecessors per gate.
 std::vector<std::vector<int>> build_dag(const std::vector<HGate>& gates);
@@ -231,5 +255,8 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
 double stage_alu_per_amp(const CompileResult& cr, int st0, int nst);
 // the same for one per-gate op
 double op_alu_per_amp(Policy pol, const DevOp& op);
+// arithmetic per amplitude a gate adds to a tile pass (register stages, tables shared by
+// several diagonal gates): the compiler's estimate of what moving it elsewhere saves
+double gate_tile_alu_per_amp(Policy pol, const HGate& g);
 
 }  // namespace qs

@@ -56,6 +56,8 @@ struct qs_plan {
   size_t stages_bytes = 0;
   void* pool_dev = nullptr;
   size_t pool_bytes = 0;
+  float* dense_w_dev = nullptr;           // ST_DENSE operands
+  size_t dense_w_bytes = 0;
   bool uploaded = false;
   bool native_alloc = true;
   cudaStream_t upload_stream = nullptr;   // the device copies were enqueued here ...

@@ -682,4 +682,21 @@ double stage_alu_per_amp(const CompileResult& cr, int st0, int nst) {
   return a;
 }
 
+double gate_tile_alu_per_amp(Policy pol, const HGate& g) {
+  bool diag = true;
+  for (int t = 0; t < g.nq; t++) diag &= g.cls[t] == CLS_Z;
+  int ctl = 0;   // controls restrict the amplitudes touched
+  if (g.kind == QS_OP_CNOT || g.kind == QS_OP_CU || g.kind == QS_OP_CP) ctl = 1;
+  if (diag) {
+    if (g.kind == QS_OP_CZ || g.kind == QS_OP_Z) return 0.0;   // sign flips
+    // diagonal factors merge into register phase tables, typically two or more per table
+    return 0.5 * pick(kMUL, pol) * fraction(g.nq >= 2 ? g.nq - 1 : 0);
+  }
+  if (g.kind == QS_OP_RX && g.nq == 1) return pick(kRXT, pol);
+  if (g.kind == QS_OP_X || g.kind == QS_OP_CNOT || g.kind == QS_OP_SWAP) return 0.0;   // moves
+  if (g.nq == 1 || g.kind == QS_OP_CU) return pick(kU1, pol) * fraction(ctl);
+  if (g.nq == 2) return pick(kU2, pol);
+  return pick(kMACK, pol) * (double)(1 << g.nq);
+}
+
 }  // namespace qs

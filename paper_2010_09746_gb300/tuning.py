@@ -40,12 +40,15 @@ def plan_class_features(plan: Plan, dtype: str) -> Dict[str, Tuple[float, float,
     pol = {"c64": "c64", "c128": "c128_df"}[dtype]
     out = {}
     b_pass, b_perm = 2 * S * s["n_passes"], 2 * S * s["n_permutes"]
+    b_dense = 2 * S * s.get("n_dense", 0)
     if s["n_passes"]:
         out[f"tile_pass_{pol}"] = (float(s["n_passes"]), b_pass, float(s["alu_instr"]))
     if s["n_permutes"]:
         out["permute"] = (float(s["n_permutes"]), b_perm, 0.0)
+    if s.get("n_dense", 0):
+        out["dense_mma_c64"] = (float(s["n_dense"]), b_dense, 0.0)
     if s["n_pergate"]:
-        out[f"gate_{pol}"] = (float(s["n_pergate"]), max(0.0, s["hbm_bytes"] - b_pass - b_perm),
+        out[f"gate_{pol}"] = (float(s["n_pergate"]), max(0.0, s["hbm_bytes"] - b_pass - b_perm - b_dense),
                               0.0 if s["n_passes"] else float(s["alu_instr"]))
     return out
 
@@ -94,6 +97,21 @@ class CostModel:
 
     def to_json(self) -> dict:
         return {"coef_ms_per_launch_byte_alu": self.coef}
+
+    def native(self, dtype: str, arith: str = "auto"):
+        """The fitted coefficients as the compiler's qs_cost_model for plans of this dtype
+        (classes without samples keep the library's defaults), so that qs_compile's choices
+        and its predicted_ms follow the measured kernel times."""
+        from . import default_cost_model
+        m = default_cost_model(dtype, arith)
+        pol = {"c64": "c64", "c128": "c128_f64" if arith == "f64" else "c128_df"}[dtype]
+        for field_, cls in (("tile", f"tile_pass_{pol}"), ("gate", f"gate_{pol}"), ("permute", "permute"),
+                            ("dense", "dense_mma_c64")):
+            if cls in self.coef:
+                arr = getattr(m, field_)
+                for i in range(3):
+                    arr[i] = self.coef[cls][i]
+        return m
 
 
 def circuit_key(n: int, dtype: str, circuit: Sequence) -> str:

@@ -307,8 +307,12 @@ int main(int argc, char** argv) {
   int32_t n = 0, nops = 0;
   int64_t nmats = 0;
   qs_compile_opts o;
+  int32_t has_cost = 0;
+  qs_cost_model cost{};
   bool ok = fread(&n, 4, 1, f) == 1 && fread(&nops, 4, 1, f) == 1 && fread(&nmats, 8, 1, f) == 1 &&
-            fread(&o, sizeof(o), 1, f) == 1;
+            fread(&o, sizeof(o), 1, f) == 1 && fread(&has_cost, 4, 1, f) == 1 &&
+            fread(&cost, sizeof(cost), 1, f) == 1;
+  o.cost = has_cost ? &cost : nullptr;
   std::vector<qs_op> ops(nops);
   std::vector<double> mats(nmats > 0 ? nmats : 1);
   ok = ok && (nops == 0 || fread(ops.data(), sizeof(qs_op), nops, f) == (size_t)nops);
@@ -351,6 +355,19 @@ int main(int argc, char** argv) {
           out[jn] = psi[j];
         }
         psi.swap(out);
+        break;
+      }
+      case ST_DENSE: {   // the fused block on storage bits 0..5, as the compiler built it
+        const C* U = &cr.dense_u[(size_t)s.dense_idx * 64 * 64];
+        for (uint64_t row = 0; row < psi.size(); row += 64) {
+          C x[64];
+          for (int i = 0; i < 64; i++) x[i] = psi[row + i];
+          for (int r = 0; r < 64; r++) {
+            C acc(0, 0);
+            for (int c = 0; c < 64; c++) acc += U[r * 64 + c] * x[c];
+            psi[row + r] = acc;
+          }
+        }
         break;
       }
       case ST_RENORM: {

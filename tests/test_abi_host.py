@@ -34,7 +34,9 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_layout():
     assert ctypes.sizeof(_lib.qs_op) == 48
-    assert ctypes.sizeof(_lib.qs_compile_opts) == 40
+    assert ctypes.sizeof(_lib.qs_compile_opts) == 48
+    assert ctypes.sizeof(_lib.qs_plan_stats) == 80
+    assert ctypes.sizeof(_lib.qs_cost_model) == 96
 
 
 def test_version():
@@ -245,7 +247,7 @@ def test_tangent_rx_lowers_the_count():
         assert a["alu_instr"] < b["alu_instr"]
         assert a["hbm_bytes"] == b["hbm_bytes"] and a["n_passes"] == b["n_passes"]
     o = qs._opts()
-    o.flags = 2
+    o.flags = 4   # no such flag
     h = ctypes.c_void_p()
     ops, nops, mats = qs.marshal(circ[:3])
     assert _lib.load().qs_compile(n, ops, nops, mats.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), mats.size,

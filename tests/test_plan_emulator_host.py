@@ -9,6 +9,7 @@ table, folding or frame mistake gives an O(1) error. The emulation's own roundin
 ~1e-15, so the bound is 1e-10. The GPU parity tests run the same compiled plans on the
 kernels.
 """
+import ctypes
 import os
 import shutil
 import struct
@@ -21,6 +22,7 @@ from oracle import sv
 from workloads import circuits as wc
 
 qs = pytest.importorskip("paper_2010_09746_gb300")
+from paper_2010_09746_gb300 import _lib  # noqa: E402
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -47,13 +49,15 @@ def emulator(tmp_path_factory):
     r = subprocess.run([nvcc, "-std=c++17", "-O2", "-o", exe] + srcs, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]
 
-    def run(n, circ, **opts):
+    def run(n, circ, cost=None, **opts):
         ops, nops, mats = qs.marshal(circ)
         o = qs._opts(**opts)
         inp, out = str(d / "in.bin"), str(d / "out.bin")
         with open(inp, "wb") as f:
             f.write(struct.pack("<iiq", n, nops, mats.size if nops else 0))
             f.write(bytes(o))
+            f.write(struct.pack("<i", 1 if cost is not None else 0))
+            f.write(bytes(cost if cost is not None else _lib.qs_cost_model()))
             f.write(bytes(ops)[: nops * 48])
             if nops:
                 f.write(np.ascontiguousarray(mats, dtype=np.float64).tobytes())
@@ -183,3 +187,61 @@ def test_emulator_sees_a_planted_mistake(emulator):
     wrong[17] = wc.Gate(g.kind, tuple(g.qubits), param=float(g.param) + 1e-3)
     ref_wrong = sv.simulate(n, wrong)
     assert float(np.max(np.abs(got - ref_wrong))) > 1e-6
+
+
+def cheap_dense_model():
+    """A cost model under which dense tensor-core blocks are cheap and tile-pass arithmetic
+    dear, so that the compiler picks dense blocks even on small states."""
+    m = _lib.qs_cost_model()
+    for i, v in enumerate((0.005, 1e-10, 1e-6)):
+        m.tile[i] = v
+    for i, v in enumerate((0.0, 1e-12, 0.0)):
+        m.dense[i] = v
+    for i, v in enumerate((0.005, 1e-10, 0.0)):
+        m.gate[i] = v
+        m.permute[i] = v
+    return m
+
+
+@pytest.mark.parametrize("n", [12, 14])
+def test_dense_blocks_fused_by_the_compiler(emulator, n):
+    """Where the cost model prefers them, gates on storage bits 0..5 leave the tile passes
+    for dense 64 x 64 blocks; the fused blocks reproduce the circuit exactly (in FP64 here;
+    on the GPU the tensor cores add complex64-level rounding)."""
+    circ = wc.rzrx_cz_circuit(n, 8, seed=n) + wc.haar_cnot_circuit(n, 3, seed=n) + \
+        wc.random_mixed_circuit(n, 60, seed=n, kmax=3)
+    ops, nops, mats = qs.marshal(circ)
+    o = qs._opts(mode="tile", dtype="c64")
+    model = cheap_dense_model()
+    o.cost = ctypes.pointer(model)
+    h = ctypes.c_void_p()
+    _lib.check(_lib.load().qs_compile(n, ops, nops, mats.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), mats.size,
+                                      None, ctypes.byref(o), ctypes.byref(h)))
+    st = _lib.qs_plan_stats()
+    _lib.check(_lib.load().qs_plan_get_stats(h, ctypes.byref(st)))
+    _lib.load().qs_plan_destroy(h)
+    assert st.n_dense > 0 and st.predicted_ms > 0
+    got, _ = emulator(n, circ, cost=model, mode="tile", dtype="c64")
+    check(got, circ, n)
+
+
+def test_no_dense_flag_and_default_model(emulator):
+    """QS_FLAG_NO_DENSE keeps every gate in tile passes; the default model picks no dense
+    block on a small state (the launch would cost more than the arithmetic it saves), and
+    complex128 plans never get one."""
+    n = 14
+    circ = wc.rzrx_cz_circuit(n, 8, seed=3)
+    for dtype, kw, want in (("c64", {}, 0), ("c64", {"flags": _lib.QS_FLAG_NO_DENSE}, 0), ("c128", {}, 0)):
+        model = cheap_dense_model() if kw or dtype == "c128" else None
+        ops, nops, mats = qs.marshal(circ)
+        o = qs._opts(mode="tile", dtype=dtype)
+        o.flags |= kw.get("flags", 0)
+        if model is not None:
+            o.cost = ctypes.pointer(model)
+        h = ctypes.c_void_p()
+        _lib.check(_lib.load().qs_compile(n, ops, nops, mats.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          mats.size, None, ctypes.byref(o), ctypes.byref(h)))
+        st = _lib.qs_plan_stats()
+        _lib.check(_lib.load().qs_plan_get_stats(h, ctypes.byref(st)))
+        _lib.load().qs_plan_destroy(h)
+        assert st.n_dense == want, (dtype, kw)
