@@ -319,12 +319,11 @@ class State:
 class Batch:
     """Many independent circuits run together (qs_batch_create): list of (n, circuit)."""
 
-    def __init__(self, circuits, dtype="c64", stream=None, graph=True, **opts):
-        L = _L()
+    @staticmethod
+    def marshal(circuits):
+        """(n list, qs_op array, op offsets, matrix doubles) of a list of (n, circuit): the
+        arrays qs_batch_create takes; pass them as `marshalled` to skip this step."""
         circuits = list(circuits)
-        self.count = len(circuits)
-        self.ns = [int(n) for n, _ in circuits]
-        self.dtype = _DTYPES[dtype]
         allg = []
         offs = [0]
         for _, c in circuits:
@@ -332,6 +331,14 @@ class Batch:
             allg.extend(c)
             offs.append(offs[-1] + len(c))
         ops, nops, mats = marshal(allg)
+        return [int(n) for n, _ in circuits], ops, offs, mats
+
+    def __init__(self, circuits=None, dtype="c64", stream=None, graph=True, marshalled=None, **opts):
+        L = _L()
+        ns, ops, offs, mats = marshalled if marshalled is not None else Batch.marshal(circuits)
+        self.count = len(ns)
+        self.ns = list(ns)
+        self.dtype = _DTYPES[dtype]
         n_arr = np.ascontiguousarray(self.ns, dtype=np.int32)
         off_arr = np.ascontiguousarray(offs, dtype=np.int64)
         o = _opts(dtype=dtype, **opts)

@@ -504,6 +504,7 @@ bool compile_tile(int n, const std::vector<HGate>& gates, const std::vector<int>
     if (!z) nondiag_left++;
   }
   auto deferred = [&](int v, uint64_t T) { return allz[v] && (qmask[v] & T) == 0 && nondiag_left > 0; };
+  std::vector<uint64_t> okm(G, 0);   // candidate-bit masks of the pass search
   for (int v = 0; v < G; v++)
     if (__builtin_popcountll(ndm[v] | low) > L) {
       *err = "gate " + std::to_string(v) + " needs more qubits than a tile holds";
@@ -553,13 +554,28 @@ bool compile_tile(int n, const std::vector<HGate>& gates, const std::vector<int>
         for (int b = 0; b < n; b++)
           if ((ndm[v] >> b) & 1) demand[b]++;
     while (nt < L) {
+      // one program-order sweep scores every candidate bit b at once: okm[v] has bit b set
+      // iff gate v would be scheduled in a pass over T | b (its non-diagonal bits covered,
+      // not deferred, every unfinished predecessor scheduled as well)
+      const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+      const uint64_t cand = all & ~T;
+      int score[64] = {0};
+      for (int v : S.rem) {
+        const uint64_t miss = ndm[v] & ~T;
+        uint64_t m = (miss == 0) ? cand : ((miss & (miss - 1)) == 0 ? (miss & cand) : 0ull);
+        if (m && allz[v] && nondiag_left > 0 && !(qmask[v] & T)) m &= qmask[v];   // deferred unless b is one of its bits
+        for (int p : S.preds[v]) {
+          if (!m) break;
+          if (!S.done[p]) m &= okm[p];
+        }
+        okm[v] = m;
+        for (uint64_t mm = m; mm; mm &= mm - 1) score[__builtin_ctzll(mm)]++;
+      }
       int best_b = -1, best_s = -1, best_d = -1;
       for (int b = 0; b < n; b++) {
         if ((T >> b) & 1) continue;
-        const uint64_t T2 = T | (1ull << b);
-        const int s = S.closure(T2, ndm, tmp, 1 << 30, [&](int v) { return deferred(v, T2); });
-        if (s > best_s || (s == best_s && demand[b] > best_d)) {
-          best_s = s;
+        if (score[b] > best_s || (score[b] == best_s && demand[b] > best_d)) {
+          best_s = score[b];
           best_d = demand[b];
           best_b = b;
         }

@@ -412,6 +412,7 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
     preds[j].erase(std::unique(preds[j].begin(), preds[j].end()), preds[j].end());
   }
   std::vector<char> done(N, 0), tmp(N, 0);
+  std::vector<uint32_t> okm(N, 0);   // candidate-bit masks of the stage search
   std::vector<int> rem(N);
   for (int i = 0; i < N; i++) rem[i] = i;
   *st0 = (int)out->stages.size();
@@ -431,22 +432,11 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
     return !info[v].smem_only && info[v].need == 0 && info[v].tbits != 0 && (info[v].tbits & R) == 0 &&
            nondiag_left > 0;
   };
-  auto closure = [&](uint32_t R) {
-    int cnt = 0;
-    for (int v : rem) {
-      bool ok = !info[v].smem_only && (info[v].need & ~R) == 0 && !deferred(v, R);
-      if (ok)
-        for (int p : preds[v])
-          if (!done[p] && !tmp[p]) {
-            ok = false;
-            break;
-          }
-      tmp[v] = ok;
-      cnt += ok;
-    }
-    for (int v : rem) tmp[v] = 0;
-    return cnt;
-  };
+  // A stage's choice only looks at the first kWindow remaining ops: rem is in program order
+  // and an op's predecessors come before it, so the count over that prefix is exact for the
+  // ops in it, and the ops further on rarely change which register bits win.  It bounds the
+  // search to O(kWindow) per candidate instead of O(ops in the pass).
+  constexpr size_t kWindow = 768;
   while (!rem.empty()) {
     // the earliest ready op
     int first = -1;
@@ -487,21 +477,42 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
           break;
         }
       while (nr < K) {
+        // one sweep scores every candidate bit b at once: okm[v] has bit b set iff op v
+        // would be scheduled with register bits R | b (its needs covered, not deferred,
+        // every unfinished predecessor scheduled as well)
+        const uint32_t all = (L >= 32) ? 0xFFFFFFFFu : ((1u << L) - 1u);
+        const uint32_t cand = all & ~R;
+        const size_t lim = std::min(rem.size(), kWindow);
+        int score[32] = {0};
+        int rank[32];
+        for (int b = 0; b < 32; b++) rank[b] = 1 << 30;
+        for (size_t r = 0; r < lim; r++) {
+          const int v = rem[r];
+          const OpInfo& in = info[v];
+          uint32_t m = 0;
+          if (!in.smem_only) {
+            const uint32_t miss = in.need & ~R;
+            m = (miss == 0) ? cand : ((miss & (miss - 1)) == 0 ? (miss & cand) : 0u);
+            if (m && !in.need && in.tbits && nondiag_left > 0 && !(in.tbits & R)) m &= in.tbits;   // deferred unless b holds one of its bits
+            for (int p : preds[v]) {
+              if (!m) break;
+              if (!done[p]) m &= okm[p];
+            }
+          }
+          okm[v] = m;
+          for (uint32_t mm = m; mm; mm &= mm - 1) score[__builtin_ctz(mm)]++;
+          for (uint32_t nb = in.need & cand; nb; nb &= nb - 1) {
+            const int b = __builtin_ctz(nb);
+            if (rank[b] == (1 << 30)) rank[b] = (int)r;
+          }
+        }
         int best = -1, best_s = -1, best_rank = 1 << 30;
         for (int b = 0; b < L; b++) {
           if ((R >> b) & 1u) continue;
-          const int s = closure(R | (1u << b));
-          // rank: position of the earliest remaining op needing b
-          int rank = 1 << 30;
-          for (size_t r = 0; r < rem.size(); r++)
-            if ((info[rem[r]].need >> b) & 1u) {
-              rank = (int)r;
-              break;
-            }
-          if (s > best_s || (s == best_s && rank < best_rank)) {
+          if (score[b] > best_s || (score[b] == best_s && rank[b] < best_rank)) {
             best = b;
-            best_s = s;
-            best_rank = rank;
+            best_s = score[b];
+            best_rank = rank[b];
           }
         }
         R |= 1u << best;
@@ -630,6 +641,11 @@ const Cost kRXT{2, 2, 24};      // one real product and a sum per component (tan
 const Cost kMUL{4, 4, 32};      // complex multiply (diagonal factor, table entry)
 const Cost kU1{8, 8, 80};       // two complex products and a sum
 const Cost kNEG{0, 0, 0};       // sign flips
+// amplitude moves (X / CNOT targets, SWAP) do no arithmetic but cost instructions of the
+// same order: register shuffles, and in the double-float phase frame a quarter-turn (lane
+// swap and sign flips) of each moved amplitude.  Counted as instruction equivalents so that
+// circuits made mostly of moves are not predicted free.
+const Cost kMOVE{2, 2, 8};
 const Cost kU2{16, 16, 172};    // per amplitude of a 4x4 block
 const Cost kMACK{4, 4, 46};     // per amplitude per column of a 2^k block
 const Cost kCONV{0, 0, 72};     // FP64 <-> (hi, lo) split / join per pass
@@ -647,6 +663,8 @@ double op_alu_per_amp(Policy pol, const DevOp& o) {
     case OP_PHASE: return (o.mat < 0 ? pick(kNEG, pol) : pick(kMUL, pol)) * fraction(ctl);
     case OP_U2: return pick(kU2, pol) * fraction(ctl);
     case OP_DENSE: return pick(kMACK, pol) * (double)(1 << o.nk) * fraction(ctl);
+    case OP_X: return pick(kMOVE, pol) * fraction(ctl);
+    case OP_SWAP: return pick(kMOVE, pol) * fraction(ctl + 1);
     default: return 0.0;
   }
 }
@@ -675,6 +693,7 @@ double stage_alu_per_amp(const CompileResult& cr, int st0, int nst) {
           break;
         case OP_PHASE: a += (r.neg ? pick(kNEG, cr.pol) : pick(kMUL, cr.pol)) * fraction(ctl); break;
         case OP_U2: a += pick(kU2, cr.pol) * fraction(ctl); break;
+        case OP_X: a += pick(kMOVE, cr.pol) * fraction(ctl); break;
         default: break;
       }
     }
@@ -693,7 +712,9 @@ double gate_tile_alu_per_amp(Policy pol, const HGate& g) {
     return 0.5 * pick(kMUL, pol) * fraction(g.nq >= 2 ? g.nq - 1 : 0);
   }
   if (g.kind == QS_OP_RX && g.nq == 1) return pick(kRXT, pol);
-  if (g.kind == QS_OP_X || g.kind == QS_OP_CNOT || g.kind == QS_OP_SWAP) return 0.0;   // moves
+  if (g.kind == QS_OP_X) return pick(kMOVE, pol);
+  if (g.kind == QS_OP_CNOT) return pick(kMOVE, pol) * fraction(1);
+  if (g.kind == QS_OP_SWAP) return pick(kMOVE, pol) * fraction(1);
   if (g.nq == 1 || g.kind == QS_OP_CU) return pick(kU1, pol) * fraction(ctl);
   if (g.nq == 2) return pick(kU2, pol);
   return pick(kMACK, pol) * (double)(1 << g.nq);

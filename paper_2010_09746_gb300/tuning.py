@@ -209,8 +209,9 @@ def autotune_batch(work, dtype: str = "c64", tile_bits: Sequence[int] = (11, 12,
     from . import Batch
     stream = torch.cuda.Stream()
     res = []
+    arrays = Batch.marshal(work)   # once for every candidate
     for L in tile_bits:
-        b = Batch(work, dtype=dtype, stream=stream, tile_bits=L)
+        b = Batch(dtype=dtype, stream=stream, tile_bits=L, marshalled=arrays)
         for _ in range(2):
             b.run()
         b.sync()
