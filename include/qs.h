@@ -418,6 +418,18 @@ qs_status qs_get_amplitudes(qs_handle h, void* out, uint64_t first, uint64_t cou
  * interleaved, the state's dtype); for checkpoint / restore and tests. */
 qs_status qs_set_amplitudes(qs_handle h, const void* in);
 
+/* Copy storage elements first .. first+count-1 between the state and DEVICE memory `dev`
+ * (interleaved, the state's dtype): to_state = 0 reads the state into dev, 1 writes dev into
+ * the state.  Enqueued on the state's stream, which the call synchronises before returning
+ * (so another stream or a communication library may use `dev` at once).  Used to exchange
+ * halves of a state slice between processes (global-qubit sharding, Sec. 2 / Appendix A). */
+qs_status qs_copy_range_device(qs_handle h, void* dev, uint64_t first, uint64_t count, int to_state);
+
+/* The full matrix of one gate as the library defines it: 2^k x 2^k complex entries, row-major,
+ * (re, im) pairs, row / column r = sum_t b(op->q[t]) 2^t, written to U_out (room for 2 * 4^6
+ * doubles); *k_out = k.  op and mats as for qs_compile (n bounds the qubit indices). */
+qs_status qs_gate_matrix(int n, const qs_op* op, const double* mats, size_t nmats, double* U_out, int* k_out);
+
 /* sum_i |alpha_i|^2 accumulated in FP64 with a fixed reduction order (deterministic).
  * Synchronises the stream. */
 qs_status qs_norm(qs_handle h, double* out);

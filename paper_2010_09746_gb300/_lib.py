@@ -126,6 +126,8 @@ SIGNATURES = {
     "qs_probabilities": (_I, [_H, _DP, _I]),
     "qs_get_amplitudes": (_I, [_H, _P, ctypes.c_uint64, ctypes.c_uint64, _I]),
     "qs_set_amplitudes": (_I, [_H, _P]),
+    "qs_copy_range_device": (_I, [_H, _P, ctypes.c_uint64, ctypes.c_uint64, _I]),
+    "qs_gate_matrix": (_I, [_I, ctypes.POINTER(qs_op), _DP, ctypes.c_size_t, _DP, _IP]),
     "qs_norm": (_I, [_H, _DP]),
     "qs_norm_noalloc": (_I, [_P, _I, _I, _P, _P]),
     "qs_inner": (_I, [_H, _H, _DP]),

@@ -792,6 +792,34 @@ qs_status qs_set_amplitudes(qs_handle h, const void* in) {
   return QS_OK;
 }
 
+qs_status qs_copy_range_device(qs_handle h, void* dev, uint64_t first, uint64_t count, int to_state) {
+  if (!h || (!dev && count)) return fail(QS_EINVAL, "null argument");
+  const uint64_t N = 1ull << h->n;
+  if (first > N || count > N - first) return fail(QS_EINVAL, "range out of bounds");
+  if (count == 0) return QS_OK;
+  char* st = (char*)h->psi + first * h->store_bytes;
+  const size_t bytes = (size_t)count * h->store_bytes;
+  CUDA_TRY(cudaMemcpyAsync(to_state ? (void*)st : dev, to_state ? (const void*)dev : (const void*)st, bytes,
+                           cudaMemcpyDeviceToDevice, h->stream),
+           "range copy");
+  CUDA_TRY(cudaStreamSynchronize(h->stream), "range copy sync");
+  return QS_OK;
+}
+
+qs_status qs_gate_matrix(int n, const qs_op* op, const double* mats, size_t nmats, double* U_out, int* k_out) {
+  if (!op || !U_out || !k_out) return fail(QS_EINVAL, "null argument");
+  if (n < 1 || n > kMaxQubits) return fail(QS_EINVAL, "n must be in [1, 36]");
+  HGate g;
+  std::string err;
+  if (!make_hgate(n, *op, mats, nmats, &g, &err)) return fail(QS_EINVAL, err);
+  for (size_t i = 0; i < g.U.size(); i++) {
+    U_out[2 * i] = g.U[i].real();
+    U_out[2 * i + 1] = g.U[i].imag();
+  }
+  *k_out = g.nq;
+  return QS_OK;
+}
+
 qs_status qs_norm(qs_handle h, double* out) {
   if (!h || !out) return fail(QS_EINVAL, "null argument");
   const int np = norm_num_partials();
