@@ -380,6 +380,16 @@ def run_ours(args):
         "roofline": roof, "gpu_launches": launches, "kernels": kstats, "clocks": clk,
     }
 
+    def section(key, fn):
+        """A side measurement: its failure is recorded in the line instead of losing it."""
+        try:
+            out[key] = fn()
+        except Exception as e:  # noqa: BLE001
+            import traceback
+            traceback.print_exc()
+            out[key] = {"error": f"{type(e).__name__}: {e}"}
+            torch.cuda.synchronize()
+
     # ---- e2e: host circuit -> compile -> execute -> read back, every step
     if not args.no_e2e:
         ops, nops, mats = qs.marshal(circ)
@@ -423,27 +433,27 @@ def run_ours(args):
                                        reg_bits=args.reg_bits),
                           "pergate": {"mode": "pergate"}, "paper_alg1_m12": {"mode": "paper", "tile_bits": 12}})
         if args.workload == "rzrx30":
-            out["cost_model"] = fit_cost_model(qs, torch, st, stream, args, {
+            section("cost_model", lambda: fit_cost_model(qs, torch, st, stream, args, {
                 "tile": (plan, ms, kstats, args.steps), "pergate": (p_pg, ms_pg, ks_pg, 1),
-                "paper_alg1_m12": (p_pa, ms_pa, ks_pa, 1)})
+                "paper_alg1_m12": (p_pa, ms_pa, ks_pa, 1)}))
     if args.modes and args.workload == "rzrx30":
-        out["permute"] = measure_permute(qs, torch, st, stream, n, (1 << n) * (16 if args.dtype == "c128" else 8))
+        section("permute", lambda: measure_permute(qs, torch, st, stream, n, (1 << n) * (16 if args.dtype == "c128" else 8)))
     if args.small and args.workload == "rzrx30":
-        out["haar_cnot_12q"] = measure_small(qs, torch, args)
+        section("haar_cnot_12q", lambda: measure_small(qs, torch, args))
     if args.qft and args.workload == "rzrx30":
-        out["qft_like"] = measure_qft_like(qs, torch, st, stream, args)
+        section("qft_like", lambda: measure_qft_like(qs, torch, st, stream, args))
     if args.batched:
-        out["batched"] = measure_batched(qs, torch, args)
+        section("batched", lambda: measure_batched(qs, torch, args))
     if args.dense and args.workload == "rzrx30":
-        out["dense_k"] = measure_dense(qs, torch, args)
+        section("dense_k", lambda: measure_dense(qs, torch, args))
     if args.precision and args.workload == "rzrx30":
         st.close()
         torch.cuda.empty_cache()
-        out["precision"] = measure_precision(qs, torch, args)
+        section("precision", lambda: measure_precision(qs, torch, args))
     if args.serve_requests:
-        out["serving"] = measure_serving(args)
+        section("serving", lambda: measure_serving(args))
     if args.cpu_baseline and rank == 0 and world == 1:
-        out["cpu_baseline"] = cpu_baseline(args, n, circ)
+        section("cpu_baseline", lambda: cpu_baseline(args, n, circ))
     if pg:
         pg.destroy_process_group()
     return out, rank
@@ -749,6 +759,7 @@ def measure_serving(args):
     complex128 with probability 1/2), Poisson arrivals.  First all requests at once (the
     saturation throughput), then Poisson arrivals at fixed fractions of that throughput;
     latency = arrival -> result (FP64 norm and first amplitudes) in host memory."""
+    import paper_2010_09746_gb300 as qs
     from paper_2010_09746_gb300 import serve
     budget = int(args.serve_mem_gib * (1 << 30))
 
