@@ -68,3 +68,53 @@ def test_sjf_order_same_results():
     b = serve.Server(slots=2, readout=1 << 15, order="sjf").run(reqs, realtime=False)
     for rid in range(len(reqs)):
         assert a[rid].amplitudes.tobytes() == b[rid].amplitudes.tobytes()
+
+
+def test_server_c_calls_failure_and_take_semantics():
+    """Through the C calls directly: a request whose circuit does not compile comes back with
+    its status and message (the others are unaffected); a result is taken once; poll with
+    max = 0 reports nothing and keeps results for later."""
+    import ctypes
+    from paper_2010_09746_gb300 import _lib
+    L = _lib.load()
+    o = _lib.qs_server_opts()
+    o.slots = 2
+    o.readout = 8
+    h = ctypes.c_void_p()
+    _lib.check(L.qs_server_create(ctypes.byref(o), ctypes.byref(h)))
+    try:
+        good = wc.rzrx_cz_circuit(10, 3, seed=1)
+        bad = [wc.Gate("H", (0,))]
+        ids = []
+        for n, circ in ((10, good), (4, bad), (10, good)):
+            ops, nops, mats = qs.marshal(circ)
+            if circ is bad:
+                ops[0].q[0] = 7   # qubit 7 of a 4-qubit circuit: rejected by the compiler
+            sid = ctypes.c_int64()
+            _lib.check(L.qs_server_submit(h, n, _lib.QS_C128, ops, nops,
+                                          mats.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), mats.size,
+                                          ctypes.byref(sid)))
+            ids.append(sid.value)
+        cnt = ctypes.c_int()
+        _lib.check(L.qs_server_poll(h, None, 0, ctypes.byref(cnt), 0))
+        assert cnt.value == 0
+        got = {}
+        buf = (_lib.qs_server_result * 4)()
+        for _ in range(200):
+            _lib.check(L.qs_server_poll(h, buf, 4, ctypes.byref(cnt), 50))
+            for i in range(cnt.value):
+                got[buf[i].id] = (buf[i].status, buf[i].error, buf[i].amplitudes)
+            if len(got) == 3:
+                break
+        assert len(got) == 3
+        assert got[ids[1]][0] == _lib.QS_EINVAL and len(got[ids[1]][1]) > 0
+        ref = sv.simulate(10, good)
+        for k in (0, 2):
+            st, _, count = got[ids[k]]
+            assert st == _lib.QS_OK and count == 8
+            amps = np.empty(8, dtype=np.complex128)
+            _lib.check(L.qs_server_take(h, ids[k], amps.ctypes.data_as(ctypes.c_void_p), 8))
+            assert np.max(np.abs(amps - ref[:8])) <= 1e-12
+            assert L.qs_server_take(h, ids[k], amps.ctypes.data_as(ctypes.c_void_p), 8) == _lib.QS_EINVAL
+    finally:
+        L.qs_server_destroy(h)
