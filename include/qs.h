@@ -50,7 +50,8 @@ typedef enum {
   QS_ECUDA = 3,        /* a CUDA call failed */
   QS_ETIMEOUT = 4,     /* a bounded device-side wait ran out (status word set by a kernel) */
   QS_EBUSY = 5,        /* resource in use */
-  QS_EUNSUPPORTED = 6  /* valid request this build does not implement */
+  QS_EUNSUPPORTED = 6, /* valid request this build does not implement */
+  QS_ECANCELED = 7     /* a served request was cancelled before it ran (qs_server_cancel) */
 } qs_status;
 
 /* Arithmetic used for complex128 states (complex64 always computes in FP32). */
@@ -396,6 +397,10 @@ qs_status qs_server_poll(qs_server_t s, qs_server_result* out, int max, int* cou
 /* Copy the first `count` kept amplitudes of finished request `id` (interleaved (re, im) in
  * its dtype) into HOST memory and release the result. */
 qs_status qs_server_take(qs_server_t s, int64_t id, void* amps, uint64_t count);
+/* Withdraw a request that has not started on the GPU: it finishes at once with status
+ * QS_ECANCELED (reported by qs_server_poll like any result).  QS_EBUSY if it is already on
+ * the GPU or finished, QS_EINVAL for an unknown id. */
+qs_status qs_server_cancel(qs_server_t s, int64_t id);
 qs_status qs_server_get_stats(qs_server_t s, qs_server_stats* out);
 /* Finish every submitted request, then stop the threads and release everything (results
  * not taken are dropped). */

@@ -11,7 +11,7 @@ LIB_PATH = os.path.join(HERE, "libqs.so")
 
 # enums (include/qs.h)
 QS_C64, QS_C128 = 0, 1
-QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EBUSY, QS_EUNSUPPORTED = range(7)
+QS_OK, QS_EINVAL, QS_ENOMEM, QS_ECUDA, QS_ETIMEOUT, QS_EBUSY, QS_EUNSUPPORTED, QS_ECANCELED = range(8)
 QS_ARITH_AUTO, QS_ARITH_DF, QS_ARITH_F64 = 0, 1, 2
 QS_MODE_PERGATE, QS_MODE_PAPER, QS_MODE_TILE = 0, 1, 2
 QS_ORDER_LOGICAL, QS_ORDER_STORAGE = 0, 1
@@ -20,7 +20,7 @@ QS_FLAG_FULL_RX, QS_FLAG_NO_DENSE = 1, 2
 OP_CODES = {"U1": 0, "H": 1, "X": 2, "Y": 3, "Z": 4, "S": 5, "T": 6, "RZ": 7, "RX": 8, "RY": 9, "P": 10,
             "CNOT": 11, "CZ": 12, "CP": 13, "CU": 14, "SWAP": 15, "U2": 16, "UK": 17, "RELABEL": 18}
 STATUS_NAMES = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ECUDA", 4: "QS_ETIMEOUT", 5: "QS_EBUSY",
-                6: "QS_EUNSUPPORTED"}
+                6: "QS_EUNSUPPORTED", 7: "QS_ECANCELED"}
 
 
 class qs_op(ctypes.Structure):
@@ -149,6 +149,7 @@ SIGNATURES = {
                               ctypes.POINTER(ctypes.c_int64)]),
     "qs_server_poll": (_I, [_H, ctypes.POINTER(qs_server_result), _I, _IP, _I]),
     "qs_server_take": (_I, [_H, ctypes.c_int64, _P, ctypes.c_uint64]),
+    "qs_server_cancel": (_I, [_H, ctypes.c_int64]),
     "qs_server_get_stats": (_I, [_H, ctypes.POINTER(qs_server_stats)]),
     "qs_server_destroy": (_I, [_H]),
 }

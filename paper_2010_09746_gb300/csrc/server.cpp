@@ -43,8 +43,11 @@ qs_status sfail(qs_status s, const std::string& m) {
 }
 
 // one request through its whole life
+enum Phase { PH_QUEUED, PH_COMPILING, PH_READY, PH_RUNNING, PH_DONE };
 struct Req {
   int64_t id = 0;
+  Phase phase = PH_QUEUED;
+  bool cancel = false;       // asked to cancel while compiling
   int n = 0;
   qs_dtype dtype = QS_C64;
   std::vector<qs_op> ops;
@@ -93,6 +96,7 @@ struct qs_server {
   std::deque<std::shared_ptr<Req>> compile_q;
   std::vector<std::shared_ptr<Req>> ready;           // compiled, waiting for a slot
   std::map<int64_t, std::shared_ptr<Req>> finished;  // results not yet taken
+  std::map<int64_t, std::shared_ptr<Req>> live;      // submitted, not finished
   std::deque<int64_t> unreported;                    // finished ids not yet returned by poll
   std::vector<Flight> flights;                       // owned by the admission thread
   int64_t next_id = 1;
@@ -114,6 +118,20 @@ struct qs_server {
 
 namespace {
 
+// (caller holds the lock)
+void finish_request(qs_server* s, const std::shared_ptr<Req>& r, double t) {
+  r->t_done = t;
+  r->phase = PH_DONE;
+  if (r->plan) {
+    qs_plan_destroy(r->plan);   // released once its executions are done (they are)
+    r->plan = nullptr;
+  }
+  s->live.erase(r->id);
+  s->finished[r->id] = r;
+  s->unreported.push_back(r->id);
+  s->stats.completed++;
+}
+
 void compile_worker(qs_server* s) {
   cudaSetDevice(s->device);
   set_thread_native_alloc(true);
@@ -126,6 +144,7 @@ void compile_worker(qs_server* s) {
       r = s->compile_q.front();
       s->compile_q.pop_front();
       s->compiling++;
+      r->phase = PH_COMPILING;
     }
     qs_compile_opts co{};
     co.mode = QS_MODE_TILE;
@@ -133,15 +152,14 @@ void compile_worker(qs_server* s) {
     co.tile_bits = s->o.tile_bits;
     qs_plan_t p = nullptr;
     const qs_status st = qs_compile(r->n, r->ops.data(), r->ops.size(), r->mats.data(), r->mats.size(), nullptr, &co, &p);
+    const std::string cerr = st != QS_OK ? std::string(qs_last_error()) : std::string();
     std::lock_guard<std::mutex> lk(s->mu);
     s->compiling--;
-    if (st != QS_OK) {
-      r->status = st;
-      r->error = qs_last_error();
-      r->t_done = s->now();
-      s->finished[r->id] = r;
-      s->unreported.push_back(r->id);
-      s->stats.completed++;
+    if (st != QS_OK || r->cancel) {
+      if (st == QS_OK) qs_plan_destroy(p);
+      r->status = r->cancel ? QS_ECANCELED : st;
+      r->error = r->cancel ? "cancelled" : cerr;
+      finish_request(s, r, s->now());
       s->cv_done.notify_all();
       continue;
     }
@@ -155,6 +173,7 @@ void compile_worker(qs_server* s) {
     // device work: arithmetic-bound tile passes cost about their counted instructions, with
     // the HBM bytes as a floor for light circuits
     r->work = std::max(p->cr.stats.alu_instr / 40e12, p->cr.stats.hbm_bytes / 6e12) + 5e-6;
+    r->phase = PH_READY;
     s->ready.push_back(r);
     s->cv_loop.notify_one();
   }
@@ -203,17 +222,6 @@ size_t pick_next(qs_server* s, double now) {
         (s->ready[i]->work == s->ready[best]->work && s->ready[i]->t_submit < s->ready[best]->t_submit))
       best = i;
   return best;
-}
-
-void finish_request(qs_server* s, const std::shared_ptr<Req>& r, double t) {
-  r->t_done = t;
-  if (r->plan) {
-    qs_plan_destroy(r->plan);   // released once its executions are done (they are)
-    r->plan = nullptr;
-  }
-  s->finished[r->id] = r;
-  s->unreported.push_back(r->id);
-  s->stats.completed++;
 }
 
 // admit as many ready requests as slots and memory allow; returns how many started
@@ -270,7 +278,10 @@ int admit(qs_server* s) {
     sl.busy = true;
     s->mem_used += mem;
     s->stats.peak_mem_bytes = std::max(s->stats.peak_mem_bytes, (double)s->mem_used);
-    for (auto& r : group) r->t_admit = now;
+    for (auto& r : group) {
+      r->t_admit = now;
+      r->phase = PH_RUNNING;
+    }
     lk.unlock();
 
     // ---- device work, outside the lock
@@ -438,7 +449,7 @@ qs_status qs_server_create(const qs_server_opts* opts, qs_server_t* out) {
   if (o.batch_max == 0) o.batch_max = 64;
   if (o.max_wait_ms == 0) o.max_wait_ms = 1000;
   if (o.slots < 1 || o.slots > 256 || o.compile_threads < 1 || o.compile_threads > 256 || o.readout < 0 ||
-      o.batch_max < 1 || o.order < 0 || o.order > 1 || o.max_wait_ms < 0 || o.mem_budget < 0 ||
+      o.batch_max < 1 || o.order < 0 || o.order > 1 || o.max_wait_ms < 0 || o.mem_budget < 0 || o.readout > (1 << 24) ||
       o.tile_bits < 0 || o.tile_bits > kMaxTileBits || o.reserved != 0)
     return sfail(QS_EINVAL, "invalid server options");
   qs_server* s = new qs_server();
@@ -459,7 +470,10 @@ qs_status qs_server_create(const qs_server_opts* opts, qs_server_t* out) {
   s->slots.resize(o.slots);
   const size_t per_amp = 16;
   for (Slot& sl : s->slots) {
-    sl.host_bytes = (size_t)o.batch_max * (((size_t)o.readout * per_amp + 15) / 16 * 16 + 32) + 64;
+    // room for one request's read-out, and for a full batch's up to 64 MiB (admission trims
+    // a batch to what fits)
+    const size_t per_req = ((size_t)o.readout * per_amp + 15) / 16 * 16 + 32;
+    sl.host_bytes = std::max(per_req + 64, std::min<size_t>((size_t)o.batch_max * per_req + 64, (size_t)64 << 20));
     cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&sl.host, sl.host_bytes);
     if (e != cudaSuccess) {
@@ -494,6 +508,7 @@ qs_status qs_server_submit(qs_server_t s, int n, qs_dtype dtype, const qs_op* op
   r->id = s->next_id++;
   r->t_submit = s->now();
   s->compile_q.push_back(r);
+  s->live[r->id] = r;
   s->stats.submitted++;
   *id_out = r->id;
   s->cv_compile.notify_one();
@@ -541,6 +556,39 @@ qs_status qs_server_take(qs_server_t s, int64_t id, void* amps, uint64_t count) 
   if (count && !amps) return sfail(QS_EINVAL, "null amplitude buffer");
   if (count) memcpy(amps, r.amps.data(), count * eb);
   s->finished.erase(it);
+  return QS_OK;
+}
+
+qs_status qs_server_cancel(qs_server_t s, int64_t id) {
+  if (!s) return sfail(QS_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->live.find(id);
+  if (it == s->live.end()) {
+    if (s->finished.count(id)) return sfail(QS_EBUSY, "request already finished");
+    return sfail(QS_EINVAL, "no request with this id");
+  }
+  std::shared_ptr<Req> r = it->second;
+  switch (r->phase) {
+    case PH_QUEUED:
+      for (auto q = s->compile_q.begin(); q != s->compile_q.end(); ++q)
+        if (*q == r) {
+          s->compile_q.erase(q);
+          break;
+        }
+      break;
+    case PH_READY:
+      s->ready.erase(std::find(s->ready.begin(), s->ready.end(), r));
+      break;
+    case PH_COMPILING:   // the compile thread drops it when it is done
+      r->cancel = true;
+      return QS_OK;
+    default:
+      return sfail(QS_EBUSY, "request already on the GPU");
+  }
+  r->status = QS_ECANCELED;
+  r->error = "cancelled";
+  finish_request(s, r, s->now());
+  s->cv_done.notify_all();
   return QS_OK;
 }
 

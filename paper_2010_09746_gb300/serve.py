@@ -36,6 +36,7 @@ class Result:
     admit_s: float
     done_s: float
     batched: bool = False
+    status: int = 0          # qs_status; QS_ECANCELED for a request withdrawn before it ran
 
     @property
     def latency_s(self) -> float:
@@ -120,6 +121,15 @@ class Server:
         self._rid_of[sid.value] = rid
         return sid.value
 
+    def cancel(self, sid: int) -> bool:
+        """Withdraw submitted request `sid` (the id submit returned) if it has not started on the
+        GPU; its result then comes back with status QS_ECANCELED.  False if it already started."""
+        st = self._L.qs_server_cancel(self._h, int(sid))
+        if st == _lib.QS_EBUSY:
+            return False
+        _lib.check(st)
+        return True
+
     def poll(self, timeout_s: float = 0.0) -> int:
         """Collect finished requests (waiting up to timeout_s for the first); returns how many."""
         buf = (_lib.qs_server_result * 256)()
@@ -127,6 +137,13 @@ class Server:
         _lib.check(self._L.qs_server_poll(self._h, buf, 256, ctypes.byref(cnt), int(timeout_s * 1e3)))
         for i in range(cnt.value):
             r = buf[i]
+            if r.status == _lib.QS_ECANCELED:
+                rid = self._rid_of.pop(r.id)
+                self._L.qs_server_take(self._h, r.id, None, 0)
+                self.results[rid] = Result(rid, r.n, "c128" if r.dtype == QS_C128 else "c64", 0.0,
+                                           np.zeros(0, dtype=np.complex64), self._arrival.pop(r.id, r.t_submit_s),
+                                           r.t_admit_s, r.t_done_s, False, r.status)
+                continue
             if r.status != _lib.QS_OK:
                 raise _lib.QSError(r.status, f"request {self._rid_of.get(r.id)}: {r.error.decode(errors='replace')}")
             dt = "c128" if r.dtype == QS_C128 else "c64"

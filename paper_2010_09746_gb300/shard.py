@@ -129,8 +129,16 @@ class StateBackend:
         self.state.run([_Relabel(a, b)], mode="pergate")   # back to the identity permutation
 
     def buffer(self, count: int):
+        """A device buffer of `count` amplitudes; the executor asks for two per exchange, always of
+        the same size, so the two are kept and handed out in turn."""
         el = self.torch.float64 if self.dtype == "c128" else self.torch.float32
-        return self.torch.empty(2 * count, dtype=el, device=f"cuda:{self.device}")
+        pool = self.__dict__.setdefault("_bufs", [])
+        if len(pool) < 2 or pool[0].numel() != 2 * count:
+            pool[:] = [self.torch.empty(2 * count, dtype=el, device=f"cuda:{self.device}") for _ in range(2)]
+            self._next = 0
+        b = pool[self._next]
+        self._next ^= 1
+        return b
 
     def read_range(self, first: int, buf):
         _lib.check(_lib.load().qs_copy_range_device(self.state.handle, ctypes.c_void_p(buf.data_ptr()), first,

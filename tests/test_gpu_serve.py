@@ -118,3 +118,26 @@ def test_server_c_calls_failure_and_take_semantics():
             assert L.qs_server_take(h, ids[k], amps.ctypes.data_as(ctypes.c_void_p), 8) == _lib.QS_EINVAL
     finally:
         L.qs_server_destroy(h)
+
+
+def test_cancel_before_start():
+    """Requests withdrawn while they wait behind a long one finish as QS_ECANCELED; the rest
+    run and match the oracle."""
+    from paper_2010_09746_gb300 import _lib
+    srv = serve.Server(slots=1, readout=16, batch_small_n=-1)
+    long_req = wc.Request(0.0, 24, "c128", wc.rzrx_cz_circuit(24, 12, seed=3))
+    short = [wc.Request(0.0, 10, "c64", wc.rzrx_cz_circuit(10, 4, seed=s)) for s in range(6)]
+    sids = [srv.submit(0, long_req)] + [srv.submit(k + 1, r) for k, r in enumerate(short)]
+    cancelled = [srv.cancel(sid) for sid in sids[4:]]
+    assert all(cancelled)
+    while len(srv.results) < len(sids):
+        srv.poll(1.0)
+    for k in range(1, 4):
+        r = srv.results[k]
+        assert r.status == _lib.QS_OK
+        ref = sv.simulate(10, short[k - 1].circuit)[:16]
+        assert np.max(np.abs(r.amplitudes.astype(np.complex128) - ref)) <= 1e-5
+    for k in range(4, 7):
+        assert srv.results[k].status == _lib.QS_ECANCELED
+    assert not srv.cancel(sids[0])   # already ran
+    srv.close()
