@@ -399,7 +399,7 @@ qs_status qs_server_poll(qs_server_t s, qs_server_result* out, int max, int* cou
 qs_status qs_server_take(qs_server_t s, int64_t id, void* amps, uint64_t count);
 /* Withdraw a request that has not started on the GPU: it finishes at once with status
  * QS_ECANCELED (reported by qs_server_poll like any result).  QS_EBUSY if it is already on
- * the GPU or finished, QS_EINVAL for an unknown id. */
+ * the GPU or finished (taken or not), QS_EINVAL for an id this server never issued. */
 qs_status qs_server_cancel(qs_server_t s, int64_t id);
 qs_status qs_server_get_stats(qs_server_t s, qs_server_stats* out);
 /* Finish every submitted request, then stop the threads and release everything (results

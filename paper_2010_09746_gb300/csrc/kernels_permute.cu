@@ -104,16 +104,13 @@ __global__ void __launch_bounds__(kPermThreads) k_permute_tiled(S* __restrict__ 
     }
     __syncthreads();
     // read: tile-local index r enumerates the input tile bits in ascending order, so the
-    // lowest input bits vary fastest (contiguous segments); unrolled so that each thread has
-    // several loads in flight before the first store to shared memory
-#pragma unroll 4
+    // lowest input bits vary fastest (contiguous segments)
     for (int idx = threadIdx.x; idx < cnt * T; idx += kPermThreads) {
       const int u = idx >> a.tb, r = idx & (T - 1);
       buf[pad_idx<S>(idx)] = src[bin[u] | off_in[r]];
     }
     __syncthreads();
     // write: w enumerates the output tile bits in ascending output order
-#pragma unroll 4
     for (int idx = threadIdx.x; idx < cnt * T; idx += kPermThreads) {
       const int u = idx >> a.tb, w = idx & (T - 1);
       dst[bout[u] | off_out[w]] = buf[pad_idx<S>((u << a.tb) | r_of[w])];

@@ -564,7 +564,7 @@ qs_status qs_server_cancel(qs_server_t s, int64_t id) {
   std::lock_guard<std::mutex> lk(s->mu);
   auto it = s->live.find(id);
   if (it == s->live.end()) {
-    if (s->finished.count(id)) return sfail(QS_EBUSY, "request already finished");
+    if (id >= 1 && id < s->next_id) return sfail(QS_EBUSY, "request already finished");
     return sfail(QS_EINVAL, "no request with this id");
   }
   std::shared_ptr<Req> r = it->second;
