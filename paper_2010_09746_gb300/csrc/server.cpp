@@ -179,6 +179,10 @@ void compile_worker(qs_server* s) {
   }
 }
 
+// the device status word (bounded waits) is copied into the last 16 bytes of the slot's pinned
+// buffer, which the read-outs never reach
+int* status_slot(Slot& sl) { return reinterpret_cast<int*>(sl.host + sl.host_bytes - 16); }
+
 // enqueue the read-out of a finished solo run: FP64 norm and the first amplitudes into the
 // slot's pinned buffer (norm at offset 0, amplitudes from offset 16)
 cudaError_t enqueue_solo_readout(qs_server* s, Slot& sl, Flight& f) {
@@ -193,6 +197,7 @@ cudaError_t enqueue_solo_readout(qs_server* s, Slot& sl, Flight& f) {
   const size_t cnt = s->readout_count(r);
   if (e == cudaSuccess && cnt)
     e = cudaMemcpyAsync(sl.host + 16, h->psi, cnt * h->store_bytes, cudaMemcpyDeviceToHost, sl.stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(status_slot(sl), h->status_dev, sizeof(int), cudaMemcpyDeviceToHost, sl.stream);
   return e;
 }
 
@@ -207,6 +212,7 @@ cudaError_t enqueue_batch_readout(qs_server* s, Slot& sl, Flight& f) {
                           cudaMemcpyDeviceToHost, sl.stream);
     off += ((cnt * b->store_bytes + 15) / 16) * 16;
   }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(status_slot(sl), b->status_d, sizeof(int), cudaMemcpyDeviceToHost, sl.stream);
   return e;
 }
 
@@ -378,11 +384,10 @@ int reap(qs_server* s) {
     const cudaError_t q = cudaEventQuery(f.done);
     qs_status st = (q == cudaSuccess) ? QS_OK : QS_ECUDA;
     std::string err = (q == cudaSuccess) ? "" : std::string("serving: ") + cudaGetErrorString(q);
-    // a bounded device-side wait that gave up leaves its status word set
-    int dev_status = 0;
-    int* status_dev = f.state ? f.state->status_dev : (f.batch ? f.batch->status_d : nullptr);
-    if (st == QS_OK && status_dev && cudaMemcpyAsync(&dev_status, status_dev, sizeof(int), cudaMemcpyDeviceToHost, sl.stream) == cudaSuccess &&
-        cudaStreamSynchronize(sl.stream) == cudaSuccess && dev_status != 0) {
+    // a bounded device-side wait that gave up leaves its status word set (copied with the
+    // read-out, before the event)
+    const int dev_status = *status_slot(sl);
+    if (st == QS_OK && dev_status != 0) {
       st = (qs_status)dev_status;
       err = "a device-side wait timed out";
     }

@@ -213,6 +213,8 @@ class ShardedRun:
                     continue
                 # a local qubit not used by this gate takes the global position
                 cand = [x for x in range(self.n) if self.sigma[x] < self.m and self.sigma[x] not in busy]
+                if not cand:
+                    raise ValueError("gate needs more qubits than a process holds locally (n - g)")
                 loc = max(cand, key=lambda x: self.sigma[x])
                 self.transpose(loc, q)
                 busy = {self.sigma[x] for x in qubits}
