@@ -370,7 +370,8 @@ def run_ours(args):
                    "arith": {"df": "double-float (pairs of f32) on packed f32x2 lanes, f64 storage", "f32": "f32", "f64": "f64"}[policy],
                    "tile_bits": args.tile_bits or None, "low_bits": args.low_bits or None,
                    "reg_bits": args.reg_bits or None,
-                   "passes": pstats["n_passes"], "permutes": pstats["n_permutes"], "pergate": pstats["n_pergate"],
+                   "passes": pstats["n_passes"], "permutes": pstats["n_permutes"],
+                   "permute_kernels": pstats["n_permute_kernels"], "pergate": pstats["n_pergate"],
                    "parallelism": f"replicas{world}",
                    "l2": "state 16 GiB >> 129 MB L2, no flush needed" if n >= 27 else "state small vs L2"},
         "hbm_frac_step": round(total_bytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
@@ -426,7 +427,8 @@ def run_ours(args):
         ms_pa, _, ks_pa = measure(qs, st, p_pa, 1, 1, torch, stream, profile=True)
         s_pa = p_pa.stats()
         modes["paper_alg1_m12"] = {"gates_per_s": round(G / (ms_pa / 1e3), 2), "passes": s_pa["n_passes"],
-                                   "permutes": s_pa["n_permutes"], "nonlocal_gates": s_pa["n_comm_gates"]}
+                                   "permutes": s_pa["n_permutes"], "permute_kernels": s_pa["n_permute_kernels"],
+                                   "nonlocal_gates": s_pa["n_comm_gates"]}
         out["modes"] = modes
         runs_circuits.update({"tile": circ, "pergate": sub, "paper_alg1_m12": circ})
         runs_opts.update({"tile": dict(mode=args.mode, tile_bits=args.tile_bits, low_bits=args.low_bits,
@@ -490,7 +492,7 @@ def measure_small(qs, torch, args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         entry = {"gates_per_s": round(G / (ms / 1e3), 1), "launches_per_circuit": plans[0].stats()["n_passes"]
-                 + plans[0].stats()["n_pergate"] + plans[0].stats()["n_permutes"] + 1}
+                 + plans[0].stats()["n_pergate"] + plans[0].stats()["n_permute_kernels"] + 1}
         if mode != "paper":   # permutations swap buffers on the host: not replayable as one graph
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
@@ -684,7 +686,8 @@ def measure_qft_like(qs, torch, st, stream, args):
         ms, _, _ = measure(qs, st, plan, 1, 1, torch, stream)
         ps = plan.stats()
         res[mode] = {"gates_per_s": round(len(circ) / (ms / 1e3), 2), "ms": round(ms, 2), "passes": ps["n_passes"],
-                     "permutes": ps["n_permutes"], "pergate_kernels": ps["n_pergate"]}
+                     "permutes": ps["n_permutes"], "permute_kernels": ps["n_permute_kernels"],
+                     "pergate_kernels": ps["n_pergate"]}
     res["paper_alg1_m12"]["permute_bound_2(n-m)"] = 2 * (n - 12)
     return res
 

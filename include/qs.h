@@ -153,7 +153,8 @@ typedef struct {
   int64_t n_gates;        /* gates in the input circuit */
   int64_t n_passes;       /* tile passes */
   int64_t n_pergate;      /* gates executed by per-gate kernels */
-  int64_t n_permutes;     /* permutation kernels */
+  int64_t n_permutes;     /* PermuteQubits instructions (QS_MODE_PAPER: local<->global
+                             transpositions); see n_permute_kernels */
   int64_t n_comm_gates;   /* QS_MODE_PAPER: gates executed non-locally */
   double hbm_bytes;       /* algorithmic HBM bytes of one execution (reads + writes) */
   double alu_instr;       /* arithmetic instructions of one execution as the arithmetic's
@@ -162,6 +163,10 @@ typedef struct {
   double compile_ms;      /* host time spent compiling */
   int64_t n_dense;        /* dense 6-qubit blocks on the tensor cores (QS_MODE_TILE, complex64) */
   double predicted_ms;    /* the cost model's prediction of one execution */
+  int64_t n_permute_kernels; /* permutation kernel launches: a PermuteQubits right after a tile
+                                pass is folded into that pass's store (the pass writes under the
+                                new sigma to a second buffer) whenever the local qubit's storage
+                                bit is not one of the pass's contiguous segment bits */
 } qs_plan_stats;
 
 /* Per-kernel-class timing collected while profiling is on (qs_set_profiling). */

@@ -686,12 +686,24 @@ static qs_status execute_steps(qs_handle h, qs_plan_t p) {
   for (const Step& s : p->cr.steps) {
     const char* name = step_name(s, p->pol);
     if (s.kind == ST_PASS) {
+      // a PermuteQubits fused into the pass's store writes the permuted vector to the other
+      // buffer (out of place), which then becomes the state
+      const bool fused = s.pass.swap_a != s.pass.swap_b;
+      if (fused) {
+        qs_status st = ensure_scratch(h);
+        if (st != QS_OK) return st;
+      }
+      void* dst = fused ? h->scratch : h->psi;
       CUDA_TRY(timed(h, name, s.bytes,
                      [&] {
-                       return launch_tile_pass(p->pol, h->psi, s.pass, p->stages_dev, p->rops_dev, p->ops_dev,
+                       return launch_tile_pass(p->pol, h->psi, dst, s.pass, p->stages_dev, p->rops_dev, p->ops_dev,
                                                p->pool_dev, h->status_dev, h->stream);
                      }, s.alu),
                "tile pass launch");
+      if (fused) {
+        std::swap(h->psi, h->scratch);
+        h->sigma = s.perm;
+      }
     } else if (s.kind == ST_GATE) {
       CUDA_TRY(timed(h, name, s.bytes, [&] { return launch_gate(p->pol, h->psi, h->n, s.op, p->pool_dev, h->stream); },
                      s.alu),

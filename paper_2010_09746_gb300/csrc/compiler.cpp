@@ -441,10 +441,23 @@ bool compile_paper(int n, const std::vector<HGate>& gates, std::vector<int> sigm
       }
     // apply the best transposition, or run the first frontier gate non-locally
     if (have && best0 > 0) {
+      const size_t nsteps = out->steps.size();
       if (!flush()) return false;
       std::vector<int> sg = sigma;
       std::swap(sg[best_l], sg[best_g]);
-      emit_permute(n, sigma, sg, store_bytes, out);
+      const int pl = sigma[best_l], pg = sigma[best_g];
+      // PermuteQubits on the store of the tile pass just flushed (it reads under sigma and
+      // writes under sigma'): exchanging storage bits pl and pg moves whole 2^c-element
+      // segments as long as pl >= c, so it costs no extra pass; otherwise a permutation kernel
+      Step* last = out->steps.size() > nsteps ? &out->steps.back() : nullptr;
+      if (last && last->kind == ST_PASS && last->pass.swap_a == last->pass.swap_b && pl >= last->pass.c) {
+        last->pass.swap_a = pl;
+        last->pass.swap_b = pg;
+        last->perm = sg;
+      } else {
+        emit_permute(n, sigma, sg, store_bytes, out);
+        out->stats.n_permute_kernels++;
+      }
       out->stats.n_permutes++;
       out->trace.push_back({2, best_l * 64 + best_g});
       sigma = sg;

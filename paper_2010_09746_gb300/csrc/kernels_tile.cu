@@ -658,7 +658,8 @@ constexpr uint32_t kTileSmemOffset = 128;
 // Process block b of tile pass tp on the state at psi: load, stages, store.  Returns false
 // when the load's bounded wait expired (the status word is set).
 template <class A, int K, bool Lite>
-__device__ __forceinline__ bool process_block(typename A::store_t* __restrict__ psi, const TilePass& tp, uint64_t b,
+__device__ __forceinline__ bool process_block(const typename A::store_t* psi, typename A::store_t* dst,
+                                              const TilePass& tp, uint64_t b,
                                               const StageRec* __restrict__ stages, const RegOp* __restrict__ rops,
                                               const DevOp* __restrict__ dops, const typename A::mat_t* __restrict__ pool,
                                               int* __restrict__ status, unsigned char* smem, uint32_t bar,
@@ -731,14 +732,20 @@ __device__ __forceinline__ bool process_block(typename A::store_t* __restrict__ 
       Ts[px(i)] = A::to_store(from_frame<A>(v, i));
     }
   }
-  // ---- store: bulk copies back; the tile is reused only after they have been read
+  // ---- store: bulk copies back (to dst); the tile is reused only after they have been
+  // read.  A PermuteQubits fused into the pass exchanges storage bits swap_a and swap_b of
+  // every address (both >= c, so segments stay contiguous; dst is then another buffer).
   fence_async_smem();
   __syncthreads();
+  const int sa = tp.swap_a, sb = tp.swap_b;
   for (uint32_t s = tid; s < nseg; s += kTileThreads) {
     uint64_t off = 0;
     for (int k = 0; k < L - c; k++)
       if ((s >> k) & 1u) off |= 1ull << tp.tpos[c + k];
-    bulk_store(psi + (base | off), tile_s + s * seg_stride, seg_bytes);
+    uint64_t addr = base | off;
+    const uint64_t d = ((addr >> sa) ^ (addr >> sb)) & 1ull;   // 0 when sa == sb
+    addr ^= (d << sa) | (d << sb);
+    bulk_store(dst + addr, tile_s + s * seg_stride, seg_bytes);
   }
   bulk_commit();
   bulk_wait_read0();
@@ -758,7 +765,8 @@ __device__ __forceinline__ uint32_t init_tile_barrier(unsigned char* smem) {
 
 template <class A, int K, bool Lite>
 __global__ void __launch_bounds__(kTileThreads, 2)
-    k_tile_staged(typename A::store_t* __restrict__ psi, const TilePass tp, const StageRec* __restrict__ stages,
+    k_tile_staged(const typename A::store_t* psi, typename A::store_t* dst, const TilePass tp,
+                  const StageRec* __restrict__ stages,
                   const RegOp* __restrict__ rops, const DevOp* __restrict__ dops,
                   const typename A::mat_t* __restrict__ pool, int* __restrict__ status) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -766,7 +774,7 @@ __global__ void __launch_bounds__(kTileThreads, 2)
   const uint64_t nblocks = 1ull << (tp.n - tp.L);
   uint32_t phase = 0;
   for (uint64_t b = blockIdx.x; b < nblocks; b += gridDim.x)
-    if (!process_block<A, K, Lite>(psi, tp, b, stages, rops, dops, pool, status, smem, bar, phase)) return;
+    if (!process_block<A, K, Lite>(psi, dst, tp, b, stages, rops, dops, pool, status, smem, bar, phase)) return;
   bulk_wait0();
 }
 
@@ -791,8 +799,8 @@ __global__ void __launch_bounds__(kTileThreads, 2)
       else hi = mid - 1;
     }
     const BatchPass& bp = passes[lo];
-    if (!process_block<A, K, false>(psi + bp.psi_off, bp.tp, i - prefix[lo], stages, rops, dops, pool, status, smem,
-                                    bar, phase))
+    if (!process_block<A, K, false>(psi + bp.psi_off, psi + bp.psi_off, bp.tp, i - prefix[lo], stages, rops, dops,
+                                    pool, status, smem, bar, phase))
       return;
   }
   bulk_wait0();
@@ -815,7 +823,7 @@ cudaError_t tile_kernel_setup(F* kernel, std::atomic<uint64_t>& configured, int*
 }
 
 template <class A, int K, bool Lite>
-cudaError_t launch_staged_t(void* psi, const TilePass& tp, const StageRec* stages, const RegOp* rops,
+cudaError_t launch_staged_t(const void* psi, void* dst, const TilePass& tp, const StageRec* stages, const RegOp* rops,
                             const DevOp* dops, const void* pool, int* status, cudaStream_t st) {
   using S = typename A::store_t;
   const size_t smem = kTileSmemOffset + ((size_t)1 << (tp.L - tp.c)) * (((size_t)sizeof(S) << tp.c) + 16);
@@ -830,19 +838,19 @@ cudaError_t launch_staged_t(void* psi, const TilePass& tp, const StageRec* stage
   const uint64_t nblocks = 1ull << (tp.n - tp.L);
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > nblocks) grid = nblocks;
-  k_tile_staged<A, K, Lite><<<(unsigned)grid, kTileThreads, smem, st>>>((S*)psi, tp, stages, rops, dops,
-                                                                         (const typename A::mat_t*)pool, status);
+  k_tile_staged<A, K, Lite><<<(unsigned)grid, kTileThreads, smem, st>>>((const S*)psi, (S*)dst, tp, stages, rops,
+                                                                         dops, (const typename A::mat_t*)pool, status);
   return cudaGetLastError();
 }
 
 // The lighter dispatch is built for the complex64 policy at its default register width,
 // where it was measured faster (9 % on the 30-qubit circuit); for double-float it was slower.
 template <class A, int K>
-cudaError_t launch_staged(void* psi, const TilePass& tp, const StageRec* stages, const RegOp* rops,
+cudaError_t launch_staged(const void* psi, void* dst, const TilePass& tp, const StageRec* stages, const RegOp* rops,
                           const DevOp* dops, const void* pool, int* status, cudaStream_t st) {
   if constexpr (std::is_same<A, AF32>::value && K == 5)
-    if (tp.flags & kPassLite) return launch_staged_t<A, K, true>(psi, tp, stages, rops, dops, pool, status, st);
-  return launch_staged_t<A, K, false>(psi, tp, stages, rops, dops, pool, status, st);
+    if (tp.flags & kPassLite) return launch_staged_t<A, K, true>(psi, dst, tp, stages, rops, dops, pool, status, st);
+  return launch_staged_t<A, K, false>(psi, dst, tp, stages, rops, dops, pool, status, st);
 }
 
 template <class A, int K>
@@ -885,15 +893,16 @@ cudaError_t launch_batched_k(int K, void* psi, const BatchPass* passes, const ui
 }
 
 template <class A>
-cudaError_t launch_tile_t(void* psi, const TilePass& tp, const StageRec* stages, const RegOp* rops,
+cudaError_t launch_tile_t(const void* psi, void* dst, const TilePass& tp, const StageRec* stages, const RegOp* rops,
                           const DevOp* dops, const void* pool, int* status, cudaStream_t st) {
   switch (tp.K) {
-    case 1: return launch_staged<A, 1>(psi, tp, stages, rops, dops, pool, status, st);
-    case 2: return launch_staged<A, 2>(psi, tp, stages, rops, dops, pool, status, st);
-    case 3: return launch_staged<A, 3>(psi, tp, stages, rops, dops, pool, status, st);
-    case 4: return launch_staged<A, 4>(psi, tp, stages, rops, dops, pool, status, st);
+    case 1: return launch_staged<A, 1>(psi, dst, tp, stages, rops, dops, pool, status, st);
+    case 2: return launch_staged<A, 2>(psi, dst, tp, stages, rops, dops, pool, status, st);
+    case 3: return launch_staged<A, 3>(psi, dst, tp, stages, rops, dops, pool, status, st);
+    case 4: return launch_staged<A, 4>(psi, dst, tp, stages, rops, dops, pool, status, st);
     case 5:
-      if constexpr (sizeof(typename A::reg_t) <= 8) return launch_staged<A, 5>(psi, tp, stages, rops, dops, pool, status, st);
+      if constexpr (sizeof(typename A::reg_t) <= 8)
+        return launch_staged<A, 5>(psi, dst, tp, stages, rops, dops, pool, status, st);
       break;
   }
   return cudaErrorInvalidValue;
@@ -917,14 +926,14 @@ cudaError_t launch_tile_batched(Policy pol, int K, void* psi, const BatchPass* p
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_tile_pass(Policy pol, void* psi, const TilePass& tp, const StageRec* stages_dev,
+cudaError_t launch_tile_pass(Policy pol, const void* psi, void* dst, const TilePass& tp, const StageRec* stages_dev,
                              const RegOp* regops_dev, const DevOp* ops_dev, const void* pool, int* status_dev,
                              cudaStream_t s) {
-  if (tp.nst == 0) return cudaSuccess;
+  if (tp.nst == 0 && tp.swap_a == tp.swap_b && psi == dst) return cudaSuccess;
   switch (pol) {
-    case POL_F32: return launch_tile_t<AF32>(psi, tp, stages_dev, regops_dev, ops_dev, pool, status_dev, s);
-    case POL_F64: return launch_tile_t<AF64>(psi, tp, stages_dev, regops_dev, ops_dev, pool, status_dev, s);
-    case POL_DF: return launch_tile_t<ADF>(psi, tp, stages_dev, regops_dev, ops_dev, pool, status_dev, s);
+    case POL_F32: return launch_tile_t<AF32>(psi, dst, tp, stages_dev, regops_dev, ops_dev, pool, status_dev, s);
+    case POL_F64: return launch_tile_t<AF64>(psi, dst, tp, stages_dev, regops_dev, ops_dev, pool, status_dev, s);
+    case POL_DF: return launch_tile_t<ADF>(psi, dst, tp, stages_dev, regops_dev, ops_dev, pool, status_dev, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -92,6 +92,8 @@ struct TilePass {
   int32_t K;          // register bits per thread in register stages
   int32_t st0, nst;   // stage range in the plan's stage array
   int32_t flags;      // kPass* bits
+  int32_t swap_a, swap_b;   // PermuteQubits fused into the store: storage bits exchanged in every
+                            // stored address (both >= c; equal = none), written to another buffer
   int32_t tpos[kMaxTileBits];        // storage positions of tile bits, ascending
   int32_t npos[kMaxQubits];          // storage positions of the other bits, ascending
 };
@@ -122,7 +124,9 @@ struct Step {
 // ------------------------------------------------------------------------------------------
 cudaError_t launch_init_zero(void* psi, int n, int store_bytes, cudaStream_t s);
 cudaError_t launch_gate(Policy pol, void* psi, int n, const DevOp& op, const void* pool, cudaStream_t s);
-cudaError_t launch_tile_pass(Policy pol, void* psi, const TilePass& tp, const StageRec* stages_dev,
+// reads the state at psi, writes it to dst (the same buffer unless the pass carries a fused
+// permutation, tp.swap_a != tp.swap_b)
+cudaError_t launch_tile_pass(Policy pol, const void* psi, void* dst, const TilePass& tp, const StageRec* stages_dev,
                              const RegOp* regops_dev, const DevOp* ops_dev, const void* pool, int* status_dev,
                              cudaStream_t s);
 cudaError_t launch_tile_batched(Policy pol, int K, void* psi, const BatchPass* passes, const uint64_t* prefix,

@@ -27,7 +27,7 @@ from . import Plan, State, compile as qs_compile
 
 def plan_features(plan: Plan) -> Tuple[float, float, float]:
     s = plan.stats()
-    launches = s["n_passes"] + s["n_pergate"] + s["n_permutes"]
+    launches = s["n_passes"] + s["n_pergate"] + s["n_permute_kernels"]
     return float(launches), float(s["hbm_bytes"]), float(s["alu_instr"])
 
 
@@ -39,12 +39,12 @@ def plan_class_features(plan: Plan, dtype: str) -> Dict[str, Tuple[float, float,
     S = float((1 << plan.n) * (16 if dtype == "c128" else 8))
     pol = {"c64": "c64", "c128": "c128_df"}[dtype]
     out = {}
-    b_pass, b_perm = 2 * S * s["n_passes"], 2 * S * s["n_permutes"]
+    b_pass, b_perm = 2 * S * s["n_passes"], 2 * S * s["n_permute_kernels"]
     b_dense = 2 * S * s.get("n_dense", 0)
     if s["n_passes"]:
         out[f"tile_pass_{pol}"] = (float(s["n_passes"]), b_pass, float(s["alu_instr"]))
-    if s["n_permutes"]:
-        out["permute"] = (float(s["n_permutes"]), b_perm, 0.0)
+    if s["n_permute_kernels"]:
+        out["permute"] = (float(s["n_permute_kernels"]), b_perm, 0.0)
     if s.get("n_dense", 0):
         out["dense_mma_c64"] = (float(s["n_dense"]), b_dense, 0.0)
     if s["n_pergate"]:

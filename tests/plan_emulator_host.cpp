@@ -251,6 +251,7 @@ static void run_pass(std::vector<C>& psi, const CompileResult& cr, const TilePas
   const uint64_t nt = 1ull << L, nblocks = 1ull << (n - L);
   std::vector<C> T(nt);
   std::vector<uint64_t> addr(nt);
+  std::vector<C> out(psi.size());
   for (uint64_t b = 0; b < nblocks; b++) {
     uint64_t base = 0;
     for (int k = 0; k < n - L; k++)
@@ -293,8 +294,16 @@ static void run_pass(std::vector<C>& psi, const CompileResult& cr, const TilePas
         }
       }
     }
-    for (uint64_t i = 0; i < nt; i++) psi[addr[i]] = T[i] * (frame ? mi_pow(-popc(i)) : C(1, 0));
+    // the store, with the exchange of storage bits swap_a / swap_b of a fused PermuteQubits
+    // (into a separate output vector, as the kernel writes to the other buffer)
+    for (uint64_t i = 0; i < nt; i++) {
+      uint64_t a = addr[i];
+      const uint64_t d = ((a >> tp.swap_a) ^ (a >> tp.swap_b)) & 1ull;
+      a ^= (d << tp.swap_a) | (d << tp.swap_b);
+      out[a] = T[i] * (frame ? mi_pow(-popc(i)) : C(1, 0));
+    }
   }
+  psi.swap(out);
 }
 
 int main(int argc, char** argv) {

@@ -35,7 +35,7 @@ def test_library_exports_every_declared_symbol():
 def test_struct_layout():
     assert ctypes.sizeof(_lib.qs_op) == 48
     assert ctypes.sizeof(_lib.qs_compile_opts) == 48
-    assert ctypes.sizeof(_lib.qs_plan_stats) == 80
+    assert ctypes.sizeof(_lib.qs_plan_stats) == 88
     assert ctypes.sizeof(_lib.qs_cost_model) == 96
 
 

@@ -29,8 +29,13 @@ def test_mix_equals_alone_and_oracle():
     res = srv.run(reqs, realtime=True, timeout_s=120)
     assert len(res) == len(reqs)
     assert srv.peak_in_flight > 1, "no overlap happened"
-    assert srv.batched_requests > 0, "no small requests were batched"
     assert srv.peak_mem <= budget
+    # all at once through two slots: compiled requests queue up and the small ones share slots
+    srv2 = serve.Server(slots=2, mem_budget=budget, readout=1 << 15)
+    res2 = srv2.run(reqs, realtime=False, timeout_s=120)
+    assert srv2.batched_requests > 0, "no small requests were batched"
+    for rid in range(len(reqs)):
+        assert res2[rid].amplitudes.tobytes() == res[rid].amplitudes.tobytes(), f"request {rid} depends on the mix"
     for rid, r in enumerate(reqs):
         got = res[rid]
         alone = serve.Server(slots=1, readout=1 << 15).run([r], realtime=False)[0]
