@@ -103,8 +103,15 @@ typedef enum {
  * is applied in the cheaper tangent form, (I - i tan X) or (cot I - i X), with the dropped
  * cos / sin factors of a tile pass multiplied into one full-form RX of that pass (same result
  * up to rounding); this flag keeps every RX in full form.  QS_FLAG_NO_DENSE: never emit dense
- * tensor-core blocks (see qs_cost_model). */
-enum { QS_FLAG_FULL_RX = 1, QS_FLAG_NO_DENSE = 2 };
+ * tensor-core blocks (see qs_cost_model).  QS_FLAG_NO_FUSE: QS_MODE_TILE fuses, by default,
+ * every run of single-qubit gates on one qubit with no multi-qubit gate on that qubit in
+ * between (gate fusion, Sec. 1) when the run holds two or more non-diagonal gates or only
+ * diagonal ones: the run's product is applied as diag . RX . diag (an exact identity for
+ * every 2x2 unitary) just before the next multi-qubit gate on that qubit (or at the end);
+ * the result equals the unfused
+ * plan's up to rounding and the trace still lists every input gate once.  This flag turns
+ * fusion off. */
+enum { QS_FLAG_FULL_RX = 1, QS_FLAG_NO_DENSE = 2, QS_FLAG_NO_FUSE = 4 };
 
 /* Cost of one launch of each kernel class for the plan's dtype,
  *   t [ms] = c[0] + c[1] * (algorithmic HBM bytes) + c[2] * (counted arithmetic instructions),

@@ -75,7 +75,7 @@ def marshal(circuit: Iterable):
 
 
 def _opts(mode="tile", dtype="c128", arith="auto", tile_bits=0, low_bits=0, max_ops=0, scoring=0, reg_bits=0,
-          renorm_every=0, full_rx=False, dense=True, cost=None):
+          renorm_every=0, full_rx=False, dense=True, fuse=True, cost=None):
     o = _lib.qs_compile_opts()
     o.mode = _MODES[mode]
     o.dtype = _DTYPES[dtype]
@@ -84,7 +84,8 @@ def _opts(mode="tile", dtype="c128", arith="auto", tile_bits=0, low_bits=0, max_
     o.low_bits = low_bits
     o.max_ops = max_ops
     o.scoring = scoring
-    o.flags = (_lib.QS_FLAG_FULL_RX if full_rx else 0) | (0 if dense else _lib.QS_FLAG_NO_DENSE)
+    o.flags = (_lib.QS_FLAG_FULL_RX if full_rx else 0) | (0 if dense else _lib.QS_FLAG_NO_DENSE) | \
+        (0 if fuse else _lib.QS_FLAG_NO_FUSE)
     o.reg_bits = reg_bits
     o.renorm_every = renorm_every
     if cost is not None:   # a qs_cost_model (tuning.CostModel.native); read during qs_compile only

@@ -16,7 +16,7 @@ QS_ARITH_AUTO, QS_ARITH_DF, QS_ARITH_F64 = 0, 1, 2
 QS_MODE_PERGATE, QS_MODE_PAPER, QS_MODE_TILE = 0, 1, 2
 QS_ORDER_LOGICAL, QS_ORDER_STORAGE = 0, 1
 QS_DENSE_AUTO, QS_DENSE_CUDA_CORES, QS_DENSE_TENSOR = 0, 1, 2
-QS_FLAG_FULL_RX, QS_FLAG_NO_DENSE = 1, 2
+QS_FLAG_FULL_RX, QS_FLAG_NO_DENSE, QS_FLAG_NO_FUSE = 1, 2, 4
 OP_CODES = {"U1": 0, "H": 1, "X": 2, "Y": 3, "Z": 4, "S": 5, "T": 6, "RZ": 7, "RX": 8, "RY": 9, "P": 10,
             "CNOT": 11, "CZ": 12, "CP": 13, "CU": 14, "SWAP": 15, "U2": 16, "UK": 17, "RELABEL": 18}
 STATUS_NAMES = {0: "QS_OK", 1: "QS_EINVAL", 2: "QS_ENOMEM", 3: "QS_ECUDA", 4: "QS_ETIMEOUT", 5: "QS_EBUSY",

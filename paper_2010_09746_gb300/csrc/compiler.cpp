@@ -5,7 +5,11 @@
 // Locality (Sec. 2, Appendix C): a gate needs "communication" -- here: cannot run inside a
 // tile pass -- iff one of the qubits on which it acts non-diagonally sits outside the tile.
 // Controls and diagonal factors on any qubit are constants of a tile block.
+//
+// Gate fusion (Sec. 1 cites fusing consecutive gates on a common qubit subset as a known
+// optimisation) runs before the tile scheduler: see fuse_single_qubit_runs.
 #include <chrono>
+#include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -61,7 +65,7 @@ bool normalize_compile_opts(int n, qs_compile_opts* o, std::string* err) {
   };
   if (o->dtype != QS_C64 && o->dtype != QS_C128) return bad("unknown dtype");
   if (o->mode < QS_MODE_PERGATE || o->mode > QS_MODE_TILE) return bad("unknown mode");
-  if (o->flags & ~(QS_FLAG_FULL_RX | QS_FLAG_NO_DENSE)) return bad("unknown flags");
+  if (o->flags & ~(QS_FLAG_FULL_RX | QS_FLAG_NO_DENSE | QS_FLAG_NO_FUSE)) return bad("unknown flags");
   if (o->reg_bits < 0 || o->reg_bits > 5) return bad("reg_bits must be in [0, 5]");
   if (o->renorm_every < 0) return bad("renorm_every must be >= 0");
   if (o->tile_bits == 0) o->tile_bits = default_tile_bits(o->dtype);
@@ -107,6 +111,109 @@ std::vector<std::vector<int>> build_dag(const std::vector<HGate>& gates) {
     preds[j].erase(std::unique(preds[j].begin(), preds[j].end()), preds[j].end());
   }
   return preds;
+}
+
+namespace {
+
+// out = a b for row-major 2x2 matrices
+void mul2x2(const cd a[4], const cd b[4], cd out[4]) {
+  const cd r0 = a[0] * b[0] + a[1] * b[2], r1 = a[0] * b[1] + a[1] * b[3];
+  const cd r2 = a[2] * b[0] + a[3] * b[2], r3 = a[2] * b[1] + a[3] * b[3];
+  out[0] = r0;
+  out[1] = r1;
+  out[2] = r2;
+  out[3] = r3;
+}
+
+// Euler form of a U(2) matrix about the Z and X axes: U = e^{i a} RZ(b) RX(t) RZ(d) for every
+// unitary U.  Written as U = D2 RX(t) D1 with D1 = diag(1, e^{i d}) (RZ(d) up to the scalar
+// e^{-i d / 2}) and D2 = e^{i (a - d / 2)} RZ(b), so that the RX factor has the exact
+// structure c I - i s X the lowering recognises.  With V = e^{-i a} U in SU(2) (a from
+// det U = e^{2 i a}): V00 = cos(t/2) e^{-i (b + d)/2}, V01 = -i sin(t/2) e^{-i (b - d)/2}.
+// False when the three factors miss U by more than 1e-13 in some entry (U not unitary
+// enough), in which case the caller keeps the product as one general matrix.
+bool euler_zxz(const cd U[4], cd d1[4], cd rx[4], cd d2[4]) {
+  const double a = 0.5 * std::arg(U[0] * U[3] - U[1] * U[2]);
+  const cd ph = std::polar(1.0, -a);
+  const cd v00 = U[0] * ph, v01 = U[1] * ph;
+  const double ca = std::abs(v00), sb = std::abs(v01), r = std::hypot(ca, sb);
+  if (!(r > 0)) return false;
+  const double c = ca / r, s = sb / r;
+  const double sum = ca > 0 ? -std::arg(v00) : 0.0;                 // (b + d) / 2
+  const double diff = sb > 0 ? -std::arg(v01) - 0.5 * M_PI : 0.0;   // (b - d) / 2
+  const double b = sum + diff, d = sum - diff;
+  d1[0] = 1; d1[1] = 0; d1[2] = 0; d1[3] = std::polar(1.0, d);
+  rx[0] = c; rx[1] = cd(0, -s); rx[2] = cd(0, -s); rx[3] = c;
+  const cd g = std::polar(1.0, a - 0.5 * d);
+  d2[0] = g * std::polar(1.0, -0.5 * b); d2[1] = 0; d2[2] = 0; d2[3] = g * std::polar(1.0, 0.5 * b);
+  cd t[4], w[4];
+  mul2x2(rx, d1, t);
+  mul2x2(d2, t, w);
+  for (int k = 0; k < 4; k++)
+    if (std::abs(w[k] - U[k]) > 1e-13) return false;
+  return true;
+}
+
+bool is_identity(const cd m[4]) { return m[0] == cd(1, 0) && m[1] == cd(0, 0) && m[2] == cd(0, 0) && m[3] == cd(1, 0); }
+
+}  // namespace
+
+// The single-qubit gates acting on one qubit between two multi-qubit gates on that qubit
+// commute with every gate in between (those act on other qubits), so they can be applied at
+// once, as their product, just before the next multi-qubit gate on the qubit.  Inside a tile
+// pass an RX costs one tangent-form update and a diagonal factor joins a register phase table
+// (shared with the other register qubits), while a general 2x2 costs about three RX; so a run
+// is fused when it holds two or more non-diagonal gates (its product, re-expressed as
+// diagonal . RX . diagonal, costs one RX and two table factors) or consists of diagonal gates
+// only (one diagonal factor).  A run with one non-diagonal gate is kept as it is.
+void fuse_single_qubit_runs(int n, const std::vector<HGate>& in, std::vector<HGate>* out,
+                            std::vector<std::vector<int>>* origin) {
+  out->clear();
+  origin->clear();
+  std::vector<std::vector<int>> run(n);
+  auto emit = [&](const HGate& g, std::vector<int> src) {
+    out->push_back(g);
+    origin->push_back(std::move(src));
+  };
+  auto flush = [&](int q) {
+    std::vector<int>& r = run[q];
+    if (r.empty()) return;
+    int nd = 0;
+    for (int i : r) nd += in[i].cls[0] != CLS_Z;
+    if (r.size() < 2 || nd == 1) {
+      for (int i : r) emit(in[i], {i});
+      r.clear();
+      return;
+    }
+    cd U[4] = {1, 0, 0, 1}, t[4];
+    for (int i : r) {   // later gates act on the left
+      const cd G[4] = {in[i].U[0], in[i].U[1], in[i].U[2], in[i].U[3]};
+      mul2x2(G, U, t);
+      for (int k = 0; k < 4; k++) U[k] = t[k];
+    }
+    cd d1[4], rx[4], d2[4];
+    if (U[1] == cd(0, 0) && U[2] == cd(0, 0)) {
+      if (!is_identity(U)) emit(make_1q_gate(q, U), r);
+      else for (int i : r) emit(in[i], {i});   // an exact identity: keep the gates (rare)
+    } else if (euler_zxz(U, d1, rx, d2)) {
+      if (!is_identity(d1)) emit(make_1q_gate(q, d1), {});
+      emit(make_1q_gate(q, rx), r);
+      if (!is_identity(d2)) emit(make_1q_gate(q, d2), {});
+    } else {
+      emit(make_1q_gate(q, U), r);
+    }
+    r.clear();
+  };
+  for (int i = 0; i < (int)in.size(); i++) {
+    const HGate& g = in[i];
+    if (g.nq == 1) {
+      run[g.q[0]].push_back(i);
+      continue;
+    }
+    for (int t = 0; t < g.nq; t++) flush(g.q[t]);
+    emit(g, {i});
+  }
+  for (int q = 0; q < n; q++) flush(q);
 }
 
 namespace {
@@ -491,8 +598,10 @@ bool compile_paper(int n, const std::vector<HGate>& gates, std::vector<int> sigm
 // greedily: starting from the c low bits, add the bit whose inclusion lets one program-order
 // sweep schedule the most gates (ties: the bit most wanted by frontier gates, then the
 // lowest bit).  The pass then runs that sweep.
+// origin (may be null): the input gates each entry of `gates` stands for (gate fusion)
 bool compile_tile(int n, const std::vector<HGate>& gates, const std::vector<int>& sigma, const qs_compile_opts& o,
-                  int store_bytes, CompileResult* out, std::string* err) {
+                  int store_bytes, CompileResult* out, std::string* err,
+                  const std::vector<std::vector<int>>* origin = nullptr) {
   const int L = std::min(o.tile_bits, n);
   const int c = std::min(o.low_bits, L);
   const int G = (int)gates.size();
@@ -520,7 +629,8 @@ bool compile_tile(int n, const std::vector<HGate>& gates, const std::vector<int>
   std::vector<uint64_t> okm(G, 0);   // candidate-bit masks of the pass search
   for (int v = 0; v < G; v++)
     if (__builtin_popcountll(ndm[v] | low) > L) {
-      *err = "gate " + std::to_string(v) + " needs more qubits than a tile holds";
+      const int g0 = (origin && !(*origin)[v].empty()) ? (*origin)[v][0] : v;
+      *err = "gate " + std::to_string(g0) + " needs more qubits than a tile holds";
       return false;
     }
   // dense blocks on the tensor cores (complex64): every gate's full storage-bit set
@@ -657,7 +767,31 @@ bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<i
   } else if (o.mode == QS_MODE_PAPER) {
     ok = compile_paper(n, gates, sigma0, o, store_bytes, out, err);
   } else if (o.mode == QS_MODE_TILE) {
-    ok = compile_tile(n, gates, sigma0, o, store_bytes, out, err);
+    if (o.flags & QS_FLAG_NO_FUSE) {
+      ok = compile_tile(n, gates, sigma0, o, store_bytes, out, err);
+    } else {
+      std::vector<HGate> fused;
+      std::vector<std::vector<int>> origin;
+      fuse_single_qubit_runs(n, gates, &fused, &origin);
+      ok = compile_tile(n, fused, sigma0, o, store_bytes, out, err, &origin);
+      if (ok) {   // the trace names input gates: a fused gate lists the gates it stands for
+        std::vector<std::pair<int, int>> tr;
+        for (size_t i = 0; i < out->trace.size(); i++) {
+          const auto& e = out->trace[i];
+          if (e.first == 0) {
+            for (int v : origin[e.second]) tr.push_back({0, v});
+          } else if (e.first == 5) {   // dense block over the next e.second (fused) gates
+            int cnt = 0;
+            for (int k = 1; k <= e.second && i + k < out->trace.size(); k++)
+              cnt += (int)origin[out->trace[i + k].second].size();
+            tr.push_back({5, cnt});
+          } else {
+            tr.push_back(e);
+          }
+        }
+        out->trace.swap(tr);
+      }
+    }
   } else {
     *err = "unknown compile mode";
     return false;
@@ -688,15 +822,6 @@ bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<i
   double pred = 0;
   for (const Step& s : out->steps) pred += step_cost_ms(out->cost, s);
   out->stats.predicted_ms = pred;
-  if (getenv("QS_DEBUG_OPMIX")) {
-    long cnt[16] = {0}, slot_only = 0, tb = 0, gb = 0;
-    for (const RegOp& r : out->reg_ops) {
-      cnt[r.type & 15]++;
-      if (r.type == OP_DIAG) { if (r.s0 >= 0) slot_only++; else if (r.tb >= 0) tb++; else gb++; }
-    }
-    fprintf(stderr, "regops: U1 %ld RX %ld DIAG %ld (slot %ld tb %ld gbit %ld) X %ld PHASE %ld U2 %ld DTAB %ld; stages %zu\n",
-            cnt[OP_U1], cnt[OP_RX], cnt[OP_DIAG], slot_only, tb, gb, cnt[OP_X], cnt[OP_PHASE], cnt[OP_U2], cnt[OP_DTAB], out->stages.size());
-  }
   out->stats.compile_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return true;

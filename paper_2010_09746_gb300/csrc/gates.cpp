@@ -117,6 +117,17 @@ bool make_hgate(int n, const qs_op& op, const double* mats, size_t nmats, HGate*
   return true;
 }
 
+HGate make_1q_gate(int q, const cd m[4]) {
+  HGate g;
+  g.kind = QS_OP_U1;
+  g.nq = 1;
+  g.q[0] = q;
+  g.param = 0.0;
+  g.U.assign(m, m + 4);
+  classify(&g);
+  return g;
+}
+
 std::vector<unsigned char> Pool::serialise(Policy pol) const {
   const size_t E = entries();
   std::vector<unsigned char> out;

@@ -175,6 +175,15 @@ struct HGate {
 // Build the HGate of an ABI op (validates qubits and matrix offsets).
 bool make_hgate(int n, const qs_op& op, const double* mats, size_t nmats, HGate* out, std::string* err);
 
+// A single-qubit gate on logical qubit q with the 2x2 matrix m (row-major), classified.
+HGate make_1q_gate(int q, const cd m[4]);
+// Gate fusion for QS_MODE_TILE: every maximal run of single-qubit gates on one qubit (no
+// multi-qubit gate on that qubit in between) that holds at least two non-diagonal gates, or
+// only diagonal ones, is replaced by its product, re-expressed as at most three gates
+// (diagonal, RX, diagonal).  origin[i] lists the input gates that output gate i stands for
+// (empty for the extra factors of a product); every input gate appears exactly once.
+void fuse_single_qubit_runs(int n, const std::vector<HGate>& in, std::vector<HGate>* out,
+                            std::vector<std::vector<int>>* origin);
 // Matrix pool in policy format.
 struct Pool {
   std::vector<double> f64;  // (re, im) pairs

@@ -161,7 +161,7 @@ def tile_schedule(plan):
 @pytest.mark.parametrize("n,L,c,seed", [(10, 6, 2, 0), (14, 8, 3, 1), (16, 9, 3, 2), (30, 12, 3, 3)])
 def test_tile_mode_schedule_is_valid(n, L, c, seed):
     circ = wc.rzrx_cz_circuit(n, 6, seed) + wc.random_mixed_circuit(n, 60, seed, kmax=3)
-    plan = qs.compile(n, circ, mode="tile", tile_bits=L, low_bits=c)
+    plan = qs.compile(n, circ, mode="tile", tile_bits=L, low_bits=c, fuse=False)
     passes = tile_schedule(plan)
     preds = cr.build_dag(circ)
     seen = set()
@@ -185,7 +185,7 @@ def test_tile_mode_schedule_is_valid(n, L, c, seed):
 def test_tile_mode_order_simulates_to_original():
     n = 9
     circ = wc.random_mixed_circuit(n, 120, seed=5, kmax=3)
-    plan = qs.compile(n, circ, mode="tile", tile_bits=6, low_bits=2)
+    plan = qs.compile(n, circ, mode="tile", tile_bits=6, low_bits=2, fuse=False)
     order = [v for _, ids in tile_schedule(plan) for v in ids]
     np.testing.assert_allclose(sv.simulate(n, [circ[v] for v in order]), sv.simulate(n, circ), atol=1e-13)
 
@@ -247,7 +247,7 @@ def test_tangent_rx_lowers_the_count():
         assert a["alu_instr"] < b["alu_instr"]
         assert a["hbm_bytes"] == b["hbm_bytes"] and a["n_passes"] == b["n_passes"]
     o = qs._opts()
-    o.flags = 4   # no such flag
+    o.flags = 8   # no such flag
     h = ctypes.c_void_p()
     ops, nops, mats = qs.marshal(circ[:3])
     assert _lib.load().qs_compile(n, ops, nops, mats.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), mats.size,
