@@ -370,7 +370,9 @@ def run_ours(args):
                    "arith": {"df": "double-float (pairs of f32) on packed f32x2 lanes, f64 storage", "f32": "f32", "f64": "f64"}[policy],
                    "tile_bits": args.tile_bits or None, "low_bits": args.low_bits or None,
                    "reg_bits": args.reg_bits or None,
-                   "passes": pstats["n_passes"], "permutes": pstats["n_permutes"],
+                   "passes": pstats["n_passes"], "fused_gates": pstats["n_fused"],
+                   "fusion": "runs of single-qubit gates on one qubit applied as diag.RX.diag" if pstats["n_fused"] else None,
+                   "permutes": pstats["n_permutes"],
                    "permute_kernels": pstats["n_permute_kernels"], "pergate": pstats["n_pergate"],
                    "parallelism": f"replicas{world}",
                    "l2": "state 16 GiB >> 129 MB L2, no flush needed" if n >= 27 else "state small vs L2"},
@@ -423,6 +425,12 @@ def run_ours(args):
         ms_pg, _, ks_pg = measure(qs, st, p_pg, 1, 1, torch, stream, profile=True)
         modes["pergate"] = {"gates_per_s": round(len(sub) / (ms_pg / 1e3), 2), "sample": f"first {len(sub)} gates",
                             "kernels": p_pg.stats()["n_pergate"]}
+        p_uf = qs.compile(n, circ, mode="tile", dtype=args.dtype, arith=args.arith, tile_bits=args.tile_bits,
+                          low_bits=args.low_bits, reg_bits=args.reg_bits, fuse=False)
+        ms_uf, _, _ = measure(qs, st, p_uf, 1, 1, torch, stream, profile=False)
+        modes["tile_unfused"] = {"gates_per_s": round(G / (ms_uf / 1e3), 2), "passes": p_uf.stats()["n_passes"],
+                                 "alu_instr_per_amp": round(p_uf.stats()["alu_instr"] / (1 << n), 1),
+                                 "fused_alu_instr_per_amp": round(pstats["alu_instr"] / (1 << n), 1)}
         p_pa = qs.compile(n, circ, mode="paper", dtype=args.dtype, arith=args.arith, tile_bits=12)
         ms_pa, _, ks_pa = measure(qs, st, p_pa, 1, 1, torch, stream, profile=True)
         s_pa = p_pa.stats()

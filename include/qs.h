@@ -105,8 +105,9 @@ typedef enum {
  * up to rounding); this flag keeps every RX in full form.  QS_FLAG_NO_DENSE: never emit dense
  * tensor-core blocks (see qs_cost_model).  QS_FLAG_NO_FUSE: QS_MODE_TILE fuses, by default,
  * every run of single-qubit gates on one qubit with no multi-qubit gate on that qubit in
- * between (gate fusion, Sec. 1) when the run holds two or more non-diagonal gates or only
- * diagonal ones: the run's product is applied as diag . RX . diag (an exact identity for
+ * between (gate fusion, Sec. 1) when the run holds two or more non-diagonal gates, a general
+ * one (neither RX nor X in form) or only diagonal ones: the run's product is applied as
+ * diag . RX . diag (an exact identity for
  * every 2x2 unitary) just before the next multi-qubit gate on that qubit (or at the end);
  * the result equals the unfused
  * plan's up to rounding and the trace still lists every input gate once.  This flag turns
@@ -174,6 +175,8 @@ typedef struct {
                                 pass is folded into that pass's store (the pass writes under the
                                 new sigma to a second buffer) whenever the local qubit's storage
                                 bit is not one of the pass's contiguous segment bits */
+  int64_t n_fused;        /* QS_MODE_TILE: input gates absorbed into fused single-qubit products
+                             (see QS_FLAG_NO_FUSE); 0 otherwise */
 } qs_plan_stats;
 
 /* Per-kernel-class timing collected while profiling is on (qs_set_profiling). */

@@ -44,7 +44,8 @@ class qs_plan_stats(ctypes.Structure):
     _fields_ = [("n_gates", ctypes.c_int64), ("n_passes", ctypes.c_int64), ("n_pergate", ctypes.c_int64),
                 ("n_permutes", ctypes.c_int64), ("n_comm_gates", ctypes.c_int64), ("hbm_bytes", ctypes.c_double),
                 ("alu_instr", ctypes.c_double), ("compile_ms", ctypes.c_double), ("n_dense", ctypes.c_int64),
-                ("predicted_ms", ctypes.c_double), ("n_permute_kernels", ctypes.c_int64)]
+                ("predicted_ms", ctypes.c_double), ("n_permute_kernels", ctypes.c_int64),
+                ("n_fused", ctypes.c_int64)]
 
 
 class qs_kernel_stat(ctypes.Structure):

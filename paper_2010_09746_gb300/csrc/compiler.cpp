@@ -125,35 +125,6 @@ void mul2x2(const cd a[4], const cd b[4], cd out[4]) {
   out[3] = r3;
 }
 
-// Euler form of a U(2) matrix about the Z and X axes: U = e^{i a} RZ(b) RX(t) RZ(d) for every
-// unitary U.  Written as U = D2 RX(t) D1 with D1 = diag(1, e^{i d}) (RZ(d) up to the scalar
-// e^{-i d / 2}) and D2 = e^{i (a - d / 2)} RZ(b), so that the RX factor has the exact
-// structure c I - i s X the lowering recognises.  With V = e^{-i a} U in SU(2) (a from
-// det U = e^{2 i a}): V00 = cos(t/2) e^{-i (b + d)/2}, V01 = -i sin(t/2) e^{-i (b - d)/2}.
-// False when the three factors miss U by more than 1e-13 in some entry (U not unitary
-// enough), in which case the caller keeps the product as one general matrix.
-bool euler_zxz(const cd U[4], cd d1[4], cd rx[4], cd d2[4]) {
-  const double a = 0.5 * std::arg(U[0] * U[3] - U[1] * U[2]);
-  const cd ph = std::polar(1.0, -a);
-  const cd v00 = U[0] * ph, v01 = U[1] * ph;
-  const double ca = std::abs(v00), sb = std::abs(v01), r = std::hypot(ca, sb);
-  if (!(r > 0)) return false;
-  const double c = ca / r, s = sb / r;
-  const double sum = ca > 0 ? -std::arg(v00) : 0.0;                 // (b + d) / 2
-  const double diff = sb > 0 ? -std::arg(v01) - 0.5 * M_PI : 0.0;   // (b - d) / 2
-  const double b = sum + diff, d = sum - diff;
-  d1[0] = 1; d1[1] = 0; d1[2] = 0; d1[3] = std::polar(1.0, d);
-  rx[0] = c; rx[1] = cd(0, -s); rx[2] = cd(0, -s); rx[3] = c;
-  const cd g = std::polar(1.0, a - 0.5 * d);
-  d2[0] = g * std::polar(1.0, -0.5 * b); d2[1] = 0; d2[2] = 0; d2[3] = g * std::polar(1.0, 0.5 * b);
-  cd t[4], w[4];
-  mul2x2(rx, d1, t);
-  mul2x2(d2, t, w);
-  for (int k = 0; k < 4; k++)
-    if (std::abs(w[k] - U[k]) > 1e-13) return false;
-  return true;
-}
-
 bool is_identity(const cd m[4]) { return m[0] == cd(1, 0) && m[1] == cd(0, 0) && m[2] == cd(0, 0) && m[3] == cd(1, 0); }
 
 }  // namespace
@@ -161,11 +132,11 @@ bool is_identity(const cd m[4]) { return m[0] == cd(1, 0) && m[1] == cd(0, 0) &&
 // The single-qubit gates acting on one qubit between two multi-qubit gates on that qubit
 // commute with every gate in between (those act on other qubits), so they can be applied at
 // once, as their product, just before the next multi-qubit gate on the qubit.  Inside a tile
-// pass an RX costs one tangent-form update and a diagonal factor joins a register phase table
-// (shared with the other register qubits), while a general 2x2 costs about three RX; so a run
-// is fused when it holds two or more non-diagonal gates (its product, re-expressed as
-// diagonal . RX . diagonal, costs one RX and two table factors) or consists of diagonal gates
-// only (one diagonal factor).  A run with one non-diagonal gate is kept as it is.
+// pass a general single-qubit matrix is applied as diagonal . RX . diagonal (see lower_gate):
+// one tangent-form RX update plus two factors of the register phase tables, which are shared
+// with the other register qubits.  So a run is fused when it holds two or more non-diagonal
+// gates, or a general one (neither RX nor X in form), or consists of diagonal gates only (one
+// diagonal factor).  A run whose one non-diagonal gate is an RX or an X is kept as it is.
 void fuse_single_qubit_runs(int n, const std::vector<HGate>& in, std::vector<HGate>* out,
                             std::vector<std::vector<int>>* origin) {
   out->clear();
@@ -179,8 +150,16 @@ void fuse_single_qubit_runs(int n, const std::vector<HGate>& in, std::vector<HGa
     std::vector<int>& r = run[q];
     if (r.empty()) return;
     int nd = 0;
-    for (int i : r) nd += in[i].cls[0] != CLS_Z;
-    if (r.size() < 2 || nd == 1) {
+    bool general = false;
+    for (int i : r) {
+      if (in[i].cls[0] == CLS_Z) continue;
+      nd++;
+      const cd* m = in[i].U.data();
+      const bool x_form = m[0] == cd(0, 0) && m[3] == cd(0, 0) && m[1] == cd(1, 0) && m[2] == cd(1, 0);
+      const bool rx_form = m[0] == m[3] && m[0].imag() == 0.0 && m[1] == m[2] && m[1].real() == 0.0;
+      general |= !x_form && !rx_form;
+    }
+    if (r.size() < 2 || (nd == 1 && !general)) {   // a lone general gate splits at lowering
       for (int i : r) emit(in[i], {i});
       r.clear();
       return;
@@ -191,11 +170,14 @@ void fuse_single_qubit_runs(int n, const std::vector<HGate>& in, std::vector<HGa
       mul2x2(G, U, t);
       for (int k = 0; k < 4; k++) U[k] = t[k];
     }
+    // the product as separate gates diag, RX, diag: the scheduler may then place the two
+    // diagonal factors wherever their phase tables are cheapest
     cd d1[4], rx[4], d2[4];
-    if (U[1] == cd(0, 0) && U[2] == cd(0, 0)) {
-      if (!is_identity(U)) emit(make_1q_gate(q, U), r);
-      else for (int i : r) emit(in[i], {i});   // an exact identity: keep the gates (rare)
-    } else if (euler_zxz(U, d1, rx, d2)) {
+    if (is_identity(U)) {
+      for (int i : r) emit(in[i], {i});   // an exact identity: keep the gates (rare)
+    } else if (U[1] == cd(0, 0) && U[2] == cd(0, 0)) {
+      emit(make_1q_gate(q, U), r);
+    } else if (euler_split(U, d1, rx, d2)) {
       if (!is_identity(d1)) emit(make_1q_gate(q, d1), {});
       emit(make_1q_gate(q, rx), r);
       if (!is_identity(d2)) emit(make_1q_gate(q, d2), {});
@@ -774,6 +756,8 @@ bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<i
       std::vector<std::vector<int>> origin;
       fuse_single_qubit_runs(n, gates, &fused, &origin);
       ok = compile_tile(n, fused, sigma0, o, store_bytes, out, err, &origin);
+      for (size_t i = 0; i < fused.size(); i++)
+        if (origin[i].size() >= 2) out->stats.n_fused += (int64_t)origin[i].size();
       if (ok) {   // the trace names input gates: a fused gate lists the gates it stands for
         std::vector<std::pair<int, int>> tr;
         for (size_t i = 0; i < out->trace.size(); i++) {

@@ -201,6 +201,45 @@ void add_ctrl(const LowerCtx& ctx, int q, DevOp* o) {
 
 bool is_real(const cd& z) { return z.imag() == 0.0; }
 
+// out = a b for row-major 2x2 matrices
+void mul2x2(const cd a[4], const cd b[4], cd out[4]) {
+  const cd r0 = a[0] * b[0] + a[1] * b[2], r1 = a[0] * b[1] + a[1] * b[3];
+  const cd r2 = a[2] * b[0] + a[3] * b[2], r3 = a[2] * b[1] + a[3] * b[3];
+  out[0] = r0;
+  out[1] = r1;
+  out[2] = r2;
+  out[3] = r3;
+}
+
+// Euler form of a U(2) matrix about the Z and X axes: U = e^{i a} RZ(b) RX(t) RZ(d) for every
+// unitary U.  Written as U = D2 RX(t) D1 with D1 = diag(1, e^{i d}) (RZ(d) up to the scalar
+// e^{-i d / 2}) and D2 = e^{i (a - d / 2)} RZ(b), so that the RX factor has the exact
+// structure c I - i s X that lower_2x2 recognises.  With e^{i a} = sqrt(det U) and
+// V = e^{-i a} U = [[v, w], [-w*, v*]] in SU(2): v = cos(t/2) A and w = -i sin(t/2) B with
+// the unit numbers A = e^{-i (b + d)/2}, B = e^{-i (b - d)/2}; so e^{i d} = A* B and
+// D2 = e^{i a} diag(A, B*), all from complex arithmetic without angles.  False when the
+// three factors miss U by more than 1e-13 in some entry (U not unitary enough); the
+// caller then applies U as one general matrix.
+bool euler_zxz(const cd U[4], cd d1[4], cd rx[4], cd d2[4]) {
+  const cd ea = std::sqrt(U[0] * U[3] - U[1] * U[2]);
+  if (!(std::abs(ea) > 0)) return false;
+  const cd v00 = U[0] / ea, v01 = U[1] / ea;
+  const double av = std::abs(v00), aw = std::abs(v01), r = std::hypot(av, aw);
+  if (!(r > 0)) return false;
+  const double c = av / r, s = aw / r;
+  const cd A = av > 0 ? v00 / av : cd(1, 0);
+  const cd B = aw > 0 ? cd(0, 1) * v01 / aw : cd(1, 0);
+  d1[0] = 1; d1[1] = 0; d1[2] = 0; d1[3] = std::conj(A) * B;
+  rx[0] = c; rx[1] = cd(0, -s); rx[2] = cd(0, -s); rx[3] = c;
+  d2[0] = ea * A; d2[1] = 0; d2[2] = 0; d2[3] = ea * std::conj(B);
+  cd t[4], w[4];
+  mul2x2(rx, d1, t);
+  mul2x2(d2, t, w);
+  for (int k = 0; k < 4; k++)
+    if (std::abs(w[k] - U[k]) > 1e-13) return false;
+  return true;
+}
+
 // 2x2 matrix m on logical qubit t with controls ctrls
 bool lower_2x2(const cd m[4], int t, const int* ctrls, int nc, const LowerCtx& ctx, Pool& pool,
                std::vector<DevOp>& out) {
@@ -245,6 +284,14 @@ bool lower_2x2(const cd m[4], int t, const int* ctrls, int nc, const LowerCtx& c
     out.push_back(o);
     return true;
   }
+  // Inside a tile an uncontrolled general matrix runs as diag . RX . diag: in register stages
+  // the diagonal factors join the phase tables and the RX takes the tangent form, about a
+  // third of a general 2x2's arithmetic.  (A per-gate kernel keeps one pass over the state.)
+  cd d1[4], rx[4], d2[4];
+  if (ctx.tile && nc == 0 && euler_zxz(m, d1, rx, d2)) {
+    return lower_2x2(d1, t, nullptr, 0, ctx, pool, out) && lower_2x2(rx, t, nullptr, 0, ctx, pool, out) &&
+           lower_2x2(d2, t, nullptr, 0, ctx, pool, out);
+  }
   o.type = OP_U1;
   o.mat = pool.add(m[0]);
   pool.add(m[1]);
@@ -255,6 +302,8 @@ bool lower_2x2(const cd m[4], int t, const int* ctrls, int nc, const LowerCtx& c
 }
 
 }  // namespace
+
+bool euler_split(const cd U[4], cd d1[4], cd rx[4], cd d2[4]) { return euler_zxz(U, d1, rx, d2); }
 
 bool lower_gate(const HGate& g, const LowerCtx& ctx, Pool& pool, std::vector<DevOp>& out) {
   const int D = 1 << g.nq;

@@ -177,9 +177,14 @@ bool make_hgate(int n, const qs_op& op, const double* mats, size_t nmats, HGate*
 
 // A single-qubit gate on logical qubit q with the 2x2 matrix m (row-major), classified.
 HGate make_1q_gate(int q, const cd m[4]);
+// U = d2 . rx . d1 for a 2x2 unitary U: d1 = diag(1, e^{i d}), rx = c I - i s X (c, s >= 0),
+// d2 diagonal (the Euler angles of U about Z, X, Z).  False if the factors miss U by more
+// than 1e-13 in some entry.
+bool euler_split(const cd U[4], cd d1[4], cd rx[4], cd d2[4]);
 // Gate fusion for QS_MODE_TILE: every maximal run of single-qubit gates on one qubit (no
-// multi-qubit gate on that qubit in between) that holds at least two non-diagonal gates, or
-// only diagonal ones, is replaced by its product, re-expressed as at most three gates
+// multi-qubit gate on that qubit in between) that holds at least two non-diagonal gates, a
+// general one (neither RX nor X in form), or only diagonal ones, is replaced by its product,
+// re-expressed as at most three gates
 // (diagonal, RX, diagonal).  origin[i] lists the input gates that output gate i stands for
 // (empty for the extra factors of a product); every input gate appears exactly once.
 void fuse_single_qubit_runs(int n, const std::vector<HGate>& in, std::vector<HGate>* out,

@@ -198,10 +198,16 @@ void merge_diagonals(std::vector<RegOp>& rl, int K, Pool& pool) {
 // Pass-level scalars.  Every uncontrolled register-stage RX may run in tangent form,
 // (I - i t X) or (t I - i X) with |t| <= 1, dropping a real factor cos or sin; every phase
 // table dropped its entry-0 phase.  Both are scalars on the whole tile, so they commute with
-// every op of the pass: their product multiplies the first table of the pass (all of its
-// entries then get multiplied), or, in a pass without tables, the first RX, which keeps
-// the full form.
+// every op of the pass and may be applied anywhere in it.  A tangent step multiplies every
+// amplitude by 1 / |dropped factor| (up to sqrt 2), so a pass of hundreds of them would leave
+// the floating-point range; the dropped factors are therefore absorbed in segments: when the
+// current segment's growth would pass 2^kSegBits, the next uncontrolled RX keeps the full
+// form and also multiplies by the segment's factors, which brings the magnitudes back.  The
+// last segment's factors and the table phases multiply the first table of the pass (all of
+// its entries then get multiplied), or, in a pass without tables, the pass's first RX, which
+// keeps the full form; magnitudes stay within 2^(+-kSegBits) of the unit-norm state.
 void fold_pass_factors(CompileResult* out, int st0, int nst, int K) {
+  constexpr double kSegBits = 24.0;
   Pool& pool = out->pool;
   const int Dn = 1 << K;   // table entries
   std::vector<int> tabs, rxs;   // indices into out->reg_ops, in execution order
@@ -220,12 +226,21 @@ void fold_pass_factors(CompileResult* out, int st0, int nst, int K) {
     factor *= cd(pool.f64[2 * (size_t)(r.mat + Dn)], pool.f64[2 * (size_t)(r.mat + Dn) + 1]);
   }
   const size_t first_rx_kept = (!tabs.empty() || rxs.empty()) ? rxs.size() : 0;   // index in rxs kept full
-  double scale = 1.0;
+  double scale = 1.0, grow = 0.0;   // the current segment's dropped factors and their log2 growth
   for (size_t q = 0; q < rxs.size(); q++) {
     if (out->full_rx || q == first_rx_kept) continue;
     RegOp& r = out->reg_ops[rxs[q]];
     double* e = &pool.f64[2 * (size_t)r.mat];
     const double c = e[0], sn = e[1];
+    const double g = -std::log2(std::max(std::fabs(c), std::fabs(sn)));
+    if (grow + g > kSegBits) {   // full form, closing the segment
+      e[0] *= scale;
+      e[1] *= scale;
+      scale = 1.0;
+      grow = 0.0;
+      continue;
+    }
+    grow += g;
     r.type = OP_RXT;
     if (std::fabs(c) >= std::fabs(sn)) {
       r.s1 = 0;

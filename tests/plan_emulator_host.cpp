@@ -245,6 +245,10 @@ static void reg_op(std::vector<C>& x, const RegOp& op, const Pool& pool, uint32_
   }
 }
 
+// largest |amplitude| held in registers after any register op (scaled tangent-form updates
+// let it grow above 1 inside a pass; the kernels need it to stay well inside FP32 range)
+static double g_max_abs = 0;
+
 static void run_pass(std::vector<C>& psi, const CompileResult& cr, const TilePass& tp) {
   const int L = tp.L, n = tp.n;
   const bool frame = cr.pol == POL_DF;
@@ -285,6 +289,7 @@ static void run_pass(std::vector<C>& psi, const CompileResult& cr, const TilePas
           const RegOp& op = cr.reg_ops[o];
           if ((base & op.gmask) != op.gmask) continue;
           reg_op(x, op, cr.pool, gidx, base, frame);
+          for (const C& v : x) g_max_abs = std::max(g_max_abs, std::abs(v));
         }
         for (int j = 0; j < (1 << K); j++) {
           uint64_t i = gidx;
@@ -391,6 +396,19 @@ int main(int argc, char** argv) {
         return 3;
     }
   }
+  // the smallest scale any register op applies (the absorbed tangent-form factors make some
+  // entries smaller than 1; the kernels need them well above the FP32 subnormal range)
+  double min_scale = 1e300;
+  for (const RegOp& r : cr.reg_ops) {
+    if (r.type == OP_DTAB) {
+      for (int j = 0; j < 32; j++)
+        if ((r.csl >> j) & 1u) min_scale = std::min(min_scale, std::abs(entry(cr.pool, r.mat + j)));
+    } else if (r.type == OP_RX) {
+      const C e = entry(cr.pool, r.mat);
+      min_scale = std::min(min_scale, std::max(std::fabs(e.real()), std::fabs(e.imag())));
+    }
+  }
+  fprintf(stderr, "max_register_abs %.6e\nmin_register_scale %.6e\n", g_max_abs, min_scale);
   FILE* g = fopen(argv[2], "wb");
   if (!g) return 2;
   const int32_t nsteps = (int32_t)cr.steps.size();

@@ -63,6 +63,8 @@ def emulator(tmp_path_factory):
                 f.write(np.ascontiguousarray(mats, dtype=np.float64).tobytes())
         r = subprocess.run([exe, inp, out], capture_output=True, text=True, timeout=600)
         assert r.returncode == 0, r.stderr[-3000:]
+        run.max_register_abs = float(r.stderr.split("max_register_abs")[1].split()[0])
+        run.min_register_scale = float(r.stderr.split("min_register_scale")[1].split()[0])
         with open(out, "rb") as f:
             n2, nsteps = struct.unpack("<ii", f.read(8))
             sigma = np.frombuffer(f.read(4 * n2), dtype=np.int32)
@@ -93,6 +95,35 @@ def test_tile_mode_random_circuits(emulator, dtype, arith, n, L, c):
     circ = wc.random_mixed_circuit(n, 150, seed=n * 31 + L, kmax=min(4, L - c))
     got, _ = emulator(n, circ, mode="tile", dtype=dtype, arith=arith, tile_bits=L, low_bits=c)
     check(got, circ, n)
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+@pytest.mark.parametrize("n,L,c", [(6, 4, 1), (9, 6, 2), (12, 8, 3)])
+def test_fused_single_qubit_runs(emulator, dtype, arith, n, L, c):
+    """Gate fusion (the default in tile mode): runs of general, diagonal-only, identity- and
+    X-conjugated products, interrupted by CNOT / CZ / SWAP, match the oracle and the unfused
+    plan; the fused plan also holds the rzrx construction and random circuits."""
+    circ = wc.single_qubit_run_circuit(n, 9, seed=n + 17 * L) + wc.rzrx_cz_circuit(n, 4, seed=n) + \
+        wc.random_mixed_circuit(n, 40, seed=n, kmax=min(3, L - c))
+    got, _ = emulator(n, circ, mode="tile", dtype=dtype, arith=arith, tile_bits=L, low_bits=c)
+    check(got, circ, n)
+    unfused, _ = emulator(n, circ, mode="tile", dtype=dtype, arith=arith, tile_bits=L, low_bits=c, fuse=False)
+    assert float(np.max(np.abs(got - unfused))) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+def test_tangent_growth_stays_bounded_in_long_passes(emulator, dtype, arith):
+    """A pass of hundreds of tangent-form RX (a deep Haar + CNOT circuit on a tile-sized state,
+    every Haar 2x2 fused into diag . RX . diag) keeps its register magnitudes within 2^25 of
+    the unit-norm state, and no register op scales by less than 2^-25: the dropped cos / sin
+    factors are absorbed in segments (one product of all of them would be ~2^-200, zero in
+    FP32)."""
+    n = 10
+    circ = wc.haar_cnot_circuit(n, 120, seed=9)
+    got, _ = emulator(n, circ, mode="tile", dtype=dtype, arith=arith, tile_bits=10)
+    check(got, circ, n)
+    assert emulator.max_register_abs < 2.0 ** 25, emulator.max_register_abs
+    assert emulator.min_register_scale > 2.0 ** -25, emulator.min_register_scale
 
 
 @pytest.mark.parametrize("dtype,arith", MODES)

@@ -234,6 +234,34 @@ def qft_circuit(n: int) -> Circuit:
     return c
 
 
+def single_qubit_run_circuit(n: int, layers: int, seed: int) -> Circuit:
+    """Long runs of single-qubit gates on each qubit, for gate-fusion tests: per layer and
+    qubit one of a Haar 2x2, RZ + RX, S + T + P (diagonal only), H + H (identity product),
+    X + RZ + X (diagonal product), RY + Y; every third layer one CNOT, CZ or SWAP on two of
+    the upper half of the qubits interrupts their runs."""
+    rng = np.random.default_rng(seed)
+    c: Circuit = []
+    for layer in range(layers):
+        for q in range(n):
+            k = int(rng.integers(0, 6))
+            if k == 0:
+                c.append(Gate("U1", (q,), matrix=haar_2x2(rng)))
+            elif k == 1:
+                c += [Gate("RZ", (q,), param=_uniform_angle(rng)), Gate("RX", (q,), param=_uniform_angle(rng))]
+            elif k == 2:
+                c += [Gate("S", (q,)), Gate("T", (q,)), Gate("P", (q,), param=_uniform_angle(rng))]
+            elif k == 3:
+                c += [Gate("H", (q,)), Gate("H", (q,))]
+            elif k == 4:
+                c += [Gate("X", (q,)), Gate("RZ", (q,), param=_uniform_angle(rng)), Gate("X", (q,))]
+            else:
+                c += [Gate("RY", (q,), param=_uniform_angle(rng)), Gate("Y", (q,))]
+        if layer % 3 == 2 and n >= 4:
+            a, b = rng.choice(np.arange(n // 2, n), 2, replace=False)
+            c.append(Gate(str(rng.choice(["CNOT", "CZ", "SWAP"])), (int(a), int(b))))
+    return c
+
+
 def random_mixed_circuit(n: int, ngates: int, seed: int, kinds: Sequence[str] = None,
                          kmax: int = 3) -> Circuit:
     """Random circuit drawing every gate kind (for parity tests)."""
