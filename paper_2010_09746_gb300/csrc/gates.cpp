@@ -214,7 +214,7 @@ void mul2x2(const cd a[4], const cd b[4], cd out[4]) {
 // Euler form of a U(2) matrix about the Z and X axes: U = e^{i a} RZ(b) RX(t) RZ(d) for every
 // unitary U.  Written as U = D2 RX(t) D1 with D1 = diag(1, e^{i d}) (RZ(d) up to the scalar
 // e^{-i d / 2}) and D2 = e^{i (a - d / 2)} RZ(b), so that the RX factor has the exact
-// structure c I - i s X that lower_2x2 recognises.  With e^{i a} = sqrt(det U) and
+// structure c I - i s X (OP_RX).  With e^{i a} = sqrt(det U) and
 // V = e^{-i a} U = [[v, w], [-w*, v*]] in SU(2): v = cos(t/2) A and w = -i sin(t/2) B with
 // the unit numbers A = e^{-i (b + d)/2}, B = e^{-i (b - d)/2}; so e^{i d} = A* B and
 // D2 = e^{i a} diag(A, B*), all from complex arithmetic without angles.  False when the
@@ -283,14 +283,6 @@ bool lower_2x2(const cd m[4], int t, const int* ctrls, int nc, const LowerCtx& c
     o.mat = pool.add(cd(m[0].real(), -m[1].imag()));
     out.push_back(o);
     return true;
-  }
-  // Inside a tile an uncontrolled general matrix runs as diag . RX . diag: in register stages
-  // the diagonal factors join the phase tables and the RX takes the tangent form, about a
-  // third of a general 2x2's arithmetic.  (A per-gate kernel keeps one pass over the state.)
-  cd d1[4], rx[4], d2[4];
-  if (ctx.tile && nc == 0 && euler_zxz(m, d1, rx, d2)) {
-    return lower_2x2(d1, t, nullptr, 0, ctx, pool, out) && lower_2x2(rx, t, nullptr, 0, ctx, pool, out) &&
-           lower_2x2(d2, t, nullptr, 0, ctx, pool, out);
   }
   o.type = OP_U1;
   o.mat = pool.add(m[0]);

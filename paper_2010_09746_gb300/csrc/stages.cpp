@@ -616,6 +616,34 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
               out->pool.add(v);
             }
         }
+        if (r.type == OP_U1 && r.csl == 0 && r.cot == 0 && r.gmask == 0) {
+          // an uncontrolled general 2x2 in registers runs as diag . RX . diag: the diagonal
+          // factors join the stage's phase tables and the RX takes the tangent form, about a
+          // third of a general 2x2's arithmetic (shared-memory stages keep one op)
+          cd u[4], d1[4], rx[4], d2[4];
+          for (int k = 0; k < 4; k++) u[k] = cd(out->pool.f64[2 * (r.mat + k)], out->pool.f64[2 * (r.mat + k) + 1]);
+          if (euler_split(u, d1, rx, d2)) {
+            RegOp p = r;
+            if (d1[3] != cd(1, 0)) {   // diag(1, e^{i d}): a phase where the slot's bit is 1
+              p.type = OP_PHASE;
+              p.csl = 1u << r.s0;
+              p.s0 = -1;
+              p.neg = 0;
+              p.mat = out->pool.add(d1[3]);
+              rl.push_back(p);
+            }
+            p = r;
+            p.type = OP_RX;
+            p.mat = out->pool.add(cd(rx[0].real(), -rx[1].imag()));
+            rl.push_back(p);
+            p = r;
+            p.type = OP_DIAG;
+            p.mat = out->pool.add(d2[0]);
+            out->pool.add(d2[3]);
+            rl.push_back(p);
+            continue;
+          }
+        }
         rl.push_back(r);
       }
       merge_diagonals(rl, K, out->pool);
@@ -726,11 +754,16 @@ double gate_tile_alu_per_amp(Policy pol, const HGate& g) {
     // diagonal factors merge into register phase tables, typically two or more per table
     return 0.5 * pick(kMUL, pol) * fraction(g.nq >= 2 ? g.nq - 1 : 0);
   }
-  if (g.kind == QS_OP_RX && g.nq == 1) return pick(kRXT, pol);
-  if (g.kind == QS_OP_X) return pick(kMOVE, pol);
+  if (g.nq == 1) {   // by form: fused products are U1 gates whatever their matrix
+    const cd* m = g.U.data();
+    if (m[0] == cd(0, 0) && m[3] == cd(0, 0) && m[1] == cd(1, 0) && m[2] == cd(1, 0)) return pick(kMOVE, pol);
+    if (m[0] == m[3] && m[0].imag() == 0.0 && m[1] == m[2] && m[1].real() == 0.0) return pick(kRXT, pol);
+    // a general 2x2 runs in registers as diag . RX . diag, its two factors in phase tables
+    return pick(kRXT, pol) + pick(kMUL, pol);
+  }
   if (g.kind == QS_OP_CNOT) return pick(kMOVE, pol) * fraction(1);
   if (g.kind == QS_OP_SWAP) return pick(kMOVE, pol) * fraction(1);
-  if (g.nq == 1 || g.kind == QS_OP_CU) return pick(kU1, pol) * fraction(ctl);
+  if (g.kind == QS_OP_CU) return pick(kU1, pol) * fraction(ctl);
   if (g.nq == 2) return pick(kU2, pol);
   return pick(kMACK, pol) * (double)(1 << g.nq);
 }
