@@ -65,13 +65,17 @@ def test_dense_blocks_after_a_permutation_start():
     st.close()
 
 
-def test_30q_c64_default_model_against_c128():
-    """The 30-qubit circuit as complex64 with the default model's dense blocks, against the
-    oracle-validated complex128 tile path on the whole state (FP64 inner product)."""
+@pytest.mark.parametrize("model", ["default", "cheap_dense"])
+def test_30q_c64_against_c128(model):
+    """The 30-qubit circuit as complex64 -- with whatever dense blocks the default model picks
+    (none once gate fusion has shrunk the tile work), and with a model that makes dense blocks
+    cheap so that several run at full size -- against the oracle-validated complex128 tile
+    path on the whole state (FP64 inner product)."""
     n = 30
     circ = wc.rzrx_cz_circuit(n, 40, seed=0)
-    p64 = qs.compile(n, circ, mode="tile", dtype="c64")
-    assert p64.stats()["n_dense"] >= 1
+    p64 = qs.compile(n, circ, mode="tile", dtype="c64", cost=cheap_dense_model() if model == "cheap_dense" else None)
+    if model == "cheap_dense":
+        assert p64.stats()["n_dense"] >= 1
     s64 = qs.State(n, "c64")
     s64.execute(p64)
     s128 = qs.State(n, "c128")
