@@ -99,38 +99,58 @@ bool conflict(const RegOp& a, const RegOp& b) {
 // (computed on the host in FP64).
 void merge_diagonals(std::vector<RegOp>& rl, int K, Pool& pool) {
   const int N = (int)rl.size();
-  std::vector<std::vector<int>> pred(N);
-  for (int j = 0; j < N; j++)
-    for (int i = 0; i < j; i++)
-      if (conflict(rl[i], rl[j])) pred[j].push_back(i);
-  std::vector<char> done(N, 0);
+  // conflict edges from per-slot state: op j follows the last op that wrote a slot j reads
+  // or writes, and every op that read a slot j writes since that slot's last write (the
+  // other conflicts follow by transitivity); O(N K) instead of testing every pair
+  std::vector<std::vector<int>> succ(N);
+  std::vector<int> indeg(N, 0);
+  int last_w[32];
+  std::vector<int> readers[32];
+  for (int b = 0; b < 32; b++) last_w[b] = -1;
+  for (int j = 0; j < N; j++) {
+    const RegOp& r = rl[j];
+    const uint32_t w = is_diag(r) ? 0u : target_slots(r);
+    const uint32_t rd = (is_diag(r) ? diag_slots(r) : target_slots(r)) | ctrl_slots(r);
+    std::vector<int> pj;
+    for (uint32_t m = rd | w; m; m &= m - 1) {
+      const int b = __builtin_ctz(m);
+      if (last_w[b] >= 0) pj.push_back(last_w[b]);
+    }
+    for (uint32_t m = w; m; m &= m - 1) {
+      const int b = __builtin_ctz(m);
+      pj.insert(pj.end(), readers[b].begin(), readers[b].end());
+    }
+    std::sort(pj.begin(), pj.end());
+    pj.erase(std::unique(pj.begin(), pj.end()), pj.end());
+    for (int i : pj) succ[i].push_back(j);
+    indeg[j] = (int)pj.size();
+    for (uint32_t m = rd & ~w; m; m &= m - 1) readers[__builtin_ctz(m)].push_back(j);
+    for (uint32_t m = w; m; m &= m - 1) {
+      const int b = __builtin_ctz(m);
+      last_w[b] = j;
+      readers[b].clear();
+    }
+  }
+  // rounds: every op ready at the round's start of the wanted kind (diagonal, then not), in
+  // program order; ops of one round never depend on each other
   std::vector<RegOp> ord;
+  ord.reserve(N);
+  std::vector<int> ready[2];   // [0] non-diagonal, [1] diagonal
+  for (int j = 0; j < N; j++)
+    if (indeg[j] == 0) ready[is_diag(rl[j]) ? 1 : 0].push_back(j);
   int left = N;
   bool want_diag = true;
   while (left > 0) {
     std::vector<int> pick;
-    for (int j = 0; j < N; j++) {
-      if (done[j] || is_diag(rl[j]) != want_diag) continue;
-      bool ok = true;
-      for (int i : pred[j])
-        if (!done[i]) {
-          ok = false;
-          break;
-        }
-      if (ok) pick.push_back(j);
-    }
-    // ops picked in this round do not depend on each other: same-kind ops of one round
-    // never conflict (diagonal ops commute; ready non-diagonal ops have no unfinished
-    // predecessor, and a conflicting pair would make the later one wait)
+    pick.swap(ready[want_diag ? 1 : 0]);
+    std::sort(pick.begin(), pick.end());
     for (int j : pick) {
-      bool dep = false;
-      for (int i : pred[j])
-        if (!done[i]) dep = true;
-      if (dep) continue;
       ord.push_back(rl[j]);
-      done[j] = 1;
       left--;
     }
+    for (int j : pick)
+      for (int k : succ[j])
+        if (--indeg[k] == 0) ready[is_diag(rl[k]) ? 1 : 0].push_back(k);
     want_diag = !want_diag;
   }
   rl.swap(ord);
