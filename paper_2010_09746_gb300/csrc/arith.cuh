@@ -35,6 +35,8 @@ struct AF32 {
   static __device__ __forceinline__ mat_t ld(const mat_t* p) { return *p; }
   static __device__ __forceinline__ reg_t from_store(store_t v) { return v; }
   static __device__ __forceinline__ store_t to_store(reg_t v) { return v; }
+  static __device__ __forceinline__ reg_t from_store_f(store_t v, bool) { return v; }
+  static __device__ __forceinline__ store_t to_store_f(reg_t v, bool) { return v; }
   static __device__ __forceinline__ reg_t zero() { return make_float2(0.f, 0.f); }
   // u*a + v*b
   static __device__ __forceinline__ reg_t mac2(mat_t u, reg_t a, mat_t v, reg_t b) {
@@ -86,6 +88,8 @@ struct AF64 {
   static __device__ __forceinline__ mat_t ld(const mat_t* p) { return *p; }
   static __device__ __forceinline__ reg_t from_store(store_t v) { return v; }
   static __device__ __forceinline__ store_t to_store(reg_t v) { return v; }
+  static __device__ __forceinline__ reg_t from_store_f(store_t v, bool) { return v; }
+  static __device__ __forceinline__ store_t to_store_f(reg_t v, bool) { return v; }
   static __device__ __forceinline__ reg_t zero() { return make_double2(0.0, 0.0); }
   static __device__ __forceinline__ reg_t mac2(mat_t u, reg_t a, mat_t v, reg_t b) {
     double re = u.x * a.x;
@@ -416,6 +420,23 @@ struct ADF {
     const dfl r = two_sum(v.x, v.z), i = two_sum(v.y, v.w);
     return make_double2(join_double(r.hi, r.lo), join_double(i.hi, i.lo));
   }
+  // The double-float storage form a plan keeps between consecutive tile passes: the four
+  // floats of a normalised register value in the 16 bytes of an element (no binary64
+  // split or join).  It exists only inside one plan execution; the state holds binary64
+  // before and after.
+  static QS_HD reg_t from_df(store_t v) {
+    const unsigned long long a = d_bits(v.x), b = d_bits(v.y);
+    return make_float4(f_from_bits((unsigned int)a), f_from_bits((unsigned int)(a >> 32)),
+                       f_from_bits((unsigned int)b), f_from_bits((unsigned int)(b >> 32)));
+  }
+  static QS_HD store_t to_df(reg_t v) {
+    float2 s, e;
+    two_sum2(hi(v), lo(v), s, e);
+    return make_double2(d_from_bits(((unsigned long long)f_bits(s.y) << 32) | f_bits(s.x)),
+                        d_from_bits(((unsigned long long)f_bits(e.y) << 32) | f_bits(e.x)));
+  }
+  static QS_HD reg_t from_store_f(store_t v, bool df) { return df ? from_df(v) : from_store(v); }
+  static QS_HD store_t to_store_f(reg_t v, bool df) { return df ? to_df(v) : to_store(v); }
   static QS_HD reg_t zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
   // u a

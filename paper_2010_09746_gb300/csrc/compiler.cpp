@@ -715,6 +715,45 @@ bool compile_tile(int n, const std::vector<HGate>& gates, const std::vector<int>
   return true;
 }
 
+// Between two tile passes that follow one another (permutations in between move 16-byte
+// elements unchanged) the state stays in the double-float storage form, so that those
+// passes skip the binary64 split on load and the join on store; the plan's first pass reads
+// binary64, and a pass followed by anything else (a per-gate kernel, a renormalisation, the
+// end of the plan) writes binary64.  A pass without stages only moves data (a permutation
+// fused into its store) and keeps the form it reads.  The counted conversion work of a pass
+// drops accordingly: split 36 and join 36 instruction equivalents per amplitude, the
+// double-float store's normalisation 12.
+void set_double_float_storage(int n, CompileResult* out) {
+  const size_t S = out->steps.size();
+  auto real_pass = [&](size_t i) { return out->steps[i].kind == ST_PASS && out->steps[i].pass.nst > 0; };
+  bool fmt_df = false;
+  for (size_t i = 0; i < S; i++) {
+    Step& s = out->steps[i];
+    if (s.kind != ST_PASS) continue;
+    s.pass.flags &= ~(kPassInDF | kPassOutDF);
+    if (!real_pass(i)) {
+      if (fmt_df) s.pass.flags |= kPassInDF | kPassOutDF;
+      continue;
+    }
+    bool next_df = false;
+    for (size_t j = i + 1; j < S; j++) {
+      if (out->steps[j].kind == ST_PERMUTE || (out->steps[j].kind == ST_PASS && !real_pass(j))) continue;
+      next_df = real_pass(j);
+      break;
+    }
+    const double amps = (double)(1ull << n);
+    if (fmt_df) {
+      s.pass.flags |= kPassInDF;
+      s.alu -= 36.0 * amps;
+    }
+    if (next_df) {
+      s.pass.flags |= kPassOutDF;
+      s.alu -= 24.0 * amps;
+    }
+    fmt_df = next_df;
+  }
+}
+
 }  // namespace
 
 bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<int>& sigma0,
@@ -796,6 +835,7 @@ bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<i
     }
     out->steps = std::move(with);
   }
+  if (out->pol == POL_DF) set_double_float_storage(n, out);
   double bytes = 0, alu = 0;
   for (const Step& s : out->steps) {
     bytes += s.bytes;

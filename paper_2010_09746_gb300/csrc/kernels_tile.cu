@@ -563,11 +563,13 @@ __device__ __forceinline__ typename A::reg_t from_frame(typename A::reg_t v, uin
 
 // One register stage over the whole tile.  from_store / to_store: the shared-memory tile
 // holds storage-format elements before / after the stage (policies whose register format
-// differs from the storage format convert here instead of in a separate pass).
+// differs from the storage format convert here instead of in a separate pass); df_in /
+// df_out: that storage form is the double-float one a plan keeps between its passes.
 template <class A, int K, bool Lite>
 __device__ __forceinline__ void run_reg_stage(typename A::reg_t* T, const StageRec& sr, const RegOp* __restrict__ rops,
                                               const typename A::mat_t* __restrict__ pool, int L, Pad px,
-                                              uint64_t base, bool from_store, bool to_store) {
+                                              uint64_t base, bool from_store, bool to_store, bool df_in,
+                                              bool df_out) {
   using R = typename A::reg_t;
   using S = typename A::store_t;
   const uint32_t tile_mask = (L >= 32) ? 0xFFFFFFFFu : ((1u << L) - 1u);
@@ -592,9 +594,10 @@ __device__ __forceinline__ void run_reg_stage(typename A::reg_t* T, const StageR
       if constexpr (std::is_same<R, S>::value) {
         x[j] = T[p];
       } else if constexpr (A::kFrame) {
-        x[j] = from_store ? A::rot_q(A::from_store(reinterpret_cast<const S*>(T)[p]), (wg + __popc(j)) & 3u) : T[p];
+        x[j] = from_store ? A::rot_q(A::from_store_f(reinterpret_cast<const S*>(T)[p], df_in), (wg + __popc(j)) & 3u)
+                          : T[p];
       } else {
-        x[j] = from_store ? A::from_store(reinterpret_cast<const S*>(T)[p]) : T[p];
+        x[j] = from_store ? A::from_store_f(reinterpret_cast<const S*>(T)[p], df_in) : T[p];
       }
     }
     for (int k = 0; k < sr.nops; k++) {
@@ -642,10 +645,10 @@ __device__ __forceinline__ void run_reg_stage(typename A::reg_t* T, const StageR
       if constexpr (std::is_same<R, S>::value) {
         T[p] = x[j];
       } else if constexpr (A::kFrame) {
-        if (to_store) reinterpret_cast<S*>(T)[p] = A::to_store(A::rot_q(x[j], (0u - (wg + __popc(j))) & 3u));
+        if (to_store) reinterpret_cast<S*>(T)[p] = A::to_store_f(A::rot_q(x[j], (0u - (wg + __popc(j))) & 3u), df_out);
         else T[p] = x[j];
       } else {
-        if (to_store) reinterpret_cast<S*>(T)[p] = A::to_store(x[j]);
+        if (to_store) reinterpret_cast<S*>(T)[p] = A::to_store_f(x[j], df_out);
         else T[p] = x[j];
       }
     }
@@ -702,17 +705,18 @@ __device__ __forceinline__ bool process_block(const typename A::store_t* psi, ty
   phase ^= 1u;
 
   // ---- stages
+  const bool df_in = (tp.flags & kPassInDF) != 0, df_out = (tp.flags & kPassOutDF) != 0;
   bool in_store = true;   // the tile holds storage-format elements
   for (int k = 0; k < tp.nst; k++) {
     const StageRec sr = stages[tp.st0 + k];
     const bool last = (k == tp.nst - 1);
     if (sr.kind == 0) {
-      run_reg_stage<A, K, Lite>(T, sr, rops, pool, L, px, base, in_store, last);
+      run_reg_stage<A, K, Lite>(T, sr, rops, pool, L, px, base, in_store, last, df_in, df_out);
       in_store = last;
     } else {
       if (kConv && in_store) {
         S* Ts = reinterpret_cast<S*>(T);
-        for (uint32_t i = tid; i < nelem; i += kTileThreads) T[px(i)] = to_frame<A>(A::from_store(Ts[px(i)]), i);
+        for (uint32_t i = tid; i < nelem; i += kTileThreads) T[px(i)] = to_frame<A>(A::from_store_f(Ts[px(i)], df_in), i);
         __syncthreads();
       }
       in_store = false;
@@ -729,7 +733,7 @@ __device__ __forceinline__ bool process_block(const typename A::store_t* psi, ty
     S* Ts = reinterpret_cast<S*>(T);
     for (uint32_t i = tid; i < nelem; i += kTileThreads) {
       const R v = T[px(i)];
-      Ts[px(i)] = A::to_store(from_frame<A>(v, i));
+      Ts[px(i)] = A::to_store_f(from_frame<A>(v, i), df_out);
     }
   }
   // ---- store: bulk copies back (to dst); the tile is reused only after they have been

@@ -83,6 +83,11 @@ static_assert(sizeof(StageRec) == 48, "StageRec layout");
 
 // TilePass.flags: every register op of the pass is OP_RXTM, OP_DTAB, OP_PHASE or OP_RX
 constexpr int32_t kPassLite = 1;
+// TilePass.flags (double-float policy): the pass reads / writes the state in the
+// double-float storage form instead of binary64 -- set by the compiler between tile passes
+// that follow one another (permutations in between move 16-byte elements unchanged)
+constexpr int32_t kPassInDF = 2;
+constexpr int32_t kPassOutDF = 4;
 
 // Tile pass launch description.
 struct TilePass {
