@@ -102,34 +102,42 @@ void merge_diagonals(std::vector<RegOp>& rl, int K, Pool& pool) {
   // conflict edges from per-slot state: op j follows the last op that wrote a slot j reads
   // or writes, and every op that read a slot j writes since that slot's last write (the
   // other conflicts follow by transitivity); O(N K) instead of testing every pair
-  std::vector<std::vector<int>> succ(N);
-  std::vector<int> indeg(N, 0);
+  std::vector<std::pair<int, int>> edges;   // (from, to)
+  edges.reserve((size_t)N * 3);
+  std::vector<int> indeg(N, 0), seen(N, -1);
   int last_w[32];
   std::vector<int> readers[32];
   for (int b = 0; b < 32; b++) last_w[b] = -1;
+  auto edge = [&](int i, int j) {
+    if (seen[i] == j) return;
+    seen[i] = j;
+    edges.push_back({i, j});
+    indeg[j]++;
+  };
   for (int j = 0; j < N; j++) {
     const RegOp& r = rl[j];
     const uint32_t w = is_diag(r) ? 0u : target_slots(r);
     const uint32_t rd = (is_diag(r) ? diag_slots(r) : target_slots(r)) | ctrl_slots(r);
-    std::vector<int> pj;
     for (uint32_t m = rd | w; m; m &= m - 1) {
       const int b = __builtin_ctz(m);
-      if (last_w[b] >= 0) pj.push_back(last_w[b]);
+      if (last_w[b] >= 0) edge(last_w[b], j);
     }
-    for (uint32_t m = w; m; m &= m - 1) {
-      const int b = __builtin_ctz(m);
-      pj.insert(pj.end(), readers[b].begin(), readers[b].end());
-    }
-    std::sort(pj.begin(), pj.end());
-    pj.erase(std::unique(pj.begin(), pj.end()), pj.end());
-    for (int i : pj) succ[i].push_back(j);
-    indeg[j] = (int)pj.size();
+    for (uint32_t m = w; m; m &= m - 1)
+      for (int i : readers[__builtin_ctz(m)]) edge(i, j);
     for (uint32_t m = rd & ~w; m; m &= m - 1) readers[__builtin_ctz(m)].push_back(j);
     for (uint32_t m = w; m; m &= m - 1) {
       const int b = __builtin_ctz(m);
       last_w[b] = j;
       readers[b].clear();
     }
+  }
+  // successors in one array (counting sort of the edges by source)
+  std::vector<int> soff(N + 1, 0), succ(edges.size());
+  for (const auto& e : edges) soff[e.first + 1]++;
+  for (int j = 0; j < N; j++) soff[j + 1] += soff[j];
+  {
+    std::vector<int> fill(soff.begin(), soff.end() - 1);
+    for (const auto& e : edges) succ[fill[e.first]++] = e.second;
   }
   // rounds: every op ready at the round's start of the wanted kind (diagonal, then not), in
   // program order; ops of one round never depend on each other
@@ -149,12 +157,15 @@ void merge_diagonals(std::vector<RegOp>& rl, int K, Pool& pool) {
       left--;
     }
     for (int j : pick)
-      for (int k : succ[j])
+      for (int q = soff[j]; q < soff[j + 1]; q++) {
+        const int k = succ[q];
         if (--indeg[k] == 0) ready[is_diag(rl[k]) ? 1 : 0].push_back(k);
+      }
     want_diag = !want_diag;
   }
   rl.swap(ord);
-  std::vector<RegOp> out;
+  std::vector<RegOp> out, fac, rest, gen;
+  out.reserve(rl.size());
   size_t i = 0;
   const int D = 1 << K;
   while (i < rl.size()) {
@@ -164,16 +175,53 @@ void merge_diagonals(std::vector<RegOp>& rl, int K, Pool& pool) {
     }
     size_t e = i;
     while (e < rl.size() && is_diag(rl[e])) e++;
-    std::vector<RegOp> fac, rest;
+    fac.clear();
+    rest.clear();
     for (size_t k = i; k < e; k++) (slot_only(rl[k]) ? fac : rest).push_back(rl[k]);
     if (!fac.empty()) {   // even a single slot factor: a table multiply avoids per-element selects
       // entry j = product of the run's factors at register index j, divided by entry 0; an
       // entry whose factors all equal their values at index 0 is exactly 1 and skipped (it is
       // outside the mask), and entry 0's value (a phase of the whole tile) is kept after the
       // table for the pass-level fold
-      std::vector<cd> tab(D, cd(1, 0));
+      cd tab[32];
+      for (int j = 0; j < D; j++) tab[j] = cd(1, 0);
       uint32_t mask = 0;
+      // factors on one slot (a diagonal on the slot, a phase where only that slot's bit is
+      // set) multiply into one pair (value at bit 0, value at bit 1) first, so that the table
+      // costs one pass per slot instead of one per factor
+      cd sd[32][2];
+      uint32_t used = 0;
+      gen.clear();
       for (const RegOp& r : fac) {
+        int sl = -1;
+        cd d0(1, 0), d1(1, 0);
+        if (r.type == OP_DIAG && r.csl == 0 && r.s0 >= 0) {
+          sl = r.s0;
+          d0 = cd(pool.f64[2 * r.mat], pool.f64[2 * r.mat + 1]);
+          d1 = cd(pool.f64[2 * (r.mat + 1)], pool.f64[2 * (r.mat + 1) + 1]);
+        } else if (r.type == OP_PHASE && __builtin_popcount(r.csl) == 1) {
+          sl = __builtin_ctz(r.csl);
+          d1 = r.neg ? cd(-1, 0) : cd(pool.f64[2 * r.mat], pool.f64[2 * r.mat + 1]);
+        }
+        if (sl < 0) {
+          gen.push_back(r);
+          continue;
+        }
+        if (!((used >> sl) & 1u)) {
+          sd[sl][0] = sd[sl][1] = cd(1, 0);
+          used |= 1u << sl;
+        }
+        sd[sl][0] *= d0;
+        sd[sl][1] *= d1;
+      }
+      for (uint32_t u = used; u; u &= u - 1) {
+        const int sl = __builtin_ctz(u);
+        for (int j = 0; j < D; j++) tab[j] *= sd[sl][(j >> sl) & 1];
+        if (sd[sl][0] != sd[sl][1])
+          for (int j = 0; j < D; j++)
+            if ((j >> sl) & 1) mask |= 1u << j;
+      }
+      for (const RegOp& r : gen) {
         // this factor's value at register index j (1 where its slot controls are not all set)
         auto fval = [&](int j) -> cd {
           if (((uint32_t)j & r.csl) != r.csl) return cd(1, 0);
