@@ -24,15 +24,18 @@ namespace qs {
 int default_tile_bits(int dtype) { return dtype == QS_C128 ? 12 : 13; }
 
 // Per-launch cost coefficients measured on GB300 (ms, ms per byte, ms per counted
-// instruction): HBM-bound kernels at the bandwidth they reach (tile-pass floor ~6.5 TB/s,
-// per-gate ~6.4, permutation ~5.7, dense tensor-core block 3.6 ms per 17.2 GB); the tile
-// passes' arithmetic from the 30-qubit circuits (complex64 ~395 ms, double-float ~2030 ms per
-// circuit, less their HBM floor, over the counted instructions); native FP64 at 1.7 DFMA
-// per clock per SM.
+// instruction): HBM-bound kernels at the bandwidth they reach (per-gate ~6.4 TB/s,
+// permutation ~5.7, dense tensor-core block 3.6 ms per 17.2 GB); a tile pass's per-byte
+// term is what a pass with almost no arithmetic costs (complex64 4.4 ms per 17.2 GB;
+// double-float fitted on the fused 30-qubit plans, whose passes keep the state in
+// double-float form), its per-instruction term the rest of the 30-qubit circuits' time
+// (complex64 ~246 ms, double-float ~1084 ms per circuit) over the counted instructions;
+// native FP64 at 1.7 DFMA per clock per SM.
 qs_cost_model default_cost_model(Policy pol) {
   qs_cost_model m{};
-  const double tile_alu = pol == POL_F32 ? 7.2e-11 : (pol == POL_DF ? 4.12e-11 : 1.87e-9);
-  const double c_tile[3] = {0.005, 1.0 / 6.5e9, tile_alu};
+  const double tile_alu = pol == POL_F32 ? 7.0e-11 : (pol == POL_DF ? 4.27e-11 : 1.87e-9);
+  const double tile_byte = pol == POL_F32 ? 1.0 / 3.9e9 : (pol == POL_DF ? 1.0 / 5.37e9 : 1.0 / 6.5e9);
+  const double c_tile[3] = {0.005, tile_byte, tile_alu};
   const double c_gate[3] = {0.005, 1.0 / 6.4e9, pol == POL_F64 ? 1.87e-9 : 0.0};
   const double c_perm[3] = {0.005, 1.0 / 5.7e9, 0.0};
   const double c_dense[3] = {0.005, 3.6 / 17.18e9, 0.0};
