@@ -88,25 +88,24 @@ qs_status batch_from_plans(const std::vector<const qs_plan*>& plans, qs_dtype dt
     elems += ((size_t)1 << p->n);
     elems = (elems + 31) & ~(size_t)31;   // 256-byte aligned starts
   }
+  // offsets of each plan's stages, register ops, tile ops and pool entries in the
+  // concatenation (every circuit's entries start 16-byte aligned, so that its tables stay
+  // aligned), and its passes
+  std::vector<int> sbase(count), rbase(count), dbase(count);
+  std::vector<size_t> pbase(count);
+  size_t ns = 0, nr = 0, nd = 0, np = 0;
   for (int i = 0; i < count; i++) {
     const CompileResult& cr = plans[i]->cr;
     b->pol = cr.pol;
-    const int sbase = (int)b->stages.size(), rbase = (int)b->rops.size(), dbase = (int)b->dops.size();
-    const int pbase = (int)b->pool.entries();
-    for (StageRec st : cr.stages) {
-      st.op0 += (st.kind == 0) ? rbase : dbase;
-      b->stages.push_back(st);
-    }
-    for (RegOp r : cr.reg_ops) {
-      if (r.mat >= 0) r.mat += pbase;
-      b->rops.push_back(r);
-    }
-    for (DevOp d : cr.tile_ops) {
-      if (d.mat >= 0) d.mat += pbase;
-      b->dops.push_back(d);
-    }
-    b->pool.f64.insert(b->pool.f64.end(), cr.pool.f64.begin(), cr.pool.f64.end());
-    if (b->pool.entries() & 1) b->pool.add(cd(0, 0));   // next circuit's tables stay 16-byte aligned
+    sbase[i] = (int)ns;
+    rbase[i] = (int)nr;
+    dbase[i] = (int)nd;
+    pbase[i] = np;
+    ns += cr.stages.size();
+    nr += cr.reg_ops.size();
+    nd += cr.tile_ops.size();
+    np += cr.pool.entries();
+    np += np & 1;
     for (const Step& s : cr.steps) {
       if (s.kind != ST_PASS) {
         delete b;
@@ -114,7 +113,7 @@ qs_status batch_from_plans(const std::vector<const qs_plan*>& plans, qs_dtype dt
       }
       BatchPass bp;
       bp.tp = s.pass;
-      bp.tp.st0 += sbase;
+      bp.tp.st0 += sbase[i];
       bp.psi_off = b->off[i];
       if (b->K == 0) b->K = bp.tp.K;
       if (bp.tp.K != b->K) {
@@ -128,7 +127,46 @@ qs_status batch_from_plans(const std::vector<const qs_plan*>& plans, qs_dtype dt
     b->stats.n_gates += cr.stats.n_gates;
     b->stats.n_passes += cr.stats.n_passes;
   }
-  if (b->pool.entries() == 0) b->pool.add(cd(0, 0));
+  if (np == 0) np = 1;
+  // the concatenation itself, and the pool in the device format, spread over the host's
+  // cores (for thousands of circuits these are hundreds of megabytes)
+  b->stages.resize(ns);
+  b->rops.resize(nr);
+  b->dops.resize(nd);
+  const size_t eb = Pool::entry_bytes(b->pol);
+  std::vector<unsigned char> ser(np * eb, 0);
+  {
+    std::atomic<int> next(0);
+    auto worker = [&] {
+      for (int i = next.fetch_add(1); i < count; i = next.fetch_add(1)) {
+        const CompileResult& cr = plans[i]->cr;
+        const int pb = (int)pbase[i];
+        for (size_t k = 0; k < cr.stages.size(); k++) {
+          StageRec st = cr.stages[k];
+          st.op0 += (st.kind == 0) ? rbase[i] : dbase[i];
+          b->stages[sbase[i] + k] = st;
+        }
+        for (size_t k = 0; k < cr.reg_ops.size(); k++) {
+          RegOp r = cr.reg_ops[k];
+          if (r.mat >= 0) r.mat += pb;
+          b->rops[rbase[i] + k] = r;
+        }
+        for (size_t k = 0; k < cr.tile_ops.size(); k++) {
+          DevOp d = cr.tile_ops[k];
+          if (d.mat >= 0) d.mat += pb;
+          b->dops[dbase[i] + k] = d;
+        }
+        if (cr.pool.entries()) cr.pool.serialise_into(b->pol, ser.data() + pbase[i] * eb);
+      }
+    };
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = std::max(1u, std::min(nt, 64u));
+    if ((int)nt > count) nt = (unsigned)count;
+    std::vector<std::thread> pool;
+    for (unsigned t = 1; t < nt; t++) pool.emplace_back(worker);
+    worker();
+    for (auto& t : pool) t.join();
+  }
   b->total_elems = elems;
   size_t maxw = 0;
   for (auto& v : per_circuit) maxw = std::max(maxw, v.size());
@@ -161,7 +199,6 @@ qs_status batch_from_plans(const std::vector<const qs_plan*>& plans, qs_dtype dt
   b->psi = dev_alloc_as(elems * b->store_bytes, stream, b->native_alloc);
   if (b->psi) b->allocs.push_back({b->psi, elems * b->store_bytes});
   else e = cudaErrorMemoryAllocation;
-  std::vector<unsigned char> ser = b->pool.serialise(b->pol);
   b->stages_d = upload(b, b->stages, &e);
   b->rops_d = upload(b, b->rops, &e);
   b->dops_d = upload(b, b->dops, &e);

@@ -128,24 +128,22 @@ HGate make_1q_gate(int q, const cd m[4]) {
   return g;
 }
 
-std::vector<unsigned char> Pool::serialise(Policy pol) const {
+size_t Pool::entry_bytes(Policy pol) { return pol == POL_F32 ? 8 : (pol == POL_F64 ? 16 : 48); }
+
+void Pool::serialise_into(Policy pol, unsigned char* dst) const {
   const size_t E = entries();
-  std::vector<unsigned char> out;
   if (pol == POL_F32) {
-    out.resize(E * 8);
-    float* f = (float*)out.data();
+    float* f = (float*)dst;
     for (size_t k = 0; k < E; k++) {
       f[2 * k] = (float)f64[2 * k];
       f[2 * k + 1] = (float)f64[2 * k + 1];
     }
   } else if (pol == POL_F64) {
-    out.resize(E * 16);
-    memcpy(out.data(), f64.data(), E * 16);
+    memcpy(dst, f64.data(), E * 16);
   } else {
     // double-float lane patterns of u = ur + i ui (12 floats): (ur, ur) and its negation,
     // (-ui, ui) and its negation, then the negated low parts of (ur, ur) and (-ui, ui)
-    out.resize(E * 48);
-    float* f = (float*)out.data();
+    float* f = (float*)dst;
     for (size_t k = 0; k < E; k++) {
       const double ur = f64[2 * k], ui = f64[2 * k + 1];
       const float rh = (float)ur, rl = (float)(ur - (double)rh);
@@ -156,6 +154,11 @@ std::vector<unsigned char> Pool::serialise(Policy pol) const {
       e[8] = -rl; e[9] = -rl; e[10] = il; e[11] = -il;
     }
   }
+}
+
+std::vector<unsigned char> Pool::serialise(Policy pol) const {
+  std::vector<unsigned char> out(entries() * entry_bytes(pol));
+  if (!out.empty()) serialise_into(pol, out.data());
   return out;
 }
 

@@ -205,6 +205,8 @@ struct Pool {
   size_t entries() const { return f64.size() / 2; }
   // serialised for a policy: F32 -> float2, F64 -> double2, DF -> 48-byte lane patterns
   std::vector<unsigned char> serialise(Policy pol) const;
+  void serialise_into(Policy pol, unsigned char* dst) const;   // entries() * entry_bytes(pol) bytes
+  static size_t entry_bytes(Policy pol);
 };
 
 // Lower one gate to device ops with positions mapped through `bitpos` (logical qubit ->

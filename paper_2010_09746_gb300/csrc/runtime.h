@@ -80,7 +80,6 @@ struct qs_batch {
   std::vector<qs::StageRec> stages;
   std::vector<qs::RegOp> rops;
   std::vector<qs::DevOp> dops;
-  qs::Pool pool;
   struct Wave {
     std::vector<qs::BatchPass> passes;
     std::vector<uint64_t> prefix;

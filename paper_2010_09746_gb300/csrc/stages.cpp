@@ -691,23 +691,31 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
           cd u[4], d1[4], rx[4], d2[4];
           for (int k = 0; k < 4; k++) u[k] = cd(out->pool.f64[2 * (r.mat + k)], out->pool.f64[2 * (r.mat + k) + 1]);
           if (euler_split(u, d1, rx, d2)) {
+            // the three factors take over the general matrix's four pool entries (its own):
+            // the phase, the rotation (c, s), the two diagonal values
+            auto put = [&](int k, const cd& z) {
+              out->pool.f64[2 * (size_t)(r.mat + k)] = z.real();
+              out->pool.f64[2 * (size_t)(r.mat + k) + 1] = z.imag();
+            };
             RegOp p = r;
             if (d1[3] != cd(1, 0)) {   // diag(1, e^{i d}): a phase where the slot's bit is 1
               p.type = OP_PHASE;
               p.csl = 1u << r.s0;
               p.s0 = -1;
               p.neg = 0;
-              p.mat = out->pool.add(d1[3]);
+              put(0, d1[3]);
               rl.push_back(p);
             }
             p = r;
             p.type = OP_RX;
-            p.mat = out->pool.add(cd(rx[0].real(), -rx[1].imag()));
+            p.mat = r.mat + 1;
+            put(1, cd(rx[0].real(), -rx[1].imag()));
             rl.push_back(p);
             p = r;
             p.type = OP_DIAG;
-            p.mat = out->pool.add(d2[0]);
-            out->pool.add(d2[3]);
+            p.mat = r.mat + 2;
+            put(2, d2[0]);
+            put(3, d2[3]);
             rl.push_back(p);
             continue;
           }
