@@ -409,6 +409,23 @@ int main(int argc, char** argv) {
     }
   }
   fprintf(stderr, "max_register_abs %.6e\nmin_register_scale %.6e\n", g_max_abs, min_scale);
+  // the step sequence with the storage form each pass reads and writes (b = binary64,
+  // d = double-float), for the test of the compiler's double-float storage rule
+  fprintf(stderr, "steps");
+  for (const Step& s : cr.steps) {
+    switch (s.kind) {
+      case ST_PASS:
+        fprintf(stderr, " P%c%c%s", (s.pass.flags & kPassInDF) ? 'd' : 'b', (s.pass.flags & kPassOutDF) ? 'd' : 'b',
+                s.pass.nst == 0 ? "0" : "");
+        break;
+      case ST_GATE: fprintf(stderr, " G"); break;
+      case ST_PERMUTE: fprintf(stderr, " X"); break;
+      case ST_RENORM: fprintf(stderr, " R"); break;
+      case ST_DENSE: fprintf(stderr, " D"); break;
+      default: fprintf(stderr, " ?"); break;
+    }
+  }
+  fprintf(stderr, "\n");
   FILE* g = fopen(argv[2], "wb");
   if (!g) return 2;
   const int32_t nsteps = (int32_t)cr.steps.size();

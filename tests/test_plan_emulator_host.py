@@ -65,6 +65,7 @@ def emulator(tmp_path_factory):
         assert r.returncode == 0, r.stderr[-3000:]
         run.max_register_abs = float(r.stderr.split("max_register_abs")[1].split()[0])
         run.min_register_scale = float(r.stderr.split("min_register_scale")[1].split()[0])
+        run.steps = r.stderr.split("steps", 1)[1].splitlines()[0].split()
         with open(out, "rb") as f:
             n2, nsteps = struct.unpack("<ii", f.read(8))
             sigma = np.frombuffer(f.read(4 * n2), dtype=np.int32)
@@ -109,6 +110,43 @@ def test_fused_single_qubit_runs(emulator, dtype, arith, n, L, c):
     check(got, circ, n)
     unfused, _ = emulator(n, circ, mode="tile", dtype=dtype, arith=arith, tile_bits=L, low_bits=c, fuse=False)
     assert float(np.max(np.abs(got - unfused))) <= 1e-12
+
+
+def storage_forms_consistent(steps):
+    """The state's storage form along a plan: binary64 at its start and end and into every
+    per-gate kernel, renormalisation and dense block; a pass reads the form the step before
+    left (a permutation moves elements unchanged)."""
+    form = "b"
+    for t in steps:
+        if t[0] == "P":
+            if t[1] != form:
+                return False
+            form = t[2]
+        elif t in ("G", "R", "D"):
+            if form != "b":
+                return False
+    return form == "b"
+
+
+@pytest.mark.parametrize("mode,dtype,arith,kw", [
+    ("tile", "c128", "df", {"tile_bits": 8}), ("tile", "c128", "df", {"tile_bits": 8, "renorm_every": 2}),
+    ("paper", "c128", "df", {"tile_bits": 8}), ("paper", "c128", "df", {"tile_bits": 6}),
+    ("tile", "c128", "f64", {"tile_bits": 8}), ("tile", "c64", "auto", {"tile_bits": 8})])
+def test_double_float_storage_between_passes(emulator, mode, dtype, arith, kw):
+    """Consecutive double-float tile passes keep the state in double-float form (no binary64
+    split / join between them); everything else sees binary64, and the results still match
+    the oracle (the emulator computes in complex<double>, so the check here is the rule)."""
+    n = 12
+    circ = wc.rzrx_cz_circuit(n, 12, seed=5) + wc.random_mixed_circuit(n, 60, seed=5, kmax=2)
+    got, _ = emulator(n, circ, mode=mode, dtype=dtype, arith=arith, **kw)
+    check(got, circ, n)
+    steps = emulator.steps
+    assert storage_forms_consistent(steps), steps
+    uses_df = any("d" in t[1:3] for t in steps if t[0] == "P")
+    if dtype == "c128" and arith == "df" and "renorm_every" not in kw:
+        assert sum(t[0] == "P" for t in steps) >= 2 and uses_df, steps
+    if arith != "df":
+        assert not uses_df, steps
 
 
 @pytest.mark.parametrize("dtype,arith", MODES)
