@@ -307,7 +307,12 @@ qs_status qs_plan_final_permutation(qs_plan_t p, int* perm_out);
 qs_status qs_plan_get_trace(qs_plan_t p, int32_t* kinds, int32_t* values, size_t max, size_t* count);
 
 /* Enqueue the plan on the state's stream.  The state must have the plan's n and dtype and
- * the permutation the plan was compiled for; afterwards sigma is the plan's final one. */
+ * the permutation the plan was compiled for; afterwards sigma is the plan's final one.
+ * Complex128 with double-float arithmetic: between consecutive tile passes of the plan the
+ * state buffer holds an internal double-float form (four floats per element); it holds
+ * binary64 again once the plan's work on the stream has completed, which is when any read
+ * through this API or the device pointer is ordered.  A plan whose execution failed (for
+ * example QS_ETIMEOUT) leaves the state undefined. */
 qs_status qs_execute(qs_handle h, qs_plan_t p);
 
 /* qs_compile + qs_execute + qs_plan_destroy; asynchronous like qs_execute. */
