@@ -154,10 +154,12 @@ def time_plan(plan: Plan, state: State, reps: int = 2) -> float:
 
 def autotune(n: int, circuit: Sequence, dtype: str = "c128", model: Optional[CostModel] = None,
              tile_bits: Sequence[int] = (11, 12, 13), reg_bits: Sequence[int] = (3, 4, 5), measure_top: int = 2,
-             cache_path: Optional[str] = None, state: Optional[State] = None) -> dict:
-    """Pick tile width L and register bits K for `circuit`: rank every candidate with the
-    cost model (or by predicted bytes + instructions when no model is given), time the
-    best `measure_top` on the GPU, return the fastest as compile options."""
+             cache_path: Optional[str] = None, state: Optional[State] = None,
+             low_bits: Sequence[int] = (0,)) -> dict:
+    """Pick tile width L, register bits K and segment bits c (low_bits; 0 = the dtype's
+    default) for `circuit`: rank every candidate with the cost model (or by predicted bytes
+    + instructions when no model is given), time the best `measure_top` on the GPU, return
+    the fastest as compile options."""
     circuit = list(circuit)
     key = circuit_key(n, dtype, circuit)
     dev = _device_name()
@@ -172,28 +174,30 @@ def autotune(n: int, circuit: Sequence, dtype: str = "c128", model: Optional[Cos
     cands = []
     for L in tile_bits:
         for K in reg_bits:
-            if K > kmax or L > n or L - K < 0:
-                continue
-            p = qs_compile(n, circuit, mode="tile", dtype=dtype, tile_bits=L, reg_bits=K)
-            launches, b, a = plan_features(p)
-            pred = model.predict_plan(p, dtype) if model is not None else None
-            if pred is None:   # rough: the HBM time plus the arithmetic at half the FP32 issue rate
-                pred = b / 6.8e12 * 1e3 + a / 20e12 * 1e3
-            cands.append((pred, L, K, p))
+            for c in low_bits:
+                if K > kmax or L > n or L - K < 0 or c > L:
+                    continue
+                p = qs_compile(n, circuit, mode="tile", dtype=dtype, tile_bits=L, reg_bits=K, low_bits=c)
+                launches, b, a = plan_features(p)
+                pred = model.predict_plan(p, dtype) if model is not None else None
+                if pred is None:   # rough: the HBM time plus the arithmetic at half the FP32 issue rate
+                    pred = b / 6.8e12 * 1e3 + a / 20e12 * 1e3
+                cands.append((pred, L, K, c, p))
     cands.sort(key=lambda t: t[0])
     own = state is None
     st = state or State(n, dtype)
     measured = []
-    for pred, L, K, p in cands[:max(1, measure_top)]:
+    for pred, L, K, c, p in cands[:max(1, measure_top)]:
         ms = time_plan(p, st)
-        measured.append({"tile_bits": L, "reg_bits": K, "predicted_ms": pred, "measured_ms": ms})
+        measured.append({"tile_bits": L, "reg_bits": K, "low_bits": c, "predicted_ms": pred, "measured_ms": ms})
     if own:
         st.close()
     best = min(measured, key=lambda r: r["measured_ms"])
-    out = {"tile_bits": best["tile_bits"], "reg_bits": best["reg_bits"], "measured_ms": best["measured_ms"],
-           "candidates": measured, "ranked": [(round(c[0], 3), c[1], c[2]) for c in cands]}
+    out = {"tile_bits": best["tile_bits"], "reg_bits": best["reg_bits"], "low_bits": best["low_bits"],
+           "measured_ms": best["measured_ms"], "candidates": measured,
+           "ranked": [(round(c[0], 3), c[1], c[2], c[3]) for c in cands]}
     if cache_path:
-        cache[ck] = {k: out[k] for k in ("tile_bits", "reg_bits", "measured_ms")}
+        cache[ck] = {k: out[k] for k in ("tile_bits", "reg_bits", "low_bits", "measured_ms")}
         tmp = cache_path + ".tmp"
         with open(tmp, "w") as f:
             json.dump(cache, f, indent=1)

@@ -19,14 +19,15 @@ def test_autotune_and_cache(tmp_path):
     n = 16
     circ = wc.rzrx_cz_circuit(n, 8, seed=2)
     cache = os.path.join(tmp_path, "tune.json")
-    r = tuning.autotune(n, circ, dtype="c128", tile_bits=(10, 12), reg_bits=(3, 4), measure_top=2,
+    r = tuning.autotune(n, circ, dtype="c128", tile_bits=(10, 12), reg_bits=(3, 4), low_bits=(3, 4), measure_top=2,
                         cache_path=cache)
-    assert r["tile_bits"] in (10, 12) and r["reg_bits"] in (3, 4)
-    assert len(r["candidates"]) == 2
+    assert r["tile_bits"] in (10, 12) and r["reg_bits"] in (3, 4) and r["low_bits"] in (3, 4)
+    assert len(r["candidates"]) == 2 and len(r["ranked"]) == 8
     r2 = tuning.autotune(n, circ, dtype="c128", cache_path=cache)
     assert r2.get("cached") and r2["tile_bits"] == r["tile_bits"]
     st = qs.State(n, "c128")
-    st.execute(qs.compile(n, circ, mode="tile", dtype="c128", tile_bits=r["tile_bits"], reg_bits=r["reg_bits"]))
+    st.execute(qs.compile(n, circ, mode="tile", dtype="c128", tile_bits=r["tile_bits"], reg_bits=r["reg_bits"],
+                          low_bits=r["low_bits"]))
     assert np.abs(st.amplitudes() - sv.simulate(n, circ)).max() <= 1e-12
 
 
