@@ -884,7 +884,7 @@ def main(argv=None):
     ap.add_argument("--serve-requests", type=int, default=500, help="requests per serving load point (0 = skip)")
     ap.add_argument("--serve-order", default="fifo", choices=["fifo", "sjf"],
                     help="admission order: first come, or least estimated work first (1 s maximum wait)")
-    ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.5, 0.9],
+    ap.add_argument("--serve-loads", type=float, nargs="*", default=[0.5, 0.9, 1.1],
                     help="Poisson arrival rates as fractions of the measured saturation throughput")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-mem-gib", type=float, default=96.0)
