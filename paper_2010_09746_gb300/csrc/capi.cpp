@@ -581,7 +581,7 @@ qs_status qs_compile(int n, const qs_op* ops, size_t nops, const double* mats, s
   p->dtype = o.dtype;
   p->pol = policy_for((qs_dtype)o.dtype, (qs_arith)o.arith);
   p->sigma0 = s0;
-  if (!compile_circuit(n, gates, s0, o, &p->cr, &err)) {
+  if (!compile_circuit(n, std::move(gates), s0, o, &p->cr, &err)) {
     delete p;
     return fail(QS_EINVAL, err);
   }

@@ -142,14 +142,23 @@ bool is_identity(const cd m[4]) { return m[0] == cd(1, 0) && m[1] == cd(0, 0) &&
 // with the other register qubits.  So a run is fused when it holds two or more non-diagonal
 // gates, or a general one (neither RX nor X in form), or consists of diagonal gates only (one
 // diagonal factor).  A run whose one non-diagonal gate is an RX or an X is kept as it is.
-void fuse_single_qubit_runs(int n, const std::vector<HGate>& in, std::vector<HGate>* out,
-                            std::vector<std::vector<int>>* origin) {
+void fuse_single_qubit_runs(int n, std::vector<HGate>& in, std::vector<HGate>* out, FuseOrigin* origin) {
   out->clear();
-  origin->clear();
+  out->reserve(in.size());
+  origin->off.assign(1, 0);
+  origin->idx.clear();
+  origin->idx.reserve(in.size());
   std::vector<std::vector<int>> run(n);
-  auto emit = [&](const HGate& g, std::vector<int> src) {
-    out->push_back(g);
-    origin->push_back(std::move(src));
+  auto close = [&] { origin->off.push_back((int)origin->idx.size()); };
+  auto keep = [&](int i) {   // an input gate as it is (moved: the input is consumed)
+    out->push_back(std::move(in[i]));
+    origin->idx.push_back(i);
+    close();
+  };
+  auto emit = [&](HGate g, const std::vector<int>& src) {
+    out->push_back(std::move(g));
+    origin->idx.insert(origin->idx.end(), src.begin(), src.end());
+    close();
   };
   auto flush = [&](int q) {
     std::vector<int>& r = run[q];
@@ -165,7 +174,7 @@ void fuse_single_qubit_runs(int n, const std::vector<HGate>& in, std::vector<HGa
       general |= !x_form && !rx_form;
     }
     if (r.size() < 2 || (nd == 1 && !general)) {   // a lone general gate splits at lowering
-      for (int i : r) emit(in[i], {i});
+      for (int i : r) keep(i);
       r.clear();
       return;
     }
@@ -179,7 +188,7 @@ void fuse_single_qubit_runs(int n, const std::vector<HGate>& in, std::vector<HGa
     // diagonal factors wherever their phase tables are cheapest
     cd d1[4], rx[4], d2[4];
     if (is_identity(U)) {
-      for (int i : r) emit(in[i], {i});   // an exact identity: keep the gates (rare)
+      for (int i : r) keep(i);   // an exact identity: keep the gates (rare)
     } else if (U[1] == cd(0, 0) && U[2] == cd(0, 0)) {
       emit(make_1q_gate(q, U), r);
     } else if (euler_split(U, d1, rx, d2)) {
@@ -198,7 +207,7 @@ void fuse_single_qubit_runs(int n, const std::vector<HGate>& in, std::vector<HGa
       continue;
     }
     for (int t = 0; t < g.nq; t++) flush(g.q[t]);
-    emit(g, {i});
+    keep(i);
   }
   for (int q = 0; q < n; q++) flush(q);
 }
@@ -587,8 +596,7 @@ bool compile_paper(int n, const std::vector<HGate>& gates, std::vector<int> sigm
 // lowest bit).  The pass then runs that sweep.
 // origin (may be null): the input gates each entry of `gates` stands for (gate fusion)
 bool compile_tile(int n, const std::vector<HGate>& gates, const std::vector<int>& sigma, const qs_compile_opts& o,
-                  int store_bytes, CompileResult* out, std::string* err,
-                  const std::vector<std::vector<int>>* origin = nullptr) {
+                  int store_bytes, CompileResult* out, std::string* err, const FuseOrigin* origin = nullptr) {
   const int L = std::min(o.tile_bits, n);
   const int c = std::min(o.low_bits, L);
   const int G = (int)gates.size();
@@ -616,7 +624,7 @@ bool compile_tile(int n, const std::vector<HGate>& gates, const std::vector<int>
   std::vector<uint64_t> okm(G, 0);   // candidate-bit masks of the pass search
   for (int v = 0; v < G; v++)
     if (__builtin_popcountll(ndm[v] | low) > L) {
-      const int g0 = (origin && !(*origin)[v].empty()) ? (*origin)[v][0] : v;
+      const int g0 = (origin && origin->count(v)) ? origin->idx[origin->off[v]] : v;
       *err = "gate " + std::to_string(g0) + " needs more qubits than a tile holds";
       return false;
     }
@@ -761,7 +769,7 @@ void set_double_float_storage(int n, CompileResult* out) {
 
 }  // namespace
 
-bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<int>& sigma0,
+bool compile_circuit(int n, std::vector<HGate> gates, const std::vector<int>& sigma0,
                      const qs_compile_opts& o, CompileResult* out, std::string* err) {
   auto t0 = std::chrono::steady_clock::now();
   const int store_bytes = (o.dtype == QS_C128) ? 16 : 8;
@@ -797,21 +805,22 @@ bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<i
       ok = compile_tile(n, gates, sigma0, o, store_bytes, out, err);
     } else {
       std::vector<HGate> fused;
-      std::vector<std::vector<int>> origin;
-      fuse_single_qubit_runs(n, gates, &fused, &origin);
+      FuseOrigin origin;
+      fuse_single_qubit_runs(n, gates, &fused, &origin);   // consumes gates
       ok = compile_tile(n, fused, sigma0, o, store_bytes, out, err, &origin);
       for (size_t i = 0; i < fused.size(); i++)
-        if (origin[i].size() >= 2) out->stats.n_fused += (int64_t)origin[i].size();
+        if (origin.count(i) >= 2) out->stats.n_fused += origin.count(i);
       if (ok) {   // the trace names input gates: a fused gate lists the gates it stands for
         std::vector<std::pair<int, int>> tr;
+        tr.reserve(out->trace.size());
         for (size_t i = 0; i < out->trace.size(); i++) {
           const auto& e = out->trace[i];
           if (e.first == 0) {
-            for (int v : origin[e.second]) tr.push_back({0, v});
+            for (int k = origin.off[e.second]; k < origin.off[e.second + 1]; k++) tr.push_back({0, origin.idx[k]});
           } else if (e.first == 5) {   // dense block over the next e.second (fused) gates
             int cnt = 0;
             for (int k = 1; k <= e.second && i + k < out->trace.size(); k++)
-              cnt += (int)origin[out->trace[i + k].second].size();
+              cnt += origin.count(out->trace[i + k].second);
             tr.push_back({5, cnt});
           } else {
             tr.push_back(e);

@@ -190,10 +190,14 @@ bool euler_split(const cd U[4], cd d1[4], cd rx[4], cd d2[4]);
 // multi-qubit gate on that qubit in between) that holds at least two non-diagonal gates, a
 // general one (neither RX nor X in form), or only diagonal ones, is replaced by its product,
 // re-expressed as at most three gates
-// (diagonal, RX, diagonal).  origin[i] lists the input gates that output gate i stands for
-// (empty for the extra factors of a product); every input gate appears exactly once.
-void fuse_single_qubit_runs(int n, const std::vector<HGate>& in, std::vector<HGate>* out,
-                            std::vector<std::vector<int>>* origin);
+// (diagonal, RX, diagonal).  The origin lists the input gates each output gate stands for
+// (empty for the extra factors of a product); every input gate appears exactly once.  The
+// input gates are moved into the output (`in` is consumed).
+struct FuseOrigin {
+  std::vector<int> off, idx;   // output gate i stands for input gates idx[off[i] .. off[i + 1])
+  int count(size_t i) const { return off[i + 1] - off[i]; }
+};
+void fuse_single_qubit_runs(int n, std::vector<HGate>& in, std::vector<HGate>* out, FuseOrigin* origin);
 // Matrix pool in policy format.
 struct Pool {
   std::vector<double> f64;  // (re, im) pairs
@@ -242,7 +246,7 @@ struct CompileResult {
   std::vector<int> sigma_final;
   qs_plan_stats stats{};
 };
-bool compile_circuit(int n, const std::vector<HGate>& gates, const std::vector<int>& sigma0,
+bool compile_circuit(int n, std::vector<HGate> gates, const std::vector<int>& sigma0,
                      const qs_compile_opts& o, CompileResult* out, std::string* err);
 
 // Cost model the compiler uses when the caller gives none: per-launch coefficients measured
