@@ -548,17 +548,22 @@ __device__ __forceinline__ RegOp load_regop(const RegOp* p) {
   return r;
 }
 
-// Phase frame of the double-float policy: tile element i is held as (-i)^popcount(i) times
-// its value while the tile is in register format.
+// Phase frame of the double-float policy: while in register format, an element is held as
+// (-i)^popcount(its storage address) times its value, i.e. tile element i of the block at
+// `base` carries (-i)^(popcount(i) + popcount(base)).  Within a pass that is the tile frame times a
+// factor common to the tile, which every op of the pass (all linear) carries along; and a
+// permutation of address bits keeps every popcount, so the double-float storage form a plan
+// keeps between its passes stays in this frame: only binary64 loads and stores rotate.
+// wb = popcount(base) mod 4.
 template <class A>
-__device__ __forceinline__ typename A::reg_t to_frame(typename A::reg_t v, uint32_t i) {
-  if constexpr (A::kFrame) return A::rot_q(v, __popc(i) & 3u);
-  else return v;
+__device__ __forceinline__ typename A::reg_t load_framed(typename A::store_t v, uint32_t q, bool df) {
+  if constexpr (A::kFrame) return df ? A::from_df(v) : A::rot_q(A::from_store(v), q & 3u);
+  else return A::from_store_f(v, df);
 }
 template <class A>
-__device__ __forceinline__ typename A::reg_t from_frame(typename A::reg_t v, uint32_t i) {
-  if constexpr (A::kFrame) return A::rot_q(v, (0u - (uint32_t)__popc(i)) & 3u);
-  else return v;
+__device__ __forceinline__ typename A::store_t store_framed(typename A::reg_t v, uint32_t q, bool df) {
+  if constexpr (A::kFrame) return df ? A::to_df(v) : A::to_store(A::rot_q(v, (0u - q) & 3u));
+  else return A::to_store_f(v, df);
 }
 
 // One register stage over the whole tile.  from_store / to_store: the shared-memory tile
@@ -569,7 +574,7 @@ template <class A, int K, bool Lite>
 __device__ __forceinline__ void run_reg_stage(typename A::reg_t* T, const StageRec& sr, const RegOp* __restrict__ rops,
                                               const typename A::mat_t* __restrict__ pool, int L, Pad px,
                                               uint64_t base, bool from_store, bool to_store, bool df_in,
-                                              bool df_out) {
+                                              bool df_out, uint32_t wb) {
   using R = typename A::reg_t;
   using S = typename A::store_t;
   const uint32_t tile_mask = (L >= 32) ? 0xFFFFFFFFu : ((1u << L) - 1u);
@@ -615,8 +620,7 @@ __device__ __forceinline__ void run_reg_stage(typename A::reg_t* T, const StageR
       if constexpr (std::is_same<R, S>::value) {
         x[j] = T[p];
       } else if constexpr (A::kFrame) {
-        x[j] = from_store ? A::rot_q(A::from_store_f(reinterpret_cast<const S*>(T)[p], df_in), (wg + __popc(j)) & 3u)
-                          : T[p];
+        x[j] = from_store ? load_framed<A>(reinterpret_cast<const S*>(T)[p], wb + wg + __popc(j), df_in) : T[p];
       } else {
         x[j] = from_store ? A::from_store_f(reinterpret_cast<const S*>(T)[p], df_in) : T[p];
       }
@@ -679,7 +683,7 @@ __device__ __forceinline__ void run_reg_stage(typename A::reg_t* T, const StageR
       if constexpr (std::is_same<R, S>::value) {
         T[p] = x[j];
       } else if constexpr (A::kFrame) {
-        if (to_store) reinterpret_cast<S*>(T)[p] = A::to_store_f(A::rot_q(x[j], (0u - (wg + __popc(j))) & 3u), df_out);
+        if (to_store) reinterpret_cast<S*>(T)[p] = store_framed<A>(x[j], wb + wg + __popc(j), df_out);
         else T[p] = x[j];
       } else {
         if (to_store) reinterpret_cast<S*>(T)[p] = A::to_store_f(x[j], df_out);
@@ -740,17 +744,18 @@ __device__ __forceinline__ bool process_block(const typename A::store_t* psi, ty
 
   // ---- stages
   const bool df_in = (tp.flags & kPassInDF) != 0, df_out = (tp.flags & kPassOutDF) != 0;
+  const uint32_t wb = (uint32_t)__popcll(base) & 3u;   // the block's share of the storage-address frame
   bool in_store = true;   // the tile holds storage-format elements
   for (int k = 0; k < tp.nst; k++) {
     const StageRec sr = stages[tp.st0 + k];
     const bool last = (k == tp.nst - 1);
     if (sr.kind == 0) {
-      run_reg_stage<A, K, Lite>(T, sr, rops, pool, L, px, base, in_store, last, df_in, df_out);
+      run_reg_stage<A, K, Lite>(T, sr, rops, pool, L, px, base, in_store, last, df_in, df_out, wb);
       in_store = last;
     } else {
       if (kConv && in_store) {
         S* Ts = reinterpret_cast<S*>(T);
-        for (uint32_t i = tid; i < nelem; i += kTileThreads) T[px(i)] = to_frame<A>(A::from_store_f(Ts[px(i)], df_in), i);
+        for (uint32_t i = tid; i < nelem; i += kTileThreads) T[px(i)] = load_framed<A>(Ts[px(i)], wb + __popc(i), df_in);
         __syncthreads();
       }
       in_store = false;
@@ -767,7 +772,7 @@ __device__ __forceinline__ bool process_block(const typename A::store_t* psi, ty
     S* Ts = reinterpret_cast<S*>(T);
     for (uint32_t i = tid; i < nelem; i += kTileThreads) {
       const R v = T[px(i)];
-      Ts[px(i)] = A::to_store_f(from_frame<A>(v, i), df_out);
+      Ts[px(i)] = store_framed<A>(v, wb + __popc(i), df_out);
     }
   }
   // ---- store: bulk copies back (to dst); the tile is reused only after they have been
