@@ -311,9 +311,39 @@ static void run_pass(std::vector<C>& psi, const CompileResult& cr, const TilePas
   psi.swap(out);
 }
 
+// `--euler in.bin out.bin`: the library's Euler split of each 2x2 matrix in in.bin (count,
+// then 8 doubles per matrix, row-major re/im), written as a status and the three factors
+// (d1, rx, d2; 8 doubles each) per matrix, for the test to check against numpy.
+static int euler_mode(const char* in, const char* out) {
+  FILE* f = fopen(in, "rb");
+  if (!f) return 2;
+  int32_t count = 0;
+  if (fread(&count, 4, 1, f) != 1) return 2;
+  std::vector<double> m((size_t)count * 8);
+  if (count && fread(m.data(), 8, m.size(), f) != m.size()) return 2;
+  fclose(f);
+  FILE* g = fopen(out, "wb");
+  if (!g) return 2;
+  for (int k = 0; k < count; k++) {
+    C U[4], d1[4], rx[4], d2[4];
+    for (int e = 0; e < 4; e++) U[e] = C(m[8 * k + 2 * e], m[8 * k + 2 * e + 1]);
+    const int32_t okk = euler_split(U, d1, rx, d2) ? 1 : 0;
+    fwrite(&okk, 4, 1, g);
+    for (const C* fct : {d1, rx, d2})
+      for (int e = 0; e < 4; e++) {
+        const double re = fct[e].real(), im = fct[e].imag();
+        fwrite(&re, 8, 1, g);
+        fwrite(&im, 8, 1, g);
+      }
+  }
+  fclose(g);
+  return 0;
+}
+
 int main(int argc, char** argv) {
+  if (argc == 4 && std::string(argv[1]) == "--euler") return euler_mode(argv[2], argv[3]);
   if (argc != 3) {
-    fprintf(stderr, "usage: plan_emulator_host in.bin out.bin\n");
+    fprintf(stderr, "usage: plan_emulator_host in.bin out.bin | --euler in.bin out.bin\n");
     return 2;
   }
   FILE* f = fopen(argv[1], "rb");

@@ -78,6 +78,8 @@ def emulator(tmp_path_factory):
             idx |= ((ar >> q) & 1) << int(sigma[q])
         return psi[idx], nsteps
 
+    run.exe = exe
+    run.tmp = d
     return run
 
 
@@ -110,6 +112,43 @@ def test_fused_single_qubit_runs(emulator, dtype, arith, n, L, c):
     check(got, circ, n)
     unfused, _ = emulator(n, circ, mode="tile", dtype=dtype, arith=arith, tile_bits=L, low_bits=c, fuse=False)
     assert float(np.max(np.abs(got - unfused))) <= 1e-12
+
+
+def test_euler_split_of_2x2_unitaries(emulator):
+    """The split diag . RX . diag that fused runs and general gates take inside tile passes
+    (the library's own function): for Haar-random 2x2 unitaries and exact special cases (X, Y,
+    H, S, diagonal, an RX, a matrix with a tiny off-diagonal) the factors have the forms the
+    lowering needs -- d1 = diag(1, .), rx = c I - i s X with c, s >= 0, d2 diagonal -- and
+    their product, taken with numpy, reproduces the matrix to 1e-14."""
+    rng = np.random.default_rng(11)
+    h = 1 / np.sqrt(2)
+    mats = [wc.haar_2x2(rng) for _ in range(300)]
+    eps = 1e-9
+    mats += [np.array([[0, 1], [1, 0]]), np.array([[0, -1j], [1j, 0]]), np.array([[h, h], [h, -h]]),
+             np.diag([1, 1j]), np.diag([np.exp(0.3j), np.exp(-1.1j)]),
+             np.array([[np.cos(0.2), -1j * np.sin(0.2)], [-1j * np.sin(0.2), np.cos(0.2)]]),
+             np.array([[np.sqrt(1 - eps ** 2), eps], [-eps, np.sqrt(1 - eps ** 2)]]) * np.exp(0.7j)]
+    mats = [np.asarray(m, dtype=np.complex128) for m in mats]
+    inp, out = str(emulator.tmp / "euler_in.bin"), str(emulator.tmp / "euler_out.bin")
+    with open(inp, "wb") as f:
+        f.write(struct.pack("<i", len(mats)))
+        for m in mats:
+            f.write(np.ascontiguousarray(m.reshape(-1)).view(np.float64).tobytes())
+    r = subprocess.run([emulator.exe, "--euler", inp, out], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stderr
+    raw = open(out, "rb").read()
+    rec = 4 + 3 * 64
+    assert len(raw) == rec * len(mats)
+    for k, m in enumerate(mats):
+        ok = struct.unpack("<i", raw[rec * k: rec * k + 4])[0]
+        fac = np.frombuffer(raw[rec * k + 4: rec * (k + 1)], dtype=np.complex128).reshape(3, 2, 2)
+        d1, rx, d2 = fac
+        assert ok == 1, k
+        assert d1[0, 0] == 1 and d1[0, 1] == 0 and d1[1, 0] == 0, k
+        assert rx[0, 0] == rx[1, 1] and rx[0, 0].imag == 0 and rx[0, 0].real >= 0, k
+        assert rx[0, 1] == rx[1, 0] and rx[0, 1].real == 0 and rx[0, 1].imag <= 0, k
+        assert d2[0, 1] == 0 and d2[1, 0] == 0, k
+        assert np.max(np.abs(d2 @ rx @ d1 - m)) <= 1e-14, (k, np.max(np.abs(d2 @ rx @ d1 - m)))
 
 
 def storage_forms_consistent(steps):
