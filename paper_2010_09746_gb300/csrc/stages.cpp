@@ -85,14 +85,7 @@ uint32_t ctrl_slots(const RegOp& r) { return r.csl; }
 
 // Two register ops must keep their order iff one changes a slot the other reads: a
 // non-diagonal op changes its target slots; every op reads its targets and slot controls.
-bool conflict(const RegOp& a, const RegOp& b) {
-  const uint32_t wa = is_diag(a) ? 0u : target_slots(a), wb = is_diag(b) ? 0u : target_slots(b);
-  const uint32_t ra = (is_diag(a) ? diag_slots(a) : target_slots(a)) | ctrl_slots(a);
-  const uint32_t rb = (is_diag(b) ? diag_slots(b) : target_slots(b)) | ctrl_slots(b);
-  return (wa & rb) || (wb & ra);
-}
-
-// Reorder a stage's ops (a valid linear extension of their conflicts) so that diagonal ops
+// Reorder a stage's ops (a valid linear extension of those conflicts) so that diagonal ops
 // form long runs -- repeatedly emit every ready diagonal op, then every ready non-diagonal
 // one -- and replace the slot-only diagonal factors of each run by one table op:
 // entry j of a 2^K-entry table is the product of the run's factors at register index j
