@@ -110,6 +110,9 @@ struct qs_server {
   double now() const {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
+  // one amplitude vector per request: the server compiles tile-mode plans only, whose steps
+  // (tile passes, dense blocks, renormalisations) all run in place, so no request ever
+  // allocates the permutation buffer (the compile worker refuses a plan that would)
   size_t state_bytes(const Req& r) const { return (size_t)(r.dtype == QS_C128 ? 16 : 8) << r.n; }
   size_t readout_count(const Req& r) const {
     return (size_t)std::min<uint64_t>(1ull << r.n, (uint64_t)o.readout);
@@ -159,6 +162,17 @@ void compile_worker(qs_server* s) {
       if (st == QS_OK) qs_plan_destroy(p);
       r->status = r->cancel ? QS_ECANCELED : st;
       r->error = r->cancel ? "cancelled" : cerr;
+      finish_request(s, r, s->now());
+      s->cv_done.notify_all();
+      continue;
+    }
+    bool in_place = true;
+    for (const Step& stp : p->cr.steps)
+      if (stp.kind == ST_PERMUTE || (stp.kind == ST_PASS && stp.pass.swap_a != stp.pass.swap_b)) in_place = false;
+    if (!in_place) {   // the memory admission counts one vector per request
+      qs_plan_destroy(p);
+      r->status = QS_EUNSUPPORTED;
+      r->error = "served plans must run in place (no permutation buffer)";
       finish_request(s, r, s->now());
       s->cv_done.notify_all();
       continue;
