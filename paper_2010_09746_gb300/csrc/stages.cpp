@@ -90,17 +90,35 @@ uint32_t ctrl_slots(const RegOp& r) { return r.csl; }
 // one -- and replace the slot-only diagonal factors of each run by one table op:
 // entry j of a 2^K-entry table is the product of the run's factors at register index j
 // (computed on the host in FP64).
+// Working arrays of merge_diagonals, kept per thread: the function runs once per register
+// stage (tens of thousands of times for a large batch of small circuits), and allocating
+// them on every call cost more than the merge itself.
+struct MergeScratch {
+  std::vector<std::pair<int, int>> edges;   // (from, to)
+  std::vector<int> indeg, seen, soff, succ, fill, pick;
+  std::vector<int> readers[32];
+  std::vector<int> ready[2];   // [0] non-diagonal, [1] diagonal
+  std::vector<RegOp> ord, out, fac, rest, gen;
+};
+
 void merge_diagonals(std::vector<RegOp>& rl, int K, Pool& pool) {
+  thread_local MergeScratch ws;
   const int N = (int)rl.size();
   // conflict edges from per-slot state: op j follows the last op that wrote a slot j reads
   // or writes, and every op that read a slot j writes since that slot's last write (the
   // other conflicts follow by transitivity); O(N K) instead of testing every pair
-  std::vector<std::pair<int, int>> edges;   // (from, to)
-  edges.reserve((size_t)N * 3);
-  std::vector<int> indeg(N, 0), seen(N, -1);
+  std::vector<std::pair<int, int>>& edges = ws.edges;
+  edges.clear();
+  std::vector<int>& indeg = ws.indeg;
+  std::vector<int>& seen = ws.seen;
+  indeg.assign(N, 0);
+  seen.assign(N, -1);
   int last_w[32];
-  std::vector<int> readers[32];
-  for (int b = 0; b < 32; b++) last_w[b] = -1;
+  std::vector<int>* readers = ws.readers;
+  for (int b = 0; b < 32; b++) {
+    last_w[b] = -1;
+    readers[b].clear();
+  }
   auto edge = [&](int i, int j) {
     if (seen[i] == j) return;
     seen[i] = j;
@@ -125,24 +143,30 @@ void merge_diagonals(std::vector<RegOp>& rl, int K, Pool& pool) {
     }
   }
   // successors in one array (counting sort of the edges by source)
-  std::vector<int> soff(N + 1, 0), succ(edges.size());
+  std::vector<int>& soff = ws.soff;
+  std::vector<int>& succ = ws.succ;
+  std::vector<int>& fill = ws.fill;
+  soff.assign(N + 1, 0);
+  succ.resize(edges.size());
   for (const auto& e : edges) soff[e.first + 1]++;
   for (int j = 0; j < N; j++) soff[j + 1] += soff[j];
-  {
-    std::vector<int> fill(soff.begin(), soff.end() - 1);
-    for (const auto& e : edges) succ[fill[e.first]++] = e.second;
-  }
+  fill.assign(soff.begin(), soff.end() - 1);
+  for (const auto& e : edges) succ[fill[e.first]++] = e.second;
   // rounds: every op ready at the round's start of the wanted kind (diagonal, then not), in
   // program order; ops of one round never depend on each other
-  std::vector<RegOp> ord;
+  std::vector<RegOp>& ord = ws.ord;
+  ord.clear();
   ord.reserve(N);
-  std::vector<int> ready[2];   // [0] non-diagonal, [1] diagonal
+  std::vector<int>* ready = ws.ready;
+  ready[0].clear();
+  ready[1].clear();
   for (int j = 0; j < N; j++)
     if (indeg[j] == 0) ready[is_diag(rl[j]) ? 1 : 0].push_back(j);
   int left = N;
   bool want_diag = true;
+  std::vector<int>& pick = ws.pick;
   while (left > 0) {
-    std::vector<int> pick;
+    pick.clear();
     pick.swap(ready[want_diag ? 1 : 0]);
     std::sort(pick.begin(), pick.end());
     for (int j : pick) {
@@ -157,7 +181,11 @@ void merge_diagonals(std::vector<RegOp>& rl, int K, Pool& pool) {
     want_diag = !want_diag;
   }
   rl.swap(ord);
-  std::vector<RegOp> out, fac, rest, gen;
+  std::vector<RegOp>& out = ws.out;
+  std::vector<RegOp>& fac = ws.fac;
+  std::vector<RegOp>& rest = ws.rest;
+  std::vector<RegOp>& gen = ws.gen;
+  out.clear();
   out.reserve(rl.size());
   size_t i = 0;
   const int D = 1 << K;
