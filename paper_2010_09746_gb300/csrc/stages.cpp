@@ -481,10 +481,27 @@ int register_bits(int dtype, int L, int requested) {
   return std::min(k, L);
 }
 
+// Working arrays of build_stages, kept per thread like merge_diagonals' (one call per pass).
+struct StageScratch {
+  std::vector<OpInfo> info;
+  std::vector<std::vector<int>> preds;
+  struct BS {
+    int cls = -1;
+    std::vector<int> cur, prev;
+  };
+  BS bs[32];
+  std::vector<char> done, tmp;
+  std::vector<uint32_t> okm;
+  std::vector<int> rem, take;
+  std::vector<RegOp> rl;
+};
+
 void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* out, int* st0, int* nst) {
   const int N = (int)ops.size();
+  thread_local StageScratch ws;
 
-  std::vector<OpInfo> info(N);
+  std::vector<OpInfo>& info = ws.info;
+  info.resize(N);
   for (int i = 0; i < N; i++) {
     info[i] = classify_op(ops[i]);
     // an op whose non-diagonal bits outnumber the register bits (a 4x4 block with K = 1)
@@ -492,15 +509,18 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
     if (__builtin_popcount(info[i].need) > K) info[i].smem_only = true;
   }
   // dependency DAG over tile bits (same grouping rule as the circuit DAG)
-  std::vector<std::vector<int>> preds(N);
-  struct BS {
-    int cls = -1;
-    std::vector<int> cur, prev;
-  };
-  std::vector<BS> bs(32);
+  std::vector<std::vector<int>>& preds = ws.preds;
+  if (preds.size() < (size_t)N) preds.resize(N);
+  for (int j = 0; j < N; j++) preds[j].clear();
+  StageScratch::BS* bs = ws.bs;
+  for (int b = 0; b < 32; b++) {
+    bs[b].cls = -1;
+    bs[b].cur.clear();
+    bs[b].prev.clear();
+  }
   for (int j = 0; j < N; j++) {
     for (int t = 0; t < info[j].nb; t++) {
-      BS& s = bs[info[j].bit[t]];
+      StageScratch::BS& s = bs[info[j].bit[t]];
       const int c = info[j].cls[t];
       if (s.cls >= 0 && c == s.cls && c != CLS_N) {
         preds[j].insert(preds[j].end(), s.prev.begin(), s.prev.end());
@@ -515,9 +535,14 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
     std::sort(preds[j].begin(), preds[j].end());
     preds[j].erase(std::unique(preds[j].begin(), preds[j].end()), preds[j].end());
   }
-  std::vector<char> done(N, 0), tmp(N, 0);
-  std::vector<uint32_t> okm(N, 0);   // candidate-bit masks of the stage search
-  std::vector<int> rem(N);
+  std::vector<char>& done = ws.done;
+  std::vector<char>& tmp = ws.tmp;
+  done.assign(N, 0);
+  tmp.assign(N, 0);
+  std::vector<uint32_t>& okm = ws.okm;   // candidate-bit masks of the stage search
+  okm.assign(N, 0);
+  std::vector<int>& rem = ws.rem;
+  rem.resize(N);
   for (int i = 0; i < N; i++) rem[i] = i;
   *st0 = (int)out->stages.size();
   auto ready = [&](int v) {
@@ -552,7 +577,8 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
       }
     StageRec st;
     memset(&st, 0, sizeof(st));
-    std::vector<int> take;
+    std::vector<int>& take = ws.take;
+    take.clear();
     if (info[first].smem_only || K < 1) {
       st.kind = 1;
       // every ready shared-memory-only op (in program order, with intra-stage chaining)
@@ -652,7 +678,8 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
       for (int b = 0; b < 32; b++) slot[b] = -1;
       for (int k = 0; k < K; k++) slot[st.rbits[k]] = k;
       const uint32_t R = (uint32_t)st.rmask;
-      std::vector<RegOp> rl;
+      std::vector<RegOp>& rl = ws.rl;
+      rl.clear();
       for (int v : take) {
         const DevOp& o = ops[v];
         RegOp r;
