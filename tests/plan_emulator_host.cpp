@@ -445,8 +445,10 @@ int main(int argc, char** argv) {
   for (const Step& s : cr.steps) {
     switch (s.kind) {
       case ST_PASS:
-        fprintf(stderr, " P%c%c%s", (s.pass.flags & kPassInDF) ? 'd' : 'b', (s.pass.flags & kPassOutDF) ? 'd' : 'b',
-                s.pass.nst == 0 ? "0" : "");
+        // P, form read, form written, "0" for a pass without stages, "s" for a pass whose
+        // store carries a permutation (written out of place)
+        fprintf(stderr, " P%c%c%s%s", (s.pass.flags & kPassInDF) ? 'd' : 'b', (s.pass.flags & kPassOutDF) ? 'd' : 'b',
+                s.pass.nst == 0 ? "0" : "", s.pass.swap_a != s.pass.swap_b ? "s" : "");
         break;
       case ST_GATE: fprintf(stderr, " G"); break;
       case ST_PERMUTE: fprintf(stderr, " X"); break;

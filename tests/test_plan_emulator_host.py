@@ -188,6 +188,31 @@ def test_double_float_storage_between_passes(emulator, mode, dtype, arith, kw):
         assert not uses_df, steps
 
 
+def out_of_place(steps):
+    """Steps that write the state into the second buffer: a permutation kernel, or a tile
+    pass whose store carries a permutation."""
+    return [t for t in steps if t == "X" or (t[0] == "P" and t.endswith("s"))]
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_tile_plans_run_in_place(emulator, dtype):
+    """The serving memory admission counts one state vector per request because tile-mode
+    plans (what the server compiles) never write the state out of place: no permutation
+    kernel, no permutation fused into a pass's store, whatever the circuit.  Algorithm 1's
+    plans on the same circuits do both, so the check can see them."""
+    n = 12
+    circs = [wc.rzrx_cz_circuit(n, 10, seed=3), wc.qft_like_circuit(n), wc.haar_cnot_circuit(n, 8, 4),
+             wc.random_mixed_circuit(n, 200, seed=3, kmax=3), wc.single_qubit_run_circuit(n, 6, seed=3)]
+    seen_paper = []
+    for circ in circs:
+        for kw in ({}, {"tile_bits": 8}, {"tile_bits": 8, "renorm_every": 2}):
+            emulator(n, circ, mode="tile", dtype=dtype, **kw)
+            assert not out_of_place(emulator.steps), (kw, emulator.steps)
+        emulator(n, circ, mode="paper", dtype=dtype, tile_bits=8)
+        seen_paper += out_of_place(emulator.steps)
+    assert any(t == "X" for t in seen_paper) and any(t != "X" for t in seen_paper), seen_paper
+
+
 @pytest.mark.parametrize("dtype,arith", MODES)
 def test_tangent_growth_stays_bounded_in_long_passes(emulator, dtype, arith):
     """A pass of hundreds of tangent-form RX (a deep Haar + CNOT circuit on a tile-sized state,
