@@ -687,7 +687,9 @@ bool compile_tile(int n, const std::vector<HGate>& gates, const std::vector<int>
           if (!S.done[p]) m &= okm[p];
         }
         okm[v] = m;
-        for (uint64_t mm = m; mm; mm &= mm - 1) score[__builtin_ctzll(mm)]++;
+        // a gate that runs under every candidate adds the same to every score: skipped
+        if (m != cand)
+          for (uint64_t mm = m; mm; mm &= mm - 1) score[__builtin_ctzll(mm)]++;
       }
       int best_b = -1, best_s = -1, best_d = -1;
       for (int b = 0; b < n; b++) {

@@ -631,7 +631,9 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
             }
           }
           okm[v] = m;
-          for (uint32_t mm = m; mm; mm &= mm - 1) score[__builtin_ctz(mm)]++;
+          // an op that runs under every candidate adds the same to every score: skipped
+          if (m != cand)
+            for (uint32_t mm = m; mm; mm &= mm - 1) score[__builtin_ctz(mm)]++;
           for (uint32_t nb = in.need & cand; nb; nb &= nb - 1) {
             const int b = __builtin_ctz(nb);
             if (rank[b] == (1 << 30)) rank[b] = (int)r;
