@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../paper_2010_09746_gb300/csrc/qs_internal.h"
@@ -314,6 +315,56 @@ static void run_pass(std::vector<C>& psi, const CompileResult& cr, const TilePas
 // `--euler in.bin out.bin`: the library's Euler split of each 2x2 matrix in in.bin (count,
 // then 8 doubles per matrix, row-major re/im), written as a status and the three factors
 // (d1, rx, d2; 8 doubles each) per matrix, for the test to check against numpy.
+// Every field of a compiled plan that reaches the device or the launches, as bytes (fields
+// one by one, so that struct padding does not enter).
+static std::vector<unsigned char> plan_bytes(const CompileResult& cr) {
+  std::vector<unsigned char> b;
+  auto put = [&](const auto& x) {
+    const unsigned char* p = reinterpret_cast<const unsigned char*>(&x);
+    b.insert(b.end(), p, p + sizeof(x));
+  };
+  for (const Step& s : cr.steps) {
+    put(s.kind); put(s.pass.L); put(s.pass.c); put(s.pass.K); put(s.pass.st0); put(s.pass.nst);
+    put(s.pass.flags); put(s.pass.swap_a); put(s.pass.swap_b); put(s.bytes); put(s.alu); put(s.dense_idx);
+    for (int k = 0; k < s.pass.L; k++) put(s.pass.tpos[k]);
+    for (int v : s.src_of) put(v);
+  }
+  for (const StageRec& st : cr.stages) {
+    put(st.kind); put(st.op0); put(st.nops); put(st.rmask);
+    for (int k = 0; k < 8; k++) put(st.rbits[k]);
+  }
+  for (const RegOp& r : cr.reg_ops) {
+    put(r.type); put(r.s0); put(r.s1); put(r.tb); put(r.neg); put(r.csl); put(r.cot); put(r.mat);
+    put(r.gmask); put(r.gbit);
+  }
+  for (const DevOp& d : cr.tile_ops) {
+    put(d.type); put(d.k0); put(d.k1); put(d.nk); put(d.cmask); put(d.gmask); put(d.mat); put(d.gbit);
+  }
+  for (double v : cr.pool.f64) put(v);
+  for (float v : cr.dense_w) put(v);
+  return b;
+}
+
+// The compiler keeps working arrays per thread: the same circuit compiled on several threads
+// at once, a few times each, must give the serial plan byte for byte.
+static bool threads_consistent(int n, const std::vector<HGate>& gates, const std::vector<int>& sigma0,
+                               const qs_compile_opts& o, const std::vector<unsigned char>& want, int nthreads) {
+  std::vector<int> ok(nthreads, 1);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nthreads; t++)
+    th.emplace_back([&, t] {
+      for (int rep = 0; rep < 3; rep++) {
+        CompileResult cr;
+        std::string e;
+        if (!compile_circuit(n, gates, sigma0, o, &cr, &e) || plan_bytes(cr) != want) ok[t] = 0;
+      }
+    });
+  for (auto& x : th) x.join();
+  for (int v : ok)
+    if (!v) return false;
+  return true;
+}
+
 static int euler_mode(const char* in, const char* out) {
   FILE* f = fopen(in, "rb");
   if (!f) return 2;
@@ -342,8 +393,14 @@ static int euler_mode(const char* in, const char* out) {
 
 int main(int argc, char** argv) {
   if (argc == 4 && std::string(argv[1]) == "--euler") return euler_mode(argv[2], argv[3]);
+  // optional: --threads T (also compile on T threads at once and compare the plans)
+  int nthreads = 0;
+  if (argc == 5 && std::string(argv[3]) == "--threads") {
+    nthreads = atoi(argv[4]);
+    argc = 3;
+  }
   if (argc != 3) {
-    fprintf(stderr, "usage: plan_emulator_host in.bin out.bin | --euler in.bin out.bin\n");
+    fprintf(stderr, "usage: plan_emulator_host in.bin out.bin [--threads T] | --euler in.bin out.bin\n");
     return 2;
   }
   FILE* f = fopen(argv[1], "rb");
@@ -384,6 +441,8 @@ int main(int argc, char** argv) {
     fprintf(stderr, "compile: %s\n", err.c_str());
     return 4;
   }
+  if (nthreads > 0)
+    fprintf(stderr, "threads_consistent %d\n", threads_consistent(n, gates, sigma0, o, plan_bytes(cr), nthreads) ? 1 : 0);
   std::vector<C> psi(1ull << n, C(0, 0));
   psi[0] = 1;
   for (const Step& s : cr.steps) {

@@ -49,7 +49,7 @@ def emulator(tmp_path_factory):
     r = subprocess.run([nvcc, "-std=c++17", "-O2", "-o", exe] + srcs, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-3000:]
 
-    def run(n, circ, cost=None, **opts):
+    def run(n, circ, cost=None, threads=0, **opts):
         ops, nops, mats = qs.marshal(circ)
         o = qs._opts(**opts)
         inp, out = str(d / "in.bin"), str(d / "out.bin")
@@ -61,8 +61,11 @@ def emulator(tmp_path_factory):
             f.write(bytes(ops)[: nops * 48])
             if nops:
                 f.write(np.ascontiguousarray(mats, dtype=np.float64).tobytes())
-        r = subprocess.run([exe, inp, out], capture_output=True, text=True, timeout=600)
+        extra = ["--threads", str(threads)] if threads else []
+        r = subprocess.run([exe, inp, out] + extra, capture_output=True, text=True, timeout=600)
         assert r.returncode == 0, r.stderr[-3000:]
+        run.threads_consistent = (int(r.stderr.split("threads_consistent")[1].split()[0])
+                                  if threads else None)
         run.max_register_abs = float(r.stderr.split("max_register_abs")[1].split()[0])
         run.min_register_scale = float(r.stderr.split("min_register_scale")[1].split()[0])
         run.steps = r.stderr.split("steps", 1)[1].splitlines()[0].split()
@@ -186,6 +189,18 @@ def test_double_float_storage_between_passes(emulator, mode, dtype, arith, kw):
         assert sum(t[0] == "P" for t in steps) >= 2 and uses_df, steps
     if arith != "df":
         assert not uses_df, steps
+
+
+@pytest.mark.parametrize("dtype,arith", MODES)
+def test_compiles_on_many_threads_at_once(emulator, dtype, arith):
+    """Batch builds and the server compile on many host threads at once, and the compiler
+    keeps its working arrays per thread: eight threads compiling the same circuits three
+    times each produce the serial plan byte for byte (stages, register ops, pool entries)."""
+    rng = np.random.default_rng(13)
+    for n, circ in ((12, wc.rzrx_cz_circuit(12, 10, seed=13)), (14, wc.mixed_batch_circuit(14, 30, rng)),
+                    (11, wc.qft_like_circuit(11))):
+        emulator(n, circ, dtype=dtype, arith=arith, threads=8)
+        assert emulator.threads_consistent == 1
 
 
 def out_of_place(steps):
