@@ -393,3 +393,61 @@ def test_no_dense_flag_and_default_model(emulator):
         _lib.check(_lib.load().qs_plan_get_stats(h, ctypes.byref(st)))
         _lib.load().qs_plan_destroy(h)
         assert st.n_dense == want, (dtype, kw)
+
+
+def test_random_configurations(emulator):
+    """Seeded random circuits and compile options together: 3-12 qubits; every gate kind, or
+    a few kinds, or diagonal-heavy, X-heavy, single-qubit runs, the benchmark construction
+    plus Appendix C's circuit; tile, Algorithm 1 and per-gate modes; random tile, low and
+    register bits, renormalisation, full-form RX, fusion off.  Every plan matches the oracle;
+    the only refusal allowed is a gate wider than the tile the options leave room for."""
+    kinds_all = [k for k in wc.KINDS if k != "RELABEL"]
+    diag = ["Z", "S", "T", "RZ", "P", "CZ", "CP", "U1"]
+    xs = ["X", "RX", "CNOT", "H", "U1", "RY"]
+    refused = 0
+    for seed in range(150):
+        rng = np.random.default_rng(1000 + seed)
+        n = int(rng.integers(3, 13))
+        dtype, arith = MODES[int(rng.integers(0, 3))]
+        mode = ["tile", "tile", "tile", "paper", "pergate"][int(rng.integers(0, 5))]
+        which = int(rng.integers(0, 6))
+        kmax = int(rng.integers(1, 4))
+        ng = int(rng.integers(1, 300))
+        if which == 0:
+            circ = wc.random_mixed_circuit(n, ng, seed=seed, kmax=kmax)
+        elif which == 1:
+            kinds = [str(k) for k in rng.choice(kinds_all, size=int(rng.integers(1, 5)), replace=False)]
+            circ = wc.random_mixed_circuit(n, ng, seed=seed, kinds=kinds, kmax=kmax)
+        elif which == 2:
+            circ = wc.random_mixed_circuit(n, ng, seed=seed, kinds=diag, kmax=kmax)
+        elif which == 3:
+            circ = wc.random_mixed_circuit(n, ng, seed=seed, kinds=xs, kmax=kmax)
+        elif which == 4:
+            circ = wc.single_qubit_run_circuit(n, int(rng.integers(1, 8)), seed=seed)
+        else:
+            circ = wc.rzrx_cz_circuit(n, int(rng.integers(1, 10)), seed=seed) + wc.qft_like_circuit(n)
+        kw = {}
+        if mode != "pergate":
+            if rng.random() < 0.7:
+                kw["tile_bits"] = int(rng.integers(min(n, 3), n + 1))
+                if rng.random() < 0.5:
+                    kw["low_bits"] = int(rng.integers(0, max(1, kw["tile_bits"] - 2)))
+            if rng.random() < 0.3:
+                kw["reg_bits"] = int(rng.integers(1, 6))
+        if rng.random() < 0.2:
+            kw["renorm_every"] = int(rng.integers(1, 4))
+        if rng.random() < 0.2:
+            kw["full_rx"] = True
+        if rng.random() < 0.2:
+            kw["fuse"] = False
+        what = f"seed {seed}: n={n} {dtype}/{arith} {mode} circuit {which} {kw}"
+        try:
+            got, _ = emulator(n, circ, mode=mode, dtype=dtype, arith=arith, **kw)
+        except AssertionError as e:
+            assert "needs more qubits than a tile holds" in str(e) and "tile_bits" in kw, (what, str(e)[-500:])
+            refused += 1
+            continue
+        ref = sv.simulate(n, circ)
+        err = float(np.max(np.abs(got - ref)))
+        assert err <= TOL, (what, err)
+    assert refused < 40, refused
