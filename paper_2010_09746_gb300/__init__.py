@@ -9,6 +9,7 @@ torch.cuda.Stream.
 from __future__ import annotations
 
 import ctypes
+import itertools
 from typing import Iterable, List, Optional, Sequence
 
 import numpy as np
@@ -48,30 +49,48 @@ def _cmat(m) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(m, dtype=np.complex128)).view(np.float64).ravel().copy()
 
 
+# qs_op as a numpy record (same field order, sizes and alignment as the C struct)
+_OP_DTYPE = np.dtype([("kind", "<i4"), ("nq", "<i4"), ("q", "<i4", (6,)), ("param", "<f8"), ("mat", "<i8")],
+                     align=True)
+assert _OP_DTYPE.itemsize == ctypes.sizeof(_lib.qs_op)
+
+
 def marshal(circuit: Iterable):
-    """Gate objects (attributes kind, qubits, param, matrix) -> (qs_op array, matrix doubles)."""
+    """Gate objects (attributes kind, qubits, param, matrix) -> (qs_op array, matrix doubles).
+
+    The fields are gathered with one list comprehension each and written column by column
+    into a record array that the qs_op array shares, and the matrices are concatenated in
+    one call, so that a batch of millions of gates marshals in C loops rather than one
+    ctypes field write at a time."""
     gates = list(circuit)
-    ops = (_lib.qs_op * max(1, len(gates)))()
-    mats: List[np.ndarray] = []
-    off = 0
-    for i, g in enumerate(gates):
-        o = ops[i]
-        o.kind = _lib.OP_CODES[g.kind]
-        qs = tuple(g.qubits)
-        o.nq = len(qs)
-        for t, q in enumerate(qs):
-            o.q[t] = int(q)
-        o.param = float(getattr(g, "param", 0.0) or 0.0)
-        m = getattr(g, "matrix", None)
-        if m is not None:
-            flat = _cmat(m)
-            o.mat = off
-            mats.append(flat)
-            off += flat.size
-        else:
-            o.mat = -1
-    buf = np.concatenate(mats) if mats else np.zeros(1)
-    return ops, len(gates), np.ascontiguousarray(buf, dtype=np.float64)
+    N = len(gates)
+    rec = np.zeros(max(1, N), dtype=_OP_DTYPE)
+    codes = _lib.OP_CODES
+    rec["kind"][:N] = [codes[g.kind] for g in gates]
+    qls = [tuple(g.qubits) for g in gates]
+    nq = np.fromiter(map(len, qls), dtype=np.int64, count=N)
+    if N and int(nq.max()) > 6:
+        raise ValueError("a gate acts on more than 6 qubits")
+    rec["nq"][:N] = nq
+    total = int(nq.sum())
+    if total:   # qubit t of gate i goes to q[i][t]
+        flat = np.fromiter(itertools.chain.from_iterable(qls), dtype=np.int64, count=total)
+        row = np.repeat(np.arange(N), nq)
+        col = np.arange(total) - np.repeat(np.cumsum(nq) - nq, nq)
+        rec["q"][row, col] = flat
+    rec["param"][:N] = [float(getattr(g, "param", 0.0) or 0.0) for g in gates]
+    ms = [getattr(g, "matrix", None) for g in gates]
+    has = [i for i, m in enumerate(ms) if m is not None]
+    rec["mat"][:N] = -1
+    if has:
+        arrs = [np.asarray(ms[i], dtype=np.complex128) for i in has]
+        sizes = np.fromiter(map(np.size, arrs), dtype=np.int64, count=len(arrs))
+        rec["mat"][np.array(has)] = 2 * (np.cumsum(sizes) - sizes)   # first double of each matrix
+        buf = np.concatenate(arrs, axis=None).view(np.float64)      # each matrix row-major
+    else:
+        buf = np.zeros(1)
+    ops = (_lib.qs_op * max(1, N)).from_buffer(rec)
+    return ops, N, np.ascontiguousarray(buf, dtype=np.float64)
 
 
 def _opts(mode="tile", dtype="c128", arith="auto", tile_bits=0, low_bits=0, max_ops=0, scoring=0, reg_bits=0,

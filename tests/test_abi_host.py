@@ -39,6 +39,37 @@ def test_struct_layout():
     assert ctypes.sizeof(_lib.qs_cost_model) == 96
 
 
+def test_marshal_matches_field_by_field():
+    """The binding's column-wise marshalling gives the qs_op records and matrix doubles that
+    writing each struct field in turn gives: kind, qubits, param, the first double of the
+    gate's matrix (-1 without one), and each matrix as row-major (re, im) pairs."""
+    rng = np.random.default_rng(4)
+    circs = [wc.random_mixed_circuit(12, 400, seed=4, kmax=6), wc.qft_like_circuit(9),
+             wc.rzrx_cz_circuit(7, 3, seed=4), [], [wc.Gate("UK", (3, 0, 5), matrix=wc.haar_unitary(8, rng))],
+             wc.mixed_batch_circuit(14, 20, rng)]
+    for circ in circs:
+        ops, n, mats = qs.marshal(circ)
+        assert n == len(circ)
+        want_mats = []
+        off = 0
+        for i, g in enumerate(circ):
+            o = ops[i]
+            assert o.kind == _lib.OP_CODES[g.kind] and o.nq == len(g.qubits)
+            assert list(o.q)[:o.nq] == list(g.qubits) and all(v == 0 for v in list(o.q)[o.nq:])
+            assert o.param == float(g.param or 0.0)
+            if g.matrix is None:
+                assert o.mat == -1
+            else:
+                assert o.mat == off
+                flat = [x for z in np.asarray(g.matrix, dtype=complex).ravel() for x in (z.real, z.imag)]
+                want_mats += flat
+                off += len(flat)
+        if want_mats:
+            assert np.array_equal(mats, np.array(want_mats))
+    with pytest.raises(ValueError):
+        qs.marshal([type("G", (), {"kind": "UK", "qubits": tuple(range(7)), "param": 0.0, "matrix": None})()])
+
+
 def test_version():
     assert b"sm_103a" in _lib.load().qs_version()
 
