@@ -280,6 +280,7 @@ void merge_diagonals(std::vector<RegOp>& rl, int K, Pool& pool) {
     i = e;
   }
   rl.swap(out);
+  if (N > (1 << 16)) ws = MergeScratch();   // keep no arrays of an unusually large stage
 }
 
 }  // namespace
@@ -792,6 +793,8 @@ void build_stages(const std::vector<DevOp>& ops, int L, int K, CompileResult* ou
   fold_pass_factors(out, *st0, *nst, K);
   merge_rxt_runs(out, *st0, *nst);
   if (out->pol == POL_DF) apply_phase_frame(out, *st0, *nst);
+  // a thread keeps its arrays between passes, but not those of an unusually large one
+  if (preds.size() > (1u << 16)) ws = StageScratch();
 }
 
 }  // namespace qs
